@@ -1,0 +1,96 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the benchmark.
+
+This module only draws random numbers and lays out mesh vertex coordinates; it holds none of the
+finite-element arithmetic (no basis functions, quadrature, gather/scatter or operator). Both the
+CPU oracle and the CUDA library receive exactly these arrays.
+
+Inputs (the paper's cube / ball sweeps are not available, so these stand in for them):
+  * a box mesh of the unit cube with ``nx*ny*nz`` hexahedra, vertex ``(ix, iy, iz)`` at
+    ``(ix/nx, iy/ny, iz/nz)`` optionally moved by a smooth sinusoidal displacement of amplitude
+    ``0.1*h`` that vanishes on the boundary of the cube (so the domain stays the unit cube);
+  * global vectors of length ``(nx*p+1)*(ny*p+1)*(nz*p+1)`` drawn uniform in [-1, 1];
+  * raw cell-wise arrays of length ``E*(p+1)^3`` drawn uniform in [-1, 1] (unassembled duals).
+"""
+from dataclasses import dataclass
+import math
+import numpy as np
+
+__all__ = ["Mesh", "box_mesh", "global_vector", "cellwise_random", "batched_problem_list",
+           "global_len", "cellwise_len"]
+
+
+@dataclass
+class Mesh:
+    nx: int
+    ny: int
+    nz: int
+    verts: np.ndarray  # float64, shape (nz+1, ny+1, nx+1, 3), C-contiguous
+    affine: bool       # True when no displacement was applied (uniform Cartesian cells)
+
+    @property
+    def ncells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+def box_mesh(nx, ny=None, nz=None, perturb=0.0, freq=(1, 1, 1), direction=None) -> Mesh:
+    """Unit-cube box mesh; ``perturb`` is the displacement amplitude in units of h = 1/max(n).
+
+    Displacement: ``perturb*h * sin(2 pi fx X) sin(2 pi fy Y) sin(2 pi fz Z) * direction`` with
+    ``direction`` a unit vector (default (1,1,1)/sqrt(3)). It is zero on the boundary faces.
+    """
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    x = np.arange(nx + 1, dtype=np.float64) / nx
+    y = np.arange(ny + 1, dtype=np.float64) / ny
+    z = np.arange(nz + 1, dtype=np.float64) / nz
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    verts = np.stack([X, Y, Z], axis=-1)
+    if perturb != 0.0:
+        h = 1.0 / max(nx, ny, nz)
+        d = np.ones(3) / math.sqrt(3.0) if direction is None else np.asarray(direction, np.float64)
+        d = d / np.linalg.norm(d)
+        s = (np.sin(2 * np.pi * freq[0] * X) * np.sin(2 * np.pi * freq[1] * Y)
+             * np.sin(2 * np.pi * freq[2] * Z))
+        verts = verts + perturb * h * s[..., None] * d[None, None, None, :]
+        # snap the boundary exactly (sin(2 pi k) is not exactly 0 in floating point)
+        verts[:, :, 0, 0] = 0.0
+        verts[:, :, -1, 0] = 1.0
+        verts[:, 0, :, 1] = 0.0
+        verts[:, -1, :, 1] = 1.0
+        verts[0, :, :, 2] = 0.0
+        verts[-1, :, :, 2] = 1.0
+    return Mesh(nx, ny, nz, np.ascontiguousarray(verts), affine=(perturb == 0.0))
+
+
+def global_len(mesh: Mesh, p: int) -> int:
+    return (mesh.nx * p + 1) * (mesh.ny * p + 1) * (mesh.nz * p + 1)
+
+
+def cellwise_len(mesh: Mesh, p: int) -> int:
+    return mesh.ncells * (p + 1) ** 3
+
+
+def global_vector(mesh: Mesh, p: int, seed: int = 0) -> np.ndarray:
+    """Uniform[-1,1] global vector in global lexicographic order (x fastest)."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, global_len(mesh, p))
+
+
+def cellwise_random(mesh: Mesh, p: int, seed: int = 0) -> np.ndarray:
+    """Uniform[-1,1] raw cell-wise array (no continuity), layout [cell][k][j][i]."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, cellwise_len(mesh, p))
+
+
+def batched_problem_list(count: int = 48, seed: int = 0, lo: int = 8, hi: int = 48,
+                         degrees=(2, 3, 5, 7)):
+    """Uneven batch: problem i has N_i ~ U{lo..hi} cells per direction, degree degrees[i % 4],
+    a displacement with seeded integer frequencies in {1,2,3} and a seeded unit direction."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(lo, hi + 1))
+        r = np.random.default_rng(i)
+        freq = tuple(int(f) for f in r.integers(1, 4, 3))
+        d = r.normal(size=3)
+        out.append(dict(n=n, p=degrees[i % len(degrees)], freq=freq, direction=d / np.linalg.norm(d),
+                        seed=i))
+    return out
