@@ -1,0 +1,175 @@
+/*
+ * cwfem.h -- C ABI of the GB300 (sm_103a) library for matrix-free high-order finite-element
+ * operators on cell-wise (redundant, element-local) storage.
+ *
+ * The method follows "Coalesced Matrix-Free Geometric Multigrid on Persistent Cell-Wise Storage":
+ *  - cell-wise storage, primal / dual vectors, gather G and assembly G^T: Sec. 2.1;
+ *  - the cell-local operator A: V_cell -> V_cell^*, applied matrix-free: Sec. 2.1,
+ *    Eq. (constrained_system) and the paragraph before it;
+ *  - the Poisson weak form with Q_p Gauss-Lobatto nodal elements: Sec. 2, Eq. (poisson);
+ *  - the Cartesian factored operator with one per-element scalar and the general curved
+ *    operator (gradients -> metric -> integrate gradients): Sec. 6, first paragraphs;
+ *  - direct stiffness summation S = G G^T: Sec. 4.1, Eq. (dss_operator); its structured
+ *    dimension-split realisation: Sec. 4.3, Algorithm struct_dss; averaging DSS: Sec. 5,
+ *    Eq. (averaging_dss);
+ *  - the Jacobi preconditioner D_cell^-1 S: Sec. 4.1, Eq. (jacobi_recap), with Dirichlet rows
+ *    zeroed in the stored inverse diagonal: Sec. 5, "Constraints baked into the diagonal";
+ *  - conjugate gradients in primal-dual form on cell-wise data: Sec. 4.4 and Sec. 6 (CG
+ *    preconditioned by a consistent operator is iterate-identical to assembled CG).
+ *
+ * Conventions (all entry points):
+ *  - Reference cell [0,1]^3. Degree p in 1..7, n = p+1 Gauss-Lobatto nodes and n Gauss points
+ *    per direction.
+ *  - A mesh is an nx*ny*nz block of trilinear hexahedra. Cells are numbered cx + nx*(cy + ny*cz).
+ *  - Cell-wise vectors have E*n^3 entries, layout [cell][k][j][i] (i along x fastest), a dense
+ *    caller-owned DEVICE array. Entry type follows the operator precision: double for CW_PREC_F64
+ *    and CW_PREC_F64_NATIVE, float for CW_PREC_F32 and CW_PREC_F32_BF16G, bfloat16 (uint16 bits)
+ *    for CW_PREC_BF16.
+ *  - Global vectors have (nx*p+1)(ny*p+1)(nz*p+1) doubles, index gx + Gx*(gy + Gy*gz).
+ *  - Primal inputs are continuous (all copies of a DoF equal); outputs of CW_APPLY_LOCAL are
+ *    unassembled duals (copies hold partial integrals).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Every call is
+ *    asynchronous on that stream unless stated otherwise; argument errors are detected on the
+ *    host before anything is enqueued and returned as a status; device-side errors surface as
+ *    CW_ERR_CUDA from the next call that synchronises.
+ *  - Ownership: the library owns geometry, tables, diagonals and solver scratch, all allocated
+ *    at create time (or at the first call that needs them, as documented). The caller owns every
+ *    pointer it passes. Inputs and outputs must not alias unless stated.
+ *  - Thread safety: distinct handles may be used from distinct threads; one handle must not be
+ *    used by two streams at the same time.
+ */
+#ifndef CWFEM_H
+#define CWFEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cw_mesh_s *cw_mesh;
+typedef struct cw_op_s *cw_op;
+
+typedef enum {
+    CW_OK = 0,
+    CW_ERR_ARG = 1,           /* invalid argument (NULL handle, bad size, unsupported combination) */
+    CW_ERR_OOM = 2,           /* device allocation failed */
+    CW_ERR_CUDA = 3,          /* a CUDA call failed; cw_last_error() has the message */
+    CW_ERR_NOT_CONVERGED = 4, /* solver hit maxit before the tolerance */
+    CW_ERR_BREAKDOWN = 5,     /* CG breakdown: <p,Ap> <= 0 or a non-finite scalar */
+    CW_ERR_TIMEOUT = 6,       /* a bounded device wait expired */
+    CW_ERR_UNSUPPORTED = 7    /* valid request that this build does not implement */
+} cw_status;
+
+/* operator kinds */
+#define CW_LAPLACE 1      /* K_ij = int grad phi_i . grad phi_j */
+#define CW_MASS 2         /* M_ij = int phi_i phi_j */
+#define CW_LAPLACE_MASS 3 /* K + M */
+
+/* geometry representations */
+#define CW_GEOM_AFFINE 0 /* Cartesian cells: factored 1D stiffness/mass form, per-cell scalars */
+#define CW_GEOM_METRIC 1 /* curved trilinear cells: metric w detJ J^-1 J^-T stored per quad. point */
+
+/* precisions (vector storage / metric storage / arithmetic) */
+#define CW_PREC_F64 0        /* FP64 / FP64 / double-float (FP32 pair, ~47-bit) arithmetic */
+#define CW_PREC_F64_NATIVE 1 /* FP64 / FP64 / native FP64 FMA (reference speed baseline) */
+#define CW_PREC_F32 2        /* FP32 / FP32 / FP32 */
+#define CW_PREC_F32_BF16G 3  /* FP32 / BF16 / FP32 */
+#define CW_PREC_BF16 4       /* BF16 / BF16 / FP32 accumulate */
+
+/* boundary conditions (used by the diagonal and the solver) */
+#define CW_BC_NONE 0
+#define CW_BC_DIRICHLET0 1 /* homogeneous Dirichlet on the boundary of the block */
+
+/* apply flags */
+#define CW_APPLY_LOCAL 0    /* y = A x, unassembled dual */
+#define CW_APPLY_ASSEMBLE 1 /* y = S A x = G A_CG x_g for continuous x */
+
+/* dss flags */
+#define CW_DSS_SUM 0     /* v <- S v = G G^T v */
+#define CW_DSS_AVERAGE 1 /* v <- S_bar v = G (G^T G)^-1 G^T v */
+
+/* cg modes */
+#define CW_CG_F64 0     /* Jacobi-PCG, everything FP64 (double-float apply) */
+#define CW_CG_IR_F32 1  /* FP64 iterative refinement around an FP32 Jacobi-PCG */
+#define CW_CG_IR_BF16 2 /* as IR_F32 with the inner metric stored in BF16 */
+
+typedef struct {
+    int iterations;        /* total CG iterations (inner iterations summed for IR modes) */
+    int outer_iterations;  /* IR refinement steps (1 for CW_CG_F64) */
+    double rel_residual;   /* ||m G^T(b - A u)|| / ||m G^T b|| on interior DoFs, in FP64 */
+    double energy;         /* eta(u) = <b - A u, u>, Sec. 3.5 Eq. (energy_measure) */
+    double seconds;        /* wall time of the solve measured with CUDA events on `stream` */
+} cw_cg_stats;
+
+/* Human-readable name of a status code; never NULL. */
+const char *cw_status_string(cw_status s);
+/* Message of the last error raised on the calling thread ("" if none). */
+const char *cw_last_error(void);
+
+/*
+ * Create a mesh from host vertex coordinates verts[((vz*(ny+1) + vy)*(nx+1) + vx)*3 + d]
+ * (double, (nx+1)(ny+1)(nz+1)*3 entries, copied to the device). Cell (cx,cy,cz) is the trilinear
+ * image of [0,1]^3 through its 8 vertices. nx, ny, nz >= 1. The mesh must outlive its operators.
+ */
+cw_status cw_mesh_create(int nx, int ny, int nz, const double *verts_host, cw_mesh *out);
+cw_status cw_mesh_destroy(cw_mesh m);
+
+/*
+ * Create an operator of degree p on a mesh (Sec. 2.1). Allocates and fills the geometry
+ * (CW_GEOM_METRIC: ncomp values per quadrature point, ncomp = 6 Laplace, 1 mass, 7 both, stored
+ * in the metric precision; CW_GEOM_AFFINE: 4 doubles per cell, and the mesh must be Cartesian --
+ * CW_ERR_ARG otherwise) and the 1D tables. Synchronous.
+ */
+cw_status cw_op_create(cw_mesh m, int degree, int kind, int geom, int prec, int bc, cw_op *out);
+cw_status cw_op_destroy(cw_op op);
+int64_t cw_op_cellwise_len(cw_op op); /* E * (p+1)^3, or -1 for a NULL handle */
+int64_t cw_op_global_len(cw_op op);   /* (nx p + 1)(ny p + 1)(nz p + 1), or -1 */
+/* Bytes of device memory the operator owns (geometry, tables, diagonal, solver scratch). */
+int64_t cw_op_device_bytes(cw_op op);
+
+/* x = G u: replicate a device global FP64 vector into cell-wise storage of the op's precision. */
+cw_status cw_gather(cw_op op, const double *u_global, void *x, void *stream);
+
+/*
+ * y = A x (flags = CW_APPLY_LOCAL) or y = S A x (CW_APPLY_ASSEMBLE). x primal, y dual;
+ * both cell-wise device arrays of the op's vector type; x and y must not alias.
+ */
+cw_status cw_apply(cw_op op, const void *x, void *y, int flags, void *stream);
+
+/*
+ * In-place DSS on a cell-wise device array of the op's vector type: v <- S v (CW_DSS_SUM,
+ * Algorithm struct_dss: three sequential axis passes over all interior faces) or
+ * v <- S_bar v (CW_DSS_AVERAGE: the sum divided by the DoF valence).
+ */
+cw_status cw_dss(cw_op op, void *v, int flags, void *stream);
+
+/*
+ * Cell-wise assembled diagonal: d = G diag(A_CG) (FP64, E*n^3 doubles), Sec. 4.1. With
+ * bc = CW_BC_DIRICHLET0 the entries of boundary DoFs are those of A_CG all the same.
+ */
+cw_status cw_diagonal(cw_op op, double *d, void *stream);
+
+/*
+ * Unassembled load vector b_K,i = sum_q w_q detJ f(x_q) phi_i(x_q) (FP64 cell-wise) for the
+ * manufactured problems: which = 0: f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z); which = 1:
+ * f = 2[y(1-y)z(1-z) + x(1-x)z(1-z) + x(1-x)y(1-y)]. Needs a CW_GEOM_METRIC or AFFINE op.
+ */
+cw_status cw_load_vector(cw_op op, int which, double *b, void *stream);
+
+/*
+ * Solve A_CG u_g = G^T b for the Poisson / K+M operator with homogeneous Dirichlet conditions
+ * (op bc must be CW_BC_DIRICHLET0, precision CW_PREC_F64), by Jacobi-preconditioned CG on
+ * cell-wise data from u = 0 (Sec. 4.1 Eq. (jacobi_recap); Sec. 4.4). b: FP64 cell-wise dual;
+ * u: FP64 cell-wise primal output. Stops when rel_residual <= rtol or after maxit iterations
+ * (CW_ERR_NOT_CONVERGED; u then holds the last iterate). mode selects FP64 CG or FP64 iterative
+ * refinement around an FP32 (or BF16-metric) inner CG. The first IR call on an op allocates the
+ * inner operator and its vectors. Synchronises `stream`. stats may be NULL.
+ */
+cw_status cw_cg_solve(cw_op op, const double *b, double *u, double rtol, int maxit, int mode,
+                      cw_cg_stats *stats, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CWFEM_H */

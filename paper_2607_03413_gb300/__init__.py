@@ -1,0 +1,266 @@
+"""Python binding of libcwfem.so, the sm_103a library for matrix-free high-order FEM operators on
+cell-wise storage (apply, direct stiffness summation, Jacobi-PCG / mixed-precision refined CG).
+
+This module only marshals arguments: every step of the computation runs in the library's CUDA
+kernels. PyTorch tensors serve as device memory (``tensor.data_ptr()``) and streams
+(``torch.cuda.current_stream().cuda_stream``). There is no CPU fallback: if the compiled library
+is missing, loading fails with an error.
+
+The functions ``cw_*`` have the names and argument order of ``include/cwfem.h``; ``Mesh`` and
+``Operator`` hold handles and take tensors.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcwfem.so")
+
+# constants mirrored from include/cwfem.h
+CW_OK, CW_ERR_ARG, CW_ERR_OOM, CW_ERR_CUDA = 0, 1, 2, 3
+CW_ERR_NOT_CONVERGED, CW_ERR_BREAKDOWN, CW_ERR_TIMEOUT, CW_ERR_UNSUPPORTED = 4, 5, 6, 7
+CW_LAPLACE, CW_MASS, CW_LAPLACE_MASS = 1, 2, 3
+CW_GEOM_AFFINE, CW_GEOM_METRIC = 0, 1
+CW_PREC_F64, CW_PREC_F64_NATIVE, CW_PREC_F32, CW_PREC_F32_BF16G, CW_PREC_BF16 = 0, 1, 2, 3, 4
+CW_BC_NONE, CW_BC_DIRICHLET0 = 0, 1
+CW_APPLY_LOCAL, CW_APPLY_ASSEMBLE = 0, 1
+CW_DSS_SUM, CW_DSS_AVERAGE = 0, 1
+CW_CG_F64, CW_CG_IR_F32, CW_CG_IR_BF16 = 0, 1, 2
+
+# exported symbols declared in include/cwfem.h (checked by the CPU test suite)
+EXPORTED = [
+    "cw_status_string", "cw_last_error", "cw_mesh_create", "cw_mesh_destroy", "cw_op_create",
+    "cw_op_destroy", "cw_op_cellwise_len", "cw_op_global_len", "cw_op_device_bytes", "cw_gather",
+    "cw_apply", "cw_dss", "cw_diagonal", "cw_load_vector", "cw_cg_solve",
+]
+
+
+class CwError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.cw_last_error().decode() if _lib is not None else ""
+        super().__init__(f"{where}: {_lib.cw_status_string(status).decode()} {msg}")
+
+
+class cw_cg_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("energy", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcwfem.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libcwfem.so not found at {path}: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "cw_status_string": ([i32], ctypes.c_char_p),
+        "cw_last_error": ([], ctypes.c_char_p),
+        "cw_mesh_create": ([i32, i32, i32, vp, ctypes.POINTER(vp)], i32),
+        "cw_mesh_destroy": ([vp], i32),
+        "cw_op_create": ([vp, i32, i32, i32, i32, i32, ctypes.POINTER(vp)], i32),
+        "cw_op_destroy": ([vp], i32),
+        "cw_op_cellwise_len": ([vp], i64),
+        "cw_op_global_len": ([vp], i64),
+        "cw_op_device_bytes": ([vp], i64),
+        "cw_gather": ([vp, vp, vp, vp], i32),
+        "cw_apply": ([vp, vp, vp, i32, vp], i32),
+        "cw_dss": ([vp, vp, i32, vp], i32),
+        "cw_diagonal": ([vp, vp, vp], i32),
+        "cw_load_vector": ([vp, i32, vp, vp], i32),
+        "cw_cg_solve": ([vp, vp, vp, dbl, i32, i32, ctypes.POINTER(cw_cg_stats), vp], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(st, where):
+    if st != CW_OK:
+        raise CwError(st, where)
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return ctypes.c_void_p(stream)
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if hasattr(t, "is_cuda") and not t.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(int(t))
+
+
+# ------------------------------------------------------------------ C-ABI mirrors ----
+def cw_mesh_create(nx, ny, nz, verts_host):
+    import numpy as np
+    L = load()
+    v = np.ascontiguousarray(verts_host, dtype=np.float64)
+    assert v.size == (nx + 1) * (ny + 1) * (nz + 1) * 3
+    h = ctypes.c_void_p()
+    _check(L.cw_mesh_create(nx, ny, nz, v.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)), "cw_mesh_create")
+    return h
+
+
+def cw_mesh_destroy(h):
+    _check(load().cw_mesh_destroy(h), "cw_mesh_destroy")
+
+
+def cw_op_create(mesh, degree, kind, geom, prec, bc=CW_BC_NONE):
+    h = ctypes.c_void_p()
+    _check(load().cw_op_create(mesh, degree, kind, geom, prec, bc, ctypes.byref(h)), "cw_op_create")
+    return h
+
+
+def cw_op_destroy(h):
+    _check(load().cw_op_destroy(h), "cw_op_destroy")
+
+
+def cw_op_cellwise_len(h):
+    return load().cw_op_cellwise_len(h)
+
+
+def cw_op_global_len(h):
+    return load().cw_op_global_len(h)
+
+
+def cw_op_device_bytes(h):
+    return load().cw_op_device_bytes(h)
+
+
+def cw_gather(op, u_global, x, stream=None):
+    _check(load().cw_gather(op, _ptr(u_global), _ptr(x), _stream(stream)), "cw_gather")
+
+
+def cw_apply(op, x, y, flags=CW_APPLY_LOCAL, stream=None):
+    _check(load().cw_apply(op, _ptr(x), _ptr(y), flags, _stream(stream)), "cw_apply")
+
+
+def cw_dss(op, v, flags=CW_DSS_SUM, stream=None):
+    _check(load().cw_dss(op, _ptr(v), flags, _stream(stream)), "cw_dss")
+
+
+def cw_diagonal(op, d, stream=None):
+    _check(load().cw_diagonal(op, _ptr(d), _stream(stream)), "cw_diagonal")
+
+
+def cw_load_vector(op, which, b, stream=None):
+    _check(load().cw_load_vector(op, which, _ptr(b), _stream(stream)), "cw_load_vector")
+
+
+def cw_cg_solve(op, b, u, rtol=1e-10, maxit=10000, mode=CW_CG_F64, stream=None, check=True):
+    st = cw_cg_stats()
+    rc = load().cw_cg_solve(op, _ptr(b), _ptr(u), rtol, maxit, mode, ctypes.byref(st), _stream(stream))
+    if check and rc not in (CW_OK,):
+        raise CwError(rc, "cw_cg_solve")
+    return rc, st
+
+
+# ------------------------------------------------------------------ convenience ----
+_VEC_DTYPE = {CW_PREC_F64: "float64", CW_PREC_F64_NATIVE: "float64", CW_PREC_F32: "float32",
+              CW_PREC_F32_BF16G: "float32", CW_PREC_BF16: "bfloat16"}
+
+
+class Mesh:
+    """Owns a cw_mesh handle built from a vertex array [(nz+1),(ny+1),(nx+1),3]."""
+
+    def __init__(self, nx, ny, nz, verts):
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.handle = cw_mesh_create(nx, ny, nz, verts)
+
+    @classmethod
+    def from_synth(cls, m):
+        return cls(m.nx, m.ny, m.nz, m.verts)
+
+    def close(self):
+        if self.handle:
+            cw_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Operator:
+    """Owns a cw_op handle; methods take torch tensors on the current CUDA device."""
+
+    def __init__(self, mesh: Mesh, degree, kind=CW_LAPLACE, geom=CW_GEOM_METRIC, prec=CW_PREC_F64,
+                 bc=CW_BC_NONE):
+        self.mesh = mesh
+        self.degree, self.kind, self.geom, self.prec, self.bc = degree, kind, geom, prec, bc
+        self.handle = cw_op_create(mesh.handle, degree, kind, geom, prec, bc)
+        self.L = cw_op_cellwise_len(self.handle)
+        self.NG = cw_op_global_len(self.handle)
+
+    @property
+    def vec_dtype(self):
+        import torch
+        return getattr(torch, _VEC_DTYPE[self.prec])
+
+    def empty(self):
+        import torch
+        return torch.empty(self.L, dtype=self.vec_dtype, device="cuda")
+
+    def gather(self, u_global, x=None):
+        x = self.empty() if x is None else x
+        cw_gather(self.handle, u_global, x)
+        return x
+
+    def apply(self, x, y=None, assemble=False):
+        y = self.empty() if y is None else y
+        cw_apply(self.handle, x, y, CW_APPLY_ASSEMBLE if assemble else CW_APPLY_LOCAL)
+        return y
+
+    def dss(self, v, average=False):
+        cw_dss(self.handle, v, CW_DSS_AVERAGE if average else CW_DSS_SUM)
+        return v
+
+    def diagonal(self):
+        import torch
+        d = torch.empty(self.L, dtype=torch.float64, device="cuda")
+        cw_diagonal(self.handle, d)
+        return d
+
+    def load_vector(self, which=0):
+        import torch
+        b = torch.empty(self.L, dtype=torch.float64, device="cuda")
+        cw_load_vector(self.handle, which, b)
+        return b
+
+    def cg_solve(self, b, u=None, rtol=1e-10, maxit=10000, mode=CW_CG_F64, check=True):
+        import torch
+        u = torch.empty(self.L, dtype=torch.float64, device="cuda") if u is None else u
+        rc, st = cw_cg_solve(self.handle, b, u, rtol, maxit, mode, check=check)
+        return u, st, rc
+
+    def close(self):
+        if self.handle:
+            cw_op_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

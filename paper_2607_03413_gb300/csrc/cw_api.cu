@@ -1,0 +1,645 @@
+// cw_api.cu -- C ABI of the cell-wise FEM library: meshes, operators, gather, DSS, diagonal,
+// load vector. The sum-factorised apply kernels live in cw_apply.cuh and are instantiated in
+// the cw_inst_*.cu units; the solver is in cw_cg.cu.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "cw_apply.cuh"
+#include "cw_internal.h"
+
+namespace cw {
+
+// ------------------------------------------------------------------------------- errors ----
+static thread_local std::string g_last_error;
+void set_error(const std::string &msg) { g_last_error = msg; }
+cw_status fail(cw_status st, const std::string &msg)
+{
+    set_error(msg);
+    return st;
+}
+cw_status cuda_fail(cudaError_t e, const char *where)
+{
+    set_error(std::string(where) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? CW_ERR_OOM : CW_ERR_CUDA;
+}
+
+size_t vec_elem_size(int prec)
+{
+    switch (prec) {
+    case CW_PREC_F64:
+    case CW_PREC_F64_NATIVE: return 8;
+    case CW_PREC_F32:
+    case CW_PREC_F32_BF16G: return 4;
+    case CW_PREC_BF16: return 2;
+    }
+    return 0;
+}
+static size_t metric_elem_size(int prec)
+{
+    switch (prec) {
+    case CW_PREC_F64:
+    case CW_PREC_F64_NATIVE: return 8;
+    case CW_PREC_F32: return 4;
+    case CW_PREC_F32_BF16G:
+    case CW_PREC_BF16: return 2;
+    }
+    return 0;
+}
+bool metric_is_f64(int prec) { return prec == CW_PREC_F64 || prec == CW_PREC_F64_NATIVE; }
+
+// --------------------------------------------------------------------- device helpers ----
+struct Rule1D {
+    double xq[kMaxN], wq[kMaxN];
+    double B[kMaxN][kMaxN], Bd[kMaxN][kMaxN];
+};
+
+static Rule1D make_rule(const Tables1D &t)
+{
+    Rule1D r;
+    std::memset(&r, 0, sizeof r);
+    for (int q = 0; q < t.n; ++q) {
+        r.xq[q] = t.xq[q];
+        r.wq[q] = t.wq[q];
+        for (int m = 0; m < t.n; ++m) {
+            r.B[q][m] = t.B[q][m];
+            r.Bd[q][m] = t.Bd[q][m];
+        }
+    }
+    return r;
+}
+
+// trilinear map of cell e at reference point xi: Jacobian J[r][s] = d x_r / d xi_s and the point
+__device__ void cell_jacobian(const double *__restrict__ V, int nx, int ny, int64_t e, double xi0, double xi1,
+                              double xi2, double J[3][3], double X[3])
+{
+    const int64_t cx = e % nx, cy = (e / nx) % ny, cz = e / ((int64_t)nx * ny);
+    for (int a = 0; a < 3; ++a) {
+        X[a] = 0.0;
+        J[a][0] = J[a][1] = J[a][2] = 0.0;
+    }
+    const double xi[3] = {xi0, xi1, xi2};
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const int b0 = v & 1, b1 = (v >> 1) & 1, b2 = (v >> 2) & 1;
+        const int64_t vid = ((cz + b2) * (ny + 1) + (cy + b1)) * (int64_t)(nx + 1) + (cx + b0);
+        const double f0 = b0 ? xi[0] : 1.0 - xi[0], f1 = b1 ? xi[1] : 1.0 - xi[1], f2 = b2 ? xi[2] : 1.0 - xi[2];
+        const double d0 = b0 ? 1.0 : -1.0, d1 = b1 ? 1.0 : -1.0, d2 = b2 ? 1.0 : -1.0;
+        const double N0 = f0 * f1 * f2, g0 = d0 * f1 * f2, g1 = f0 * d1 * f2, g2 = f0 * f1 * d2;
+        for (int a = 0; a < 3; ++a) {
+            const double c = V[vid * 3 + a];
+            X[a] += c * N0;
+            J[a][0] += c * g0;
+            J[a][1] += c * g1;
+            J[a][2] += c * g2;
+        }
+    }
+}
+
+// metric of one quadrature point: (xx, yy, zz, xy, xz, yz) of w detJ J^-1 J^-T and w detJ
+__device__ void qp_metric(const double J[3][3], double w, double out[7], double *det_out)
+{
+    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    // inverse: Ji[s][r] with J^-1 = adj(J)/det, adj(J)[s][r] = cofactor(r, s)
+    double Ji[3][3];
+    Ji[0][0] = c00 / det;
+    Ji[1][0] = c01 / det;
+    Ji[2][0] = c02 / det;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    const double s = w * det;
+    // G = s * Ji Ji^T (Ji = J^-1, rows indexed by reference direction)
+    auto g = [&](int a, int b) { return s * (Ji[a][0] * Ji[b][0] + Ji[a][1] * Ji[b][1] + Ji[a][2] * Ji[b][2]); };
+    out[0] = g(0, 0);
+    out[1] = g(1, 1);
+    out[2] = g(2, 2);
+    out[3] = g(0, 1);
+    out[4] = g(0, 2);
+    out[5] = g(1, 2);
+    out[6] = s;
+    *det_out = det;
+}
+
+template <class GS>
+__device__ __forceinline__ void store_g(GS *p, double v);
+template <>
+__device__ __forceinline__ void store_g<double>(double *p, double v) { *p = v; }
+template <>
+__device__ __forceinline__ void store_g<float>(float *p, double v) { *p = static_cast<float>(v); }
+template <>
+__device__ __forceinline__ void store_g<__nv_bfloat16>(__nv_bfloat16 *p, double v) { *p = __double2bfloat16(v); }
+
+// one thread per (cell, quadrature point); comps selected by kind
+template <class GS>
+__global__ void metric_kernel(const double *__restrict__ V, int nx, int ny, int64_t E, int n, int kind, Rule1D rule,
+                              GS *__restrict__ geo, int *__restrict__ bad)
+{
+    const int n3 = n * n * n, nc = metric_ncomp(kind);
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= E * n3) return;
+    const int64_t e = t / n3;
+    const int q = (int)(t - e * n3), a = q % n, b = (q / n) % n, c = q / (n * n);
+    double J[3][3], X[3], m[7], det;
+    cell_jacobian(V, nx, ny, e, rule.xq[a], rule.xq[b], rule.xq[c], J, X);
+    qp_metric(J, rule.wq[a] * rule.wq[b] * rule.wq[c], m, &det);
+    if (!(det > 0.0)) atomicOr(bad, 1);
+    GS *g = geo + e * (int64_t)nc * n3 + q;
+    if (kind & 1)
+        for (int k = 0; k < 6; ++k) store_g(g + k * n3, m[k]);
+    if (kind & 2) store_g(g + (nc - 1) * n3, m[6]);
+}
+
+// Cartesian per-cell scalars (a_x, a_y, a_z, a_m), masked by the operator kind
+__global__ void affine_kernel(const double *__restrict__ V, int nx, int ny, int64_t E, int kind, double *__restrict__ geo)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    const int64_t cx = e % nx, cy = (e / nx) % ny, cz = e / ((int64_t)nx * ny);
+    const int64_t v0 = (cz * (ny + 1) + cy) * (int64_t)(nx + 1) + cx;
+    const double hx = V[(v0 + 1) * 3 + 0] - V[v0 * 3 + 0];
+    const double hy = V[(v0 + (nx + 1)) * 3 + 1] - V[v0 * 3 + 1];
+    const double hz = V[(v0 + (int64_t)(nx + 1) * (ny + 1)) * 3 + 2] - V[v0 * 3 + 2];
+    const bool k = kind & 1, m = kind & 2;
+    geo[e * 4 + 0] = k ? hy * hz / hx : 0.0;
+    geo[e * 4 + 1] = k ? hx * hz / hy : 0.0;
+    geo[e * 4 + 2] = k ? hx * hy / hz : 0.0;
+    geo[e * 4 + 3] = m ? hx * hy * hz : 0.0;
+}
+
+template <class VS>
+__device__ __forceinline__ void store_v(VS *p, double v);
+template <>
+__device__ __forceinline__ void store_v<double>(double *p, double v) { *p = v; }
+template <>
+__device__ __forceinline__ void store_v<float>(float *p, double v) { *p = static_cast<float>(v); }
+template <>
+__device__ __forceinline__ void store_v<__nv_bfloat16>(__nv_bfloat16 *p, double v) { *p = __double2bfloat16(v); }
+
+template <class VS>
+__global__ void gather_kernel(const double *__restrict__ ug, VS *__restrict__ x, int nx, int ny, int p, int64_t L)
+{
+    const int n = p + 1, n3 = n * n * n;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L) return;
+    const int64_t e = t / n3;
+    const int loc = (int)(t - e * n3), i = loc % n, j = (loc / n) % n, k = loc / (n * n);
+    const int64_t cx = e % nx, cy = (e / nx) % ny, cz = e / ((int64_t)nx * ny);
+    const int64_t gx = (int64_t)nx * p + 1, gy = (int64_t)ny * p + 1;
+    store_v(x + t, ug[(cx * p + i) + gx * ((cy * p + j) + gy * (cz * p + k))]);
+}
+
+// ------------------------------------------------------------------------------- DSS ----
+// One pass of Algorithm struct_dss along axis `ax`: for every interior interface normal to ax
+// between cells K_L and K_R = K_L + stride, s = v[K_L, face = p] + v[K_R, face = 0] is written to
+// both copies. One thread per (interface, face node); no atomics; exchange partners at static
+// offsets.
+template <class VS>
+struct AddOp {
+    static __device__ __forceinline__ VS add(VS a, VS b) { return a + b; }
+};
+template <>
+struct AddOp<__nv_bfloat16> {
+    static __device__ __forceinline__ __nv_bfloat16 add(__nv_bfloat16 a, __nv_bfloat16 b)
+    {
+        return __float2bfloat16_rn(__bfloat162float(a) + __bfloat162float(b));
+    }
+};
+
+template <class VS>
+__global__ void dss_axis_kernel(VS *__restrict__ v, int nx, int ny, int nz, int p, int ax)
+{
+    const int n = p + 1, n2 = n * n, n3 = n2 * n;
+    const int dims[3] = {nx, ny, nz};
+    const int64_t nitf = (int64_t)(dims[ax] - 1) * dims[(ax + 1) % 3] * dims[(ax + 2) % 3];
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nitf * n2) return;
+    const int64_t itf = t / n2;
+    const int f = (int)(t - itf * n2), fa = f % n, fb = f / n;
+    // interface -> left cell coordinates, x fastest; the axis coordinate runs over dims[ax]-1
+    int64_t c[3];
+    int64_t rem = itf;
+    for (int a = 0; a < 3; ++a) {
+        const int64_t ext = (a == ax) ? dims[a] - 1 : dims[a];
+        c[a] = rem % ext;
+        rem /= ext;
+    }
+    const int64_t KL = c[0] + (int64_t)nx * (c[1] + (int64_t)ny * c[2]);
+    const int64_t stride = (ax == 0) ? 1 : (ax == 1 ? nx : (int64_t)nx * ny);
+    const int64_t KR = KL + stride;
+    // face node (fa, fb) in the two in-face directions (lower axis first)
+    int il, ir;
+    if (ax == 0) {
+        il = p + n * fa + n2 * fb;
+        ir = n * fa + n2 * fb;
+    } else if (ax == 1) {
+        il = fa + n * p + n2 * fb;
+        ir = fa + n2 * fb;
+    } else {
+        il = fa + n * fb + n2 * p;
+        ir = fa + n * fb;
+    }
+    VS *pl = v + KL * n3 + il, *pr = v + KR * n3 + ir;
+    const VS s = AddOp<VS>::add(*pl, *pr);
+    *pl = s;
+    *pr = s;
+}
+
+template <class VS>
+struct MulOp {
+    static __device__ __forceinline__ VS mul(VS a, double s) { return static_cast<VS>(a * s); }
+};
+template <>
+struct MulOp<__nv_bfloat16> {
+    static __device__ __forceinline__ __nv_bfloat16 mul(__nv_bfloat16 a, double s)
+    {
+        return __float2bfloat16_rn(__bfloat162float(a) * static_cast<float>(s));
+    }
+};
+
+// valence of local node (i,j,k) of cell (cx,cy,cz): product over axes of 2 on interior faces
+__device__ __forceinline__ int node_valence(int64_t cx, int64_t cy, int64_t cz, int i, int j, int k, int p, int nx,
+                                            int ny, int nz)
+{
+    int v = 1;
+    if ((i == 0 && cx > 0) || (i == p && cx < nx - 1)) v *= 2;
+    if ((j == 0 && cy > 0) || (j == p && cy < ny - 1)) v *= 2;
+    if ((k == 0 && cz > 0) || (k == p && cz < nz - 1)) v *= 2;
+    return v;
+}
+
+template <class VS>
+__global__ void scale_by_valence_kernel(VS *__restrict__ v, int nx, int ny, int nz, int p, int64_t L)
+{
+    const int n = p + 1, n3 = n * n * n;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L) return;
+    const int64_t e = t / n3;
+    const int loc = (int)(t - e * n3), i = loc % n, j = (loc / n) % n, k = loc / (n * n);
+    const int64_t cx = e % nx, cy = (e / nx) % ny, cz = e / ((int64_t)nx * ny);
+    const int val = node_valence(cx, cy, cz, i, j, k, p, nx, ny, nz);
+    if (val > 1) v[t] = MulOp<VS>::mul(v[t], 1.0 / val);
+}
+
+template <class VS>
+static cudaError_t dss_typed(const Op &op, VS *v, int flags, cudaStream_t s)
+{
+    const Mesh &m = *op.mesh;
+    const int dims[3] = {m.nx, m.ny, m.nz};
+    const int n2 = op.n * op.n;
+    for (int ax = 0; ax < 3; ++ax) {
+        if (dims[ax] < 2) continue;
+        const int64_t nthr = (int64_t)(dims[ax] - 1) * dims[(ax + 1) % 3] * dims[(ax + 2) % 3] * n2;
+        const int bs = 256;
+        dss_axis_kernel<VS><<<(unsigned)((nthr + bs - 1) / bs), bs, 0, s>>>(v, m.nx, m.ny, m.nz, op.p, ax);
+    }
+    if (flags == CW_DSS_AVERAGE) {
+        const int bs = 256;
+        scale_by_valence_kernel<VS><<<(unsigned)((op.L + bs - 1) / bs), bs, 0, s>>>(v, m.nx, m.ny, m.nz, op.p, op.L);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t dss_launch(const Op &op, void *v, int flags, cudaStream_t s)
+{
+    switch (vec_elem_size(op.prec)) {
+    case 8: return dss_typed(op, static_cast<double *>(v), flags, s);
+    case 4: return dss_typed(op, static_cast<float *>(v), flags, s);
+    default: return dss_typed(op, static_cast<__nv_bfloat16 *>(v), flags, s);
+    }
+}
+
+cudaError_t apply_local(const Op &op, const void *x, void *y, cudaStream_t s)
+{
+    switch (op.prec) {
+    case CW_PREC_F64: return apply_launch_df(op, x, y, s);
+    case CW_PREC_F64_NATIVE: return apply_launch_f64n(op, x, y, s);
+    default: return apply_launch_f32(op, x, y, s);
+    }
+}
+
+// ----------------------------------------------------------- diagonal and load vector ----
+// One CTA per cell (n^3 threads): the metric of all quadrature points is computed from the
+// vertices in FP64 into shared memory, then thread i forms
+//   diag_i = sum_q (grad phi_i)^T G_q (grad phi_i) + c_q phi_i^2
+// with grad phi_i(q) = (Bd[a][i1] B[b][i2] B[c][i3], B Bd B, B B Bd).
+__global__ void diag_kernel(const double *__restrict__ V, int nx, int ny, int n, int kind, Rule1D rule,
+                            double *__restrict__ d)
+{
+    extern __shared__ double sm[];  // [7][n^3]
+    const int n3 = n * n * n;
+    const int64_t e = blockIdx.x;
+    for (int q = threadIdx.x; q < n3; q += blockDim.x) {
+        const int a = q % n, b = (q / n) % n, c = q / (n * n);
+        double J[3][3], X[3], m[7], det;
+        cell_jacobian(V, nx, ny, e, rule.xq[a], rule.xq[b], rule.xq[c], J, X);
+        qp_metric(J, rule.wq[a] * rule.wq[b] * rule.wq[c], m, &det);
+        for (int k = 0; k < 7; ++k) sm[k * n3 + q] = m[k];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n3; i += blockDim.x) {
+        const int i1 = i % n, i2 = (i / n) % n, i3 = i / (n * n);
+        double s = 0.0;
+        for (int q = 0; q < n3; ++q) {
+            const int a = q % n, b = (q / n) % n, c = q / (n * n);
+            const double B1 = rule.B[a][i1], B2 = rule.B[b][i2], B3 = rule.B[c][i3];
+            if (kind & 1) {
+                const double g0 = rule.Bd[a][i1] * B2 * B3, g1 = B1 * rule.Bd[b][i2] * B3, g2 = B1 * B2 * rule.Bd[c][i3];
+                s += sm[0 * n3 + q] * g0 * g0 + sm[1 * n3 + q] * g1 * g1 + sm[2 * n3 + q] * g2 * g2 +
+                     2.0 * (sm[3 * n3 + q] * g0 * g1 + sm[4 * n3 + q] * g0 * g2 + sm[5 * n3 + q] * g1 * g2);
+            }
+            if (kind & 2) {
+                const double ph = B1 * B2 * B3;
+                s += sm[6 * n3 + q] * ph * ph;
+            }
+        }
+        d[e * n3 + i] = s;
+    }
+}
+
+__device__ __forceinline__ void exact_rhs(int which, const double X[3], double *f)
+{
+    if (which == 0) {
+        const double pi = 3.141592653589793238462643383279502884;
+        *f = 3.0 * pi * pi * sin(pi * X[0]) * sin(pi * X[1]) * sin(pi * X[2]);
+    } else {
+        const double bx = X[0] * (1 - X[0]), by = X[1] * (1 - X[1]), bz = X[2] * (1 - X[2]);
+        *f = 2.0 * (by * bz + bx * bz + bx * by);
+    }
+}
+
+__global__ void load_kernel(const double *__restrict__ V, int nx, int ny, int n, int which, Rule1D rule,
+                            double *__restrict__ b)
+{
+    extern __shared__ double sm[];  // [n^3] : w detJ f at the quadrature points
+    const int n3 = n * n * n;
+    const int64_t e = blockIdx.x;
+    for (int q = threadIdx.x; q < n3; q += blockDim.x) {
+        const int a = q % n, bb = (q / n) % n, c = q / (n * n);
+        double J[3][3], X[3], m[7], det, f;
+        cell_jacobian(V, nx, ny, e, rule.xq[a], rule.xq[bb], rule.xq[c], J, X);
+        qp_metric(J, rule.wq[a] * rule.wq[bb] * rule.wq[c], m, &det);
+        exact_rhs(which, X, &f);
+        sm[q] = m[6] * f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n3; i += blockDim.x) {
+        const int i1 = i % n, i2 = (i / n) % n, i3 = i / (n * n);
+        double s = 0.0;
+        for (int q = 0; q < n3; ++q) {
+            const int a = q % n, bb = (q / n) % n, c = q / (n * n);
+            s += sm[q] * rule.B[a][i1] * rule.B[bb][i2] * rule.B[c][i3];
+        }
+        b[e * n3 + i] = s;
+    }
+}
+
+}  // namespace cw
+
+using namespace cw;
+
+// =================================================================================== C ABI ====
+extern "C" {
+
+const char *cw_status_string(cw_status s)
+{
+    switch (s) {
+    case CW_OK: return "CW_OK";
+    case CW_ERR_ARG: return "CW_ERR_ARG";
+    case CW_ERR_OOM: return "CW_ERR_OOM";
+    case CW_ERR_CUDA: return "CW_ERR_CUDA";
+    case CW_ERR_NOT_CONVERGED: return "CW_ERR_NOT_CONVERGED";
+    case CW_ERR_BREAKDOWN: return "CW_ERR_BREAKDOWN";
+    case CW_ERR_TIMEOUT: return "CW_ERR_TIMEOUT";
+    case CW_ERR_UNSUPPORTED: return "CW_ERR_UNSUPPORTED";
+    }
+    return "CW_ERR_UNKNOWN";
+}
+
+const char *cw_last_error(void) { return g_last_error.c_str(); }
+
+cw_status cw_mesh_create(int nx, int ny, int nz, const double *verts_host, cw_mesh *out)
+{
+    if (!out) return fail(CW_ERR_ARG, "cw_mesh_create: out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || !verts_host) return fail(CW_ERR_ARG, "cw_mesh_create: bad sizes or NULL vertices");
+    const int64_t nv = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+    if ((int64_t)nx * ny * nz > (int64_t)1 << 31) return fail(CW_ERR_ARG, "cw_mesh_create: more than 2^31 cells");
+    Mesh *m = new Mesh;
+    m->nx = nx;
+    m->ny = ny;
+    m->nz = nz;
+    m->h_verts.assign(verts_host, verts_host + nv * 3);
+    // Cartesian test: x depends on vx only, y on vy only, z on vz only
+    bool cart = true;
+    for (int64_t vz = 0; vz <= nz && cart; ++vz)
+        for (int64_t vy = 0; vy <= ny && cart; ++vy)
+            for (int64_t vx = 0; vx <= nx && cart; ++vx) {
+                const double *c = &m->h_verts[((vz * (ny + 1) + vy) * (nx + 1) + vx) * 3];
+                cart = c[0] == m->h_verts[vx * 3 + 0] && c[1] == m->h_verts[(vy * (nx + 1)) * 3 + 1] &&
+                       c[2] == m->h_verts[(vz * (ny + 1) * (nx + 1)) * 3 + 2];
+            }
+    m->cartesian = cart;
+    cudaError_t e = cudaMalloc(&m->d_verts, nv * 3 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_verts, verts_host, nv * 3 * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(m->d_verts);
+        delete m;
+        return cuda_fail(e, "cw_mesh_create");
+    }
+    *out = reinterpret_cast<cw_mesh>(m);
+    return CW_OK;
+}
+
+cw_status cw_mesh_destroy(cw_mesh mh)
+{
+    Mesh *m = reinterpret_cast<Mesh *>(mh);
+    if (!m) return fail(CW_ERR_ARG, "cw_mesh_destroy: NULL");
+    cudaFree(m->d_verts);
+    delete m;
+    return CW_OK;
+}
+
+cw_status cw_op_create(cw_mesh mh, int degree, int kind, int geom, int prec, int bc, cw_op *out)
+{
+    if (!out) return fail(CW_ERR_ARG, "cw_op_create: out is NULL");
+    *out = nullptr;
+    Mesh *m = reinterpret_cast<Mesh *>(mh);
+    if (!m) return fail(CW_ERR_ARG, "cw_op_create: NULL mesh");
+    if (degree < 1 || degree > kMaxDegree) return fail(CW_ERR_ARG, "cw_op_create: degree must be in 1..7");
+    if (kind < 1 || kind > 3) return fail(CW_ERR_ARG, "cw_op_create: bad kind");
+    if (geom != CW_GEOM_AFFINE && geom != CW_GEOM_METRIC) return fail(CW_ERR_ARG, "cw_op_create: bad geometry mode");
+    if (prec < CW_PREC_F64 || prec > CW_PREC_BF16) return fail(CW_ERR_ARG, "cw_op_create: bad precision");
+    if (bc != CW_BC_NONE && bc != CW_BC_DIRICHLET0) return fail(CW_ERR_ARG, "cw_op_create: bad bc");
+    if (geom == CW_GEOM_AFFINE && !m->cartesian)
+        return fail(CW_ERR_ARG, "cw_op_create: CW_GEOM_AFFINE needs a Cartesian (axis-aligned) mesh");
+    Op *op = new Op;
+    op->mesh = m;
+    op->p = degree;
+    op->n = degree + 1;
+    op->kind = kind;
+    op->geom = geom;
+    op->prec = prec;
+    op->bc = bc;
+    op->E = m->ncells();
+    const int n3 = op->n * op->n * op->n;
+    op->L = op->E * n3;
+    op->NG = ((int64_t)m->nx * degree + 1) * ((int64_t)m->ny * degree + 1) * ((int64_t)m->nz * degree + 1);
+    build_tables(degree, op->tab);
+    const Rule1D rule = make_rule(op->tab);
+    cudaError_t e;
+    int *d_bad = nullptr;
+    if (geom == CW_GEOM_METRIC) {
+        const int nc = metric_ncomp(kind);
+        op->geo_bytes = op->E * nc * n3 * (int64_t)metric_elem_size(prec);
+        e = cudaMalloc(&op->d_geo, op->geo_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(d_bad, 0, sizeof(int));
+        if (e == cudaSuccess) {
+            const int64_t nthr = op->E * n3;
+            const unsigned blocks = (unsigned)((nthr + 255) / 256);
+            if (metric_is_f64(prec))
+                metric_kernel<double><<<blocks, 256>>>(m->d_verts, m->nx, m->ny, op->E, op->n, kind, rule,
+                                                       static_cast<double *>(op->d_geo), d_bad);
+            else if (prec == CW_PREC_F32)
+                metric_kernel<float><<<blocks, 256>>>(m->d_verts, m->nx, m->ny, op->E, op->n, kind, rule,
+                                                      static_cast<float *>(op->d_geo), d_bad);
+            else
+                metric_kernel<__nv_bfloat16><<<blocks, 256>>>(m->d_verts, m->nx, m->ny, op->E, op->n, kind, rule,
+                                                              static_cast<__nv_bfloat16 *>(op->d_geo), d_bad);
+            e = cudaGetLastError();
+        }
+        int bad = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
+        cudaFree(d_bad);
+        if (e == cudaSuccess && bad) {
+            cudaFree(op->d_geo);
+            delete op;
+            return fail(CW_ERR_ARG, "cw_op_create: non-positive Jacobian determinant at a quadrature point");
+        }
+    } else {
+        op->geo_bytes = op->E * 4 * (int64_t)sizeof(double);
+        e = cudaMalloc(&op->d_geo, op->geo_bytes);
+        if (e == cudaSuccess) {
+            affine_kernel<<<(unsigned)((op->E + 255) / 256), 256>>>(m->d_verts, m->nx, m->ny, op->E, kind,
+                                                                     static_cast<double *>(op->d_geo));
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    if (e != cudaSuccess) {
+        cudaFree(op->d_geo);
+        delete op;
+        return cuda_fail(e, "cw_op_create");
+    }
+    op->owned_bytes = op->geo_bytes;
+    *out = reinterpret_cast<cw_op>(op);
+    return CW_OK;
+}
+
+cw_status cw_op_destroy(cw_op oh)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    if (!op) return fail(CW_ERR_ARG, "cw_op_destroy: NULL");
+    cg_release(op);
+    if (op->inner) cw_op_destroy(reinterpret_cast<cw_op>(op->inner));
+    cudaFree(op->d_geo);
+    cudaFree(op->d_dinv);
+    delete op;
+    return CW_OK;
+}
+
+int64_t cw_op_cellwise_len(cw_op oh)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    return op ? op->L : -1;
+}
+int64_t cw_op_global_len(cw_op oh)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    return op ? op->NG : -1;
+}
+int64_t cw_op_device_bytes(cw_op oh)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    if (!op) return -1;
+    return op->owned_bytes + (op->inner ? op->inner->owned_bytes : 0);
+}
+
+cw_status cw_gather(cw_op oh, const double *ug, void *x, void *stream)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    if (!op || !ug || !x) return fail(CW_ERR_ARG, "cw_gather: NULL argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const unsigned blocks = (unsigned)((op->L + 255) / 256);
+    const Mesh &m = *op->mesh;
+    switch (vec_elem_size(op->prec)) {
+    case 8: gather_kernel<double><<<blocks, 256, 0, s>>>(ug, static_cast<double *>(x), m.nx, m.ny, op->p, op->L); break;
+    case 4: gather_kernel<float><<<blocks, 256, 0, s>>>(ug, static_cast<float *>(x), m.nx, m.ny, op->p, op->L); break;
+    default:
+        gather_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(ug, static_cast<__nv_bfloat16 *>(x), m.nx, m.ny, op->p, op->L);
+    }
+    CW_CUDA_TRY(cudaGetLastError());
+    return CW_OK;
+}
+
+cw_status cw_apply(cw_op oh, const void *x, void *y, int flags, void *stream)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    if (!op || !x || !y) return fail(CW_ERR_ARG, "cw_apply: NULL argument");
+    if (flags != CW_APPLY_LOCAL && flags != CW_APPLY_ASSEMBLE) return fail(CW_ERR_ARG, "cw_apply: bad flags");
+    if (x == y) return fail(CW_ERR_ARG, "cw_apply: x and y must not alias");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CW_CUDA_TRY(apply_local(*op, x, y, s));
+    if (flags == CW_APPLY_ASSEMBLE) CW_CUDA_TRY(dss_launch(*op, y, CW_DSS_SUM, s));
+    return CW_OK;
+}
+
+cw_status cw_dss(cw_op oh, void *v, int flags, void *stream)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    if (!op || !v) return fail(CW_ERR_ARG, "cw_dss: NULL argument");
+    if (flags != CW_DSS_SUM && flags != CW_DSS_AVERAGE) return fail(CW_ERR_ARG, "cw_dss: bad flags");
+    CW_CUDA_TRY(dss_launch(*op, v, flags, static_cast<cudaStream_t>(stream)));
+    return CW_OK;
+}
+
+cw_status cw_diagonal(cw_op oh, double *d, void *stream)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    if (!op || !d) return fail(CW_ERR_ARG, "cw_diagonal: NULL argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n3 = op->n * op->n * op->n;
+    const Rule1D rule = make_rule(op->tab);
+    diag_kernel<<<(unsigned)op->E, n3 < 128 ? 128 : (n3 > 512 ? 512 : n3), 7 * n3 * sizeof(double), s>>>(
+        op->mesh->d_verts, op->mesh->nx, op->mesh->ny, op->n, op->kind, rule, d);
+    CW_CUDA_TRY(cudaGetLastError());
+    CW_CUDA_TRY(dss_typed(*op, d, CW_DSS_SUM, s));
+    return CW_OK;
+}
+
+cw_status cw_load_vector(cw_op oh, int which, double *b, void *stream)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    if (!op || !b) return fail(CW_ERR_ARG, "cw_load_vector: NULL argument");
+    if (which != 0 && which != 1) return fail(CW_ERR_ARG, "cw_load_vector: which must be 0 or 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n3 = op->n * op->n * op->n;
+    const Rule1D rule = make_rule(op->tab);
+    load_kernel<<<(unsigned)op->E, n3 < 128 ? 128 : (n3 > 512 ? 512 : n3), n3 * sizeof(double), s>>>(
+        op->mesh->d_verts, op->mesh->nx, op->mesh->ny, op->n, which, rule, b);
+    CW_CUDA_TRY(cudaGetLastError());
+    return CW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,283 @@
+// cw_apply.cuh -- sum-factorised cell-local operator kernels (the hot path).
+//
+// One CTA owns a tile of CPB consecutive cells; a cell is worked by N*N threads. A thread plays
+// three roles in turn: owner of an x-line (j,k), of a y-line (i,k) and of a z-pencil (i,j), with
+// (r % N, r / N) as its pair of indices, r in [0, N*N). 1D contractions along the owned line run
+// in registers; switching axis goes through shared memory (padded row pitch PI = N|1 keeps line
+// accesses free of bank conflicts). The 1D tables are kernel parameters (constant bank) so every
+// contraction coefficient is an immediate operand.
+//
+// Curved cells (Sec. 6, "the general cell-wise Laplacian: evaluate gradients, apply the physics,
+// integrate gradients"), per cell with u the nodal values:
+//   u_q = (B x B x B) u                 interpolation to the n^3 Gauss points
+//   g   = (D u_q along x, y, z)         reference gradient by Gauss-point collocation
+//   h   = G_q g,  m_q = c_q u_q         metric G_q = w_q detJ J^-1 J^-T, c_q = w_q detJ
+//   y   = (B^T x B^T x B^T)(D_x^T h_x + D_y^T h_y + D_z^T h_z + m_q)
+// Cartesian cells (Sec. 6, the factored form (D x B x B + B x D x B + B x B x D) det J J^-2 read
+// with D, B the 1D stiffness and mass matrices):
+//   y = a_x (M x M x K) u + a_y (M x K x M) u + a_z (K x M x M) u + a_m (M x M x M) u
+// evaluated as two x-contractions, three y-contractions and two z-contractions.
+#pragma once
+#include "cw_arith.cuh"
+
+namespace cw {
+
+template <int N, class C>
+struct TabMetric {
+    C B[N][N];  // B[q][m] = l_m(xi_q): Gauss-Lobatto basis at the Gauss points
+    C D[N][N];  // D[q][r] = derivative at xi_q of the Lagrange basis on the Gauss points
+};
+
+template <int N, class C>
+struct TabAffine {
+    C M[N][N];  // 1D mass matrix of the Gauss-Lobatto basis on [0,1]
+    C K[N][N];  // 1D stiffness matrix
+};
+
+// small helpers -------------------------------------------------------------------------------
+
+template <class S>
+__device__ __forceinline__ S ldg_nc(const S *p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 ldg_nc<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    return __ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short *>(p)));
+}
+
+// out[a] = sum_b M[a][b] in[b]  (TR=false)   or   out[a] = sum_b M[b][a] in[b]  (TR=true)
+template <int N, bool TR, class Ar>
+__device__ __forceinline__ void contract(const typename Ar::C (&M)[N][N], const typename Ar::T (&in)[N],
+                                         typename Ar::T (&out)[N])
+{
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+        typename Ar::T s = Ar::mul(in[0], TR ? M[0][a] : M[a][0]);
+#pragma unroll
+        for (int b = 1; b < N; ++b) Ar::mad(s, in[b], TR ? M[b][a] : M[a][b]);
+        out[a] = Ar::norm(s);
+    }
+}
+
+// shared-memory line access: element m of the x-line, y-line or z-pencil owned by (ra, rb)
+template <int N>
+struct Lines {
+    static constexpr int PI = N | 1;  // row pitch (odd)
+    static constexpr int CS = PI * N * N;
+    static __device__ __forceinline__ int x(int ra, int rb, int m) { return m + PI * (ra + N * rb); }
+    static __device__ __forceinline__ int y(int ra, int rb, int m) { return ra + PI * (m + N * rb); }
+    static __device__ __forceinline__ int z(int ra, int rb, int m) { return ra + PI * (rb + N * m); }
+};
+
+#define CW_LDX(s, v) _Pragma("unroll") for (int m_ = 0; m_ < N; ++m_) v[m_] = (s)[L::x(ra, rb, m_)]
+#define CW_LDY(s, v) _Pragma("unroll") for (int m_ = 0; m_ < N; ++m_) v[m_] = (s)[L::y(ra, rb, m_)]
+#define CW_LDZ(s, v) _Pragma("unroll") for (int m_ = 0; m_ < N; ++m_) v[m_] = (s)[L::z(ra, rb, m_)]
+#define CW_STX(s, v) _Pragma("unroll") for (int m_ = 0; m_ < N; ++m_) (s)[L::x(ra, rb, m_)] = v[m_]
+#define CW_STY(s, v) _Pragma("unroll") for (int m_ = 0; m_ < N; ++m_) (s)[L::y(ra, rb, m_)] = v[m_]
+#define CW_STZ(s, v) _Pragma("unroll") for (int m_ = 0; m_ < N; ++m_) (s)[L::z(ra, rb, m_)] = v[m_]
+
+// number of stored metric components per quadrature point for an operator kind
+__host__ __device__ constexpr int metric_ncomp(int kind) { return kind == 1 ? 6 : (kind == 2 ? 1 : 7); }
+
+// ------------------------------------------------------------------------ curved kernel ----
+// geo layout: [cell][comp][qp] with qp = a + N(b + N c); comps (xx, yy, zz, xy, xz, yz, mass)
+// for KIND 3, the first six for KIND 1, the mass coefficient alone for KIND 2.
+template <int N, int CPB, class Ar, class VS, class GS, int KIND>
+__global__ void __launch_bounds__(N *N *CPB) apply_metric_kernel(const VS *__restrict__ x, VS *__restrict__ y,
+                                                                  const GS *__restrict__ geo, int64_t ncells,
+                                                                  TabMetric<N, typename Ar::C> tab)
+{
+    using T = typename Ar::T;
+    using L = Lines<N>;
+    constexpr int N2 = N * N, N3 = N2 * N, CS = L::CS, NC = metric_ncomp(KIND);
+    constexpr bool HAS_K = (KIND & 1) != 0, HAS_M = (KIND & 2) != 0;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *S0 = reinterpret_cast<T *>(smem_raw);
+    const int t = threadIdx.x, c = t / N2, r = t - c * N2, ra = r % N, rb = r / N;
+    const int64_t cell = static_cast<int64_t>(blockIdx.x) * CPB + c;
+    const bool act = cell < ncells;
+    T *s0 = S0 + c * CS;
+    T *s1 = S0 + (CPB + c) * CS;
+    T *s2 = S0 + (2 * CPB + c) * CS;
+
+    T v[N], w[N];
+    // (1) x-line (j,k) = (ra, rb): N contiguous values of the cell, contracted with B along x
+    {
+        const VS *xc = x + (act ? cell : 0) * N3 + N * r;
+#pragma unroll
+        for (int m = 0; m < N; ++m) v[m] = act ? Ar::from(ldg_nc(xc + m)) : Ar::zero();
+        contract<N, false, Ar>(tab.B, v, w);
+        CW_STX(s0, w);
+    }
+    __syncthreads();
+    // (2) y-line (i,k): contract with B along y, in place
+    CW_LDY(s0, v);
+    contract<N, false, Ar>(tab.B, v, w);
+    CW_STY(s0, w);
+    __syncthreads();
+    // (3) z-pencil (i,j): contract with B along z -> u at the Gauss points (registers)
+    T u[N], acc[N];
+    CW_LDZ(s0, v);
+    contract<N, false, Ar>(tab.B, v, u);
+    T gx[N], gy[N], gz[N];
+    if constexpr (HAS_K) {
+        contract<N, false, Ar>(tab.D, u, gz);
+        CW_STZ(s0, u);
+        __syncthreads();
+        // x- and y-derivatives by collocation, as line owners
+        CW_LDX(s0, v);
+        contract<N, false, Ar>(tab.D, v, w);
+        CW_STX(s1, w);
+        CW_LDY(s0, v);
+        contract<N, false, Ar>(tab.D, v, w);
+        CW_STY(s2, w);
+        __syncthreads();
+        CW_LDZ(s1, gx);
+        CW_LDZ(s2, gy);
+    }
+    // (4) quadrature-point physics on the owned pencil, qp = (ra, rb, k)
+    {
+        const GS *gc = geo + (act ? cell : 0) * (NC * N3) + r;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const GS *g = gc + N2 * k;
+            if constexpr (HAS_K) {
+                const T gxx = Ar::from(ldg_nc(g + 0 * N3)), gyy = Ar::from(ldg_nc(g + 1 * N3));
+                const T gzz = Ar::from(ldg_nc(g + 2 * N3)), gxy = Ar::from(ldg_nc(g + 3 * N3));
+                const T gxz = Ar::from(ldg_nc(g + 4 * N3)), gyz = Ar::from(ldg_nc(g + 5 * N3));
+                T hx = Ar::mul(gx[k], gxx), hy = Ar::mul(gx[k], gxy), hz = Ar::mul(gx[k], gxz);
+                Ar::mad(hx, gy[k], gxy);
+                Ar::mad(hy, gy[k], gyy);
+                Ar::mad(hz, gy[k], gyz);
+                Ar::mad(hx, gz[k], gxz);
+                Ar::mad(hy, gz[k], gyz);
+                Ar::mad(hz, gz[k], gzz);
+                gx[k] = Ar::norm(hx);
+                gy[k] = Ar::norm(hy);
+                gz[k] = Ar::norm(hz);
+            }
+            if constexpr (HAS_M) {
+                const T cm = Ar::from(ldg_nc(g + (NC - 1) * N3));
+                acc[k] = Ar::norm(Ar::mul(u[k], cm));
+            }
+        }
+    }
+    if constexpr (HAS_K) {
+        // z-part of the transposed derivative in registers, x/y parts as line owners
+        contract<N, true, Ar>(tab.D, gz, v);
+#pragma unroll
+        for (int k = 0; k < N; ++k) acc[k] = HAS_M ? Ar::add(acc[k], v[k]) : v[k];
+        CW_STZ(s1, gx);  // own pencil only: no other thread reads s1/s2 pencils now
+        CW_STZ(s2, gy);
+        __syncthreads();
+        CW_LDX(s1, v);
+        contract<N, true, Ar>(tab.D, v, w);
+        CW_STX(s1, w);
+        CW_LDY(s2, v);
+        contract<N, true, Ar>(tab.D, v, w);
+        CW_STY(s2, w);
+        __syncthreads();
+        CW_LDZ(s1, v);
+        CW_LDZ(s2, w);
+#pragma unroll
+        for (int k = 0; k < N; ++k) acc[k] = Ar::norm(Ar::add(acc[k], Ar::add(v[k], w[k])));
+    }
+    // (5) integrate back: B^T along z (registers), y and x as line owners
+    contract<N, true, Ar>(tab.B, acc, w);
+    CW_STZ(s0, w);
+    __syncthreads();
+    CW_LDY(s0, v);
+    contract<N, true, Ar>(tab.B, v, w);
+    CW_STY(s0, w);
+    __syncthreads();
+    CW_LDX(s0, v);
+    contract<N, true, Ar>(tab.B, v, w);
+    if (act) {
+        VS *yc = y + cell * N3 + N * r;
+#pragma unroll
+        for (int m = 0; m < N; ++m) Ar::to(yc[m], w[m]);
+    }
+}
+
+// ---------------------------------------------------------------------- Cartesian kernel ----
+// geo layout: [cell][4] doubles (a_x, a_y, a_z, a_m) = (hy hz/hx, hx hz/hy, hx hy/hz, hx hy hz),
+// already multiplied by the kind mask (a_m = 0 for KIND 1, a_x = a_y = a_z = 0 for KIND 2).
+template <int N, int CPB, class Ar, class VS, int KIND>
+__global__ void __launch_bounds__(N *N *CPB) apply_affine_kernel(const VS *__restrict__ x, VS *__restrict__ y,
+                                                                  const double *__restrict__ geo, int64_t ncells,
+                                                                  TabAffine<N, typename Ar::C> tab)
+{
+    using T = typename Ar::T;
+    using L = Lines<N>;
+    constexpr int N2 = N * N, N3 = N2 * N, CS = L::CS;
+    constexpr bool HAS_K = (KIND & 1) != 0, HAS_M = (KIND & 2) != 0;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *S0 = reinterpret_cast<T *>(smem_raw);
+    const int t = threadIdx.x, c = t / N2, r = t - c * N2, ra = r % N, rb = r / N;
+    const int64_t cell = static_cast<int64_t>(blockIdx.x) * CPB + c;
+    const bool act = cell < ncells;
+    T *s0 = S0 + c * CS;
+    T *s1 = S0 + (CPB + c) * CS;
+    T v[N], P[N], Q[N];
+    // x-line: P = M_x u, Q = K_x u
+    {
+        const VS *xc = x + (act ? cell : 0) * N3 + N * r;
+#pragma unroll
+        for (int m = 0; m < N; ++m) v[m] = act ? Ar::from(ldg_nc(xc + m)) : Ar::zero();
+        contract<N, false, Ar>(tab.M, v, P);
+        CW_STX(s0, P);
+        if constexpr (HAS_K) {
+            contract<N, false, Ar>(tab.K, v, Q);
+            CW_STX(s1, Q);
+        }
+    }
+    const double *gc = geo + (act ? cell : 0) * 4;
+    const T ax = Ar::from(__ldg(gc + 0)), ay = Ar::from(__ldg(gc + 1));
+    const T az = Ar::from(__ldg(gc + 2)), am = Ar::from(__ldg(gc + 3));
+    __syncthreads();
+    // y-line: R1 = M_y P, R2 = K_y P, R3 = M_y Q; W = a_x R3 + a_y R2 + a_m R1
+    {
+        T R1[N], W[N];
+        CW_LDY(s0, v);
+        contract<N, false, Ar>(tab.M, v, R1);
+        if constexpr (HAS_K) {
+            T R2[N], R3[N];
+            contract<N, false, Ar>(tab.K, v, R2);
+            CW_LDY(s1, v);
+            contract<N, false, Ar>(tab.M, v, R3);
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+                T s = Ar::mul(R3[m], ax);
+                Ar::mad(s, R2[m], ay);
+                if constexpr (HAS_M) Ar::mad(s, R1[m], am);
+                W[m] = Ar::norm(s);
+                R1[m] = Ar::norm(Ar::mul(R1[m], az));
+            }
+            CW_STY(s1, R1);
+        } else {
+#pragma unroll
+            for (int m = 0; m < N; ++m) W[m] = Ar::norm(Ar::mul(R1[m], am));
+        }
+        CW_STY(s0, W);
+    }
+    __syncthreads();
+    // z-pencil: y = M_z W + K_z (a_z R1)
+    {
+        T out[N];
+        CW_LDZ(s0, v);
+        contract<N, false, Ar>(tab.M, v, out);
+        if constexpr (HAS_K) {
+            T R[N], KR[N];
+            CW_LDZ(s1, R);
+            contract<N, false, Ar>(tab.K, R, KR);
+#pragma unroll
+            for (int m = 0; m < N; ++m) out[m] = Ar::norm(Ar::add(out[m], KR[m]));
+        }
+        if (act) {
+            VS *yc = y + cell * N3 + r;
+#pragma unroll
+            for (int m = 0; m < N; ++m) Ar::to(yc[N2 * m], out[m]);
+        }
+    }
+}
+
+}  // namespace cw

@@ -1,0 +1,168 @@
+// cw_arith.cuh -- arithmetic types for the cell-wise operator kernels.
+//
+// GB300 executes native FP64 FMA at about 1/64 of the FP32 rate (measured 1.0 TFLOP/s FP64 vs
+// 73 TFLOP/s FP32), so the FP64 operator path computes in double-float arithmetic: a value is an
+// unevaluated sum hi + lo of two floats (Dekker 1971; error-free TwoSum of Knuth and the
+// FMA-based TwoProduct, as collected by Muller et al., "Handbook of Floating-Point Arithmetic").
+// Storage stays IEEE FP64; a double is split into (hi, lo) with integer bit operations (the
+// FP64->FP32 conversion instructions run on the slow FP64 pipe) keeping 24 + 23 significant bits,
+// i.e. a relative truncation error below 2^-46.
+#pragma once
+#include <cuda_bf16.h>
+#include <cstdint>
+
+namespace cw {
+
+struct df64 {
+    float hi, lo;
+};
+
+// ---------------------------------------------------------------- conversions ----
+
+// Split a double into hi + lo floats using integer operations only. |x| < 2^-126 maps to 0 and
+// the low part is dropped when it would be subnormal (|x| < 2^-80); both are far below the
+// precision the operator needs relative to the vector norm.
+__device__ __forceinline__ df64 split_f64(double x)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned h32 = static_cast<unsigned>(b >> 32), l32 = static_cast<unsigned>(b);
+    const unsigned sign = h32 & 0x80000000u;
+    const int e = static_cast<int>((h32 >> 20) & 0x7FFu);
+    const int fe = e - 896;  // float biased exponent
+    const unsigned mhi = ((h32 & 0xFFFFFu) << 3) | (l32 >> 29);
+    df64 r;
+    if (fe <= 0) {
+        r.hi = 0.0f;
+        r.lo = 0.0f;
+        return r;
+    }
+    r.hi = __uint_as_float(sign | (static_cast<unsigned>(min(fe, 255)) << 23) | (fe >= 255 ? 0u : mhi));
+    // remainder: the low 29 mantissa bits, worth rem * 2^(e-1075); keep its top 23 bits
+    const unsigned r23 = (l32 & 0x1FFFFFFFu) >> 6;
+    const float f = __fsub_rn(__uint_as_float(0x4B000000u | r23), 8388608.0f);  // exact
+    const int se = e - 942;  // biased exponent of 2^(e-1069)
+    const float scale = __uint_as_float(static_cast<unsigned>(max(se, 1)) << 23);
+    const float lo = __fmul_rn(f, scale);
+    r.lo = (se >= 1) ? __uint_as_float(__float_as_uint(lo) | sign) : 0.0f;
+    return r;
+}
+
+// Exact widening float -> double with integer operations (zero and subnormals map to +-0).
+__device__ __forceinline__ double widen_f32(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned sign = u & 0x80000000u;
+    const unsigned e = (u >> 23) & 0xFFu;
+    const unsigned m = u & 0x7FFFFFu;
+    const unsigned hi = (e == 0u) ? sign : (sign | ((e + 896u) << 20) | (m >> 3));
+    const unsigned lo = (e == 0u) ? 0u : (m << 29);
+    return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(hi) << 32) | lo));
+}
+
+__device__ __forceinline__ double df_to_double(df64 a) { return __dadd_rn(widen_f32(a.hi), widen_f32(a.lo)); }
+
+// ---------------------------------------------------------- double-float ops ----
+
+// s + e = a + b exactly (TwoSum, no ordering requirement)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// renormalise so that |lo| <= ulp(hi)/2 (Fast2Sum; valid because |lo| is small against |hi|)
+__device__ __forceinline__ df64 df_norm(df64 a)
+{
+    df64 r;
+    r.hi = __fadd_rn(a.hi, a.lo);
+    r.lo = __fsub_rn(a.lo, __fsub_rn(r.hi, a.hi));
+    return r;
+}
+
+// product of two double-float numbers (low-order term lo*lo dropped), not normalised
+__device__ __forceinline__ df64 df_mul(df64 a, df64 b)
+{
+    df64 r;
+    r.hi = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -r.hi);  // exact error of the product
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    r.lo = e;
+    return r;
+}
+
+// acc += a * b, lazily normalised (acc.lo collects all low-order terms)
+__device__ __forceinline__ void df_mad(df64 &acc, df64 a, df64 b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    float s, t;
+    two_sum(acc.hi, p, s, t);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, e));
+}
+
+__device__ __forceinline__ df64 df_add(df64 a, df64 b)
+{
+    float s, t;
+    two_sum(a.hi, b.hi, s, t);
+    df64 r;
+    r.hi = s;
+    r.lo = __fadd_rn(t, __fadd_rn(a.lo, b.lo));
+    return r;
+}
+
+// ------------------------------------------------------------ arithmetic traits ----
+// Each trait defines the register type T, the constant type C used for the 1D tables, and
+// mul / mad / add / norm plus conversions from and to each storage type.
+
+struct ArDF {  // double-float arithmetic
+    using T = df64;
+    using C = df64;
+    static __device__ __forceinline__ T zero() { return T{0.0f, 0.0f}; }
+    static __device__ __forceinline__ T mul(T a, C b) { return df_mul(a, b); }
+    static __device__ __forceinline__ void mad(T &acc, T a, C b) { df_mad(acc, a, b); }
+    static __device__ __forceinline__ T add(T a, T b) { return df_add(a, b); }
+    static __device__ __forceinline__ T norm(T a) { return df_norm(a); }
+    static __device__ __forceinline__ T from(double v) { return split_f64(v); }
+    static __device__ __forceinline__ T from(float v) { return T{v, 0.0f}; }
+    static __device__ __forceinline__ void to(double &d, T a) { d = df_to_double(a); }
+    static __device__ __forceinline__ double to_f64(T a) { return df_to_double(a); }
+};
+
+struct ArF64 {  // native FP64
+    using T = double;
+    using C = double;
+    static __device__ __forceinline__ T zero() { return 0.0; }
+    static __device__ __forceinline__ T mul(T a, C b) { return a * b; }
+    static __device__ __forceinline__ void mad(T &acc, T a, C b) { acc = fma(a, b, acc); }
+    static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    static __device__ __forceinline__ T norm(T a) { return a; }
+    static __device__ __forceinline__ T from(double v) { return v; }
+    static __device__ __forceinline__ void to(double &d, T a) { d = a; }
+    static __device__ __forceinline__ double to_f64(T a) { return a; }
+};
+
+struct ArF32 {  // FP32
+    using T = float;
+    using C = float;
+    static __device__ __forceinline__ T zero() { return 0.0f; }
+    static __device__ __forceinline__ T mul(T a, C b) { return a * b; }
+    static __device__ __forceinline__ void mad(T &acc, T a, C b) { acc = fmaf(a, b, acc); }
+    static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    static __device__ __forceinline__ T norm(T a) { return a; }
+    static __device__ __forceinline__ T from(float v) { return v; }
+    static __device__ __forceinline__ T from(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ void to(float &d, T a) { d = a; }
+    static __device__ __forceinline__ void to(__nv_bfloat16 &d, T a) { d = __float2bfloat16_rn(a); }
+    static __device__ __forceinline__ double to_f64(T a) { return static_cast<double>(a); }
+};
+
+// host-side construction of table constants for each trait
+template <class Ar>
+struct ConstMaker;
+
+}  // namespace cw

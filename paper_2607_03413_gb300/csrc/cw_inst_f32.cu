@@ -1,0 +1,14 @@
+// FP32 vectors, FP32 metric, FP32 arithmetic (CW_PREC_F32), plus the FP32-arithmetic dispatch.
+#include "cw_launch.cuh"
+namespace cw {
+cudaError_t apply_launch_f32g16(const Op &op, const void *x, void *y, cudaStream_t s);
+cudaError_t apply_launch_bf16(const Op &op, const void *x, void *y, cudaStream_t s);
+cudaError_t apply_launch_f32(const Op &op, const void *x, void *y, cudaStream_t s)
+{
+    switch (op.prec) {
+    case CW_PREC_F32: return launch_degree<ArF32, float, float>(op, x, y, s);
+    case CW_PREC_F32_BF16G: return apply_launch_f32g16(op, x, y, s);
+    default: return apply_launch_bf16(op, x, y, s);
+    }
+}
+}  // namespace cw

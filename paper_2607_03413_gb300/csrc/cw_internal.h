@@ -1,0 +1,77 @@
+// cw_internal.h -- host-side structures shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cwfem.h"
+
+namespace cw {
+
+constexpr int kMaxDegree = 7;
+constexpr int kMaxN = kMaxDegree + 1;
+
+// 1D tables of one degree, in double (built from long-double rules by cw_tables.cpp)
+struct Tables1D {
+    int p = 0, n = 0;
+    double gll[kMaxN];          // Gauss-Lobatto nodes on [0,1]
+    double xq[kMaxN], wq[kMaxN];  // Gauss points and weights on [0,1]
+    double B[kMaxN][kMaxN];     // B[q][m] = l_m(xq)
+    double Bd[kMaxN][kMaxN];    // Bd[q][m] = l_m'(xq)
+    double D[kMaxN][kMaxN];     // collocation derivative on the Gauss points
+    double M1[kMaxN][kMaxN];    // 1D mass matrix of the GLL basis
+    double K1[kMaxN][kMaxN];    // 1D stiffness matrix of the GLL basis
+};
+void build_tables(int p, Tables1D &t);
+
+struct Mesh {
+    int nx = 0, ny = 0, nz = 0;
+    double *d_verts = nullptr;
+    std::vector<double> h_verts;
+    bool cartesian = false;
+    int64_t ncells() const { return (int64_t)nx * ny * nz; }
+};
+
+struct CgScratch;
+
+struct Op {
+    Mesh *mesh = nullptr;
+    int p = 0, n = 0, kind = 0, geom = 0, prec = 0, bc = 0;
+    int64_t E = 0, L = 0, NG = 0;
+    Tables1D tab;
+    void *d_geo = nullptr;  // metric [E][ncomp][n^3] in the metric type, or affine [E][4] doubles
+    int64_t geo_bytes = 0;
+    double *d_dinv = nullptr;  // cell-wise masked inverse diagonal (solver), lazily
+    CgScratch *cg = nullptr;
+    Op *inner = nullptr;  // reduced-precision twin used by iterative refinement
+    int64_t owned_bytes = 0;
+};
+
+size_t vec_elem_size(int prec);
+bool metric_is_f64(int prec);
+
+// launchers implemented in the instantiation units
+cudaError_t apply_launch_df(const Op &op, const void *x, void *y, cudaStream_t s);
+cudaError_t apply_launch_f64n(const Op &op, const void *x, void *y, cudaStream_t s);
+cudaError_t apply_launch_f32(const Op &op, const void *x, void *y, cudaStream_t s);
+
+// dispatch to the right unit
+cudaError_t apply_local(const Op &op, const void *x, void *y, cudaStream_t s);
+cudaError_t dss_launch(const Op &op, void *v, int flags, cudaStream_t s);
+
+// solver scratch release (cw_cg.cu)
+void cg_release(Op *op);
+
+// error reporting (thread-local message)
+void set_error(const std::string &msg);
+cw_status fail(cw_status st, const std::string &msg);
+cw_status cuda_fail(cudaError_t e, const char *where);
+
+}  // namespace cw
+
+#define CW_CUDA_TRY(expr)                                              \
+    do {                                                               \
+        cudaError_t e_ = (expr);                                       \
+        if (e_ != cudaSuccess) return ::cw::cuda_fail(e_, #expr);      \
+    } while (0)

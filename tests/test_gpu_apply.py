@@ -1,0 +1,133 @@
+"""GPU parity of the sum-factorised apply, gather, DSS, diagonal and load vector against the FP64
+oracle, through the C ABI. FP64 paths: ||y - y_ref||_inf / ||y_ref||_inf <= 1e-12."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import rel_err, to_np
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def cw():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2607_03413_gb300 as cw
+    from paper_2607_03413_gb300 import build
+    build.build()
+    cw.load()
+    return cw
+
+
+def mesh_for(p):
+    # several tiles of every tile size plus a ragged last tile
+    return synth.box_mesh(3, 4, 5, perturb=0.2) if p <= 5 else synth.box_mesh(3, 1, 3, perturb=0.2)
+
+
+def run_apply(cw, mesh, p, kind, geom, prec, xin, assemble=False):
+    import torch
+    M = cw.Mesh.from_synth(mesh)
+    op = cw.Operator(M, p, kind, geom, prec)
+    x = torch.from_numpy(xin).cuda().to(op.vec_dtype)
+    y = op.apply(x, assemble=assemble)
+    torch.cuda.synchronize()
+    return to_np(y)
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["df64", "f64native"])
+@pytest.mark.parametrize("kind", [1, 2, 3], ids=["K", "M", "KM"])
+@pytest.mark.parametrize("p", range(1, 8))
+def test_apply_metric_f64(cw, orc, p, kind, prec):
+    mesh = mesh_for(p)
+    x = orc.gather(mesh, p, synth.global_vector(mesh, p, seed=p))
+    ref = orc.apply_local(mesh, p, kind, x)
+    y = run_apply(cw, mesh, p, kind, cw.CW_GEOM_METRIC, prec, x)
+    assert rel_err(y, ref) <= TOL64
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3], ids=["K", "M", "KM"])
+@pytest.mark.parametrize("p", range(1, 8))
+def test_apply_affine_f64(cw, orc, p, kind):
+    mesh = synth.box_mesh(5, 3, 4) if p <= 5 else synth.box_mesh(3, 2, 2)
+    x = synth.cellwise_random(mesh, p, seed=10 + p)  # the apply is cell-local: any input works
+    ref = orc.apply_local(mesh, p, kind, x)
+    y = run_apply(cw, mesh, p, kind, cw.CW_GEOM_AFFINE, cw.CW_PREC_F64, x)
+    assert rel_err(y, ref) <= TOL64
+
+
+@pytest.mark.parametrize("p", [2, 4, 7])
+def test_apply_assemble_f64(cw, orc, p):
+    mesh = mesh_for(p)
+    x = orc.gather(mesh, p, synth.global_vector(mesh, p, seed=20 + p))
+    ref = orc.dss(mesh, p, orc.apply_local(mesh, p, 3, x))
+    y = run_apply(cw, mesh, p, 3, cw.CW_GEOM_METRIC, cw.CW_PREC_F64, x, assemble=True)
+    assert rel_err(y, ref) <= TOL64
+
+
+@pytest.mark.parametrize("prec,tol", [(2, 2e-6), (3, 1e-2), (4, 3e-2)], ids=["f32", "f32_bf16g", "bf16"])
+@pytest.mark.parametrize("p", [1, 2, 4, 7])
+def test_apply_reduced_precision_error(cw, orc, p, prec, tol):
+    """Reduced precision has no parity bar from the paper; its error against the FP64 oracle is
+    measured and bounded by what the storage precision allows."""
+    mesh = mesh_for(p)
+    x = orc.gather(mesh, p, synth.global_vector(mesh, p, seed=p))
+    ref = orc.apply_local(mesh, p, 1, x)
+    y = run_apply(cw, mesh, p, 1, cw.CW_GEOM_METRIC, prec, x)
+    err = rel_err(y, ref)
+    print(f"p={p} prec={prec} rel err {err:.3e}")
+    assert err <= tol
+
+
+@pytest.mark.parametrize("p", [1, 3, 6])
+def test_gather_exact(cw, orc, p):
+    import torch
+    mesh = synth.box_mesh(4, 3, 2, perturb=0.1)
+    ug = synth.global_vector(mesh, p, seed=3)
+    M = cw.Mesh.from_synth(mesh)
+    op = cw.Operator(M, p, 1, cw.CW_GEOM_METRIC, cw.CW_PREC_F64)
+    x = op.gather(torch.from_numpy(ug).cuda())
+    assert np.array_equal(to_np(x), orc.gather(mesh, p, ug))
+
+
+@pytest.mark.parametrize("average", [False, True])
+@pytest.mark.parametrize("dims", [(4, 3, 5), (1, 3, 2), (2, 1, 1)])
+@pytest.mark.parametrize("p", [1, 2, 5])
+def test_dss(cw, orc, p, dims, average):
+    import torch
+    mesh = synth.box_mesh(*dims)
+    r = synth.cellwise_random(mesh, p, seed=5)
+    ref = orc.dss(mesh, p, r)
+    if average:
+        kappa = orc.dss(mesh, p, np.ones_like(r))
+        ref = ref / kappa
+    M = cw.Mesh.from_synth(mesh)
+    op = cw.Operator(M, p, 1, cw.CW_GEOM_METRIC, cw.CW_PREC_F64)
+    v = torch.from_numpy(r).cuda()
+    op.dss(v, average=average)
+    torch.cuda.synchronize()
+    assert rel_err(to_np(v), ref) <= 1e-15
+
+
+@pytest.mark.parametrize("kind", [1, 3])
+@pytest.mark.parametrize("p", [1, 3, 5])
+def test_diagonal(cw, orc, p, kind):
+    mesh = synth.box_mesh(3, 2, 3, perturb=0.2)
+    M = cw.Mesh.from_synth(mesh)
+    op = cw.Operator(M, p, kind, cw.CW_GEOM_METRIC, cw.CW_PREC_F64)
+    d = to_np(op.diagonal())
+    ref = orc.gather(mesh, p, orc.diagonal(mesh, p, kind))
+    assert rel_err(d, ref) <= TOL64
+
+
+@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("p", [1, 4])
+def test_load_vector(cw, orc, p, which):
+    mesh = synth.box_mesh(3, 3, 2, perturb=0.2)
+    M = cw.Mesh.from_synth(mesh)
+    op = cw.Operator(M, p, 1, cw.CW_GEOM_METRIC, cw.CW_PREC_F64)
+    b = to_np(op.load_vector(which))
+    assert rel_err(b, orc.load_vector(mesh, p, which)) <= TOL64
