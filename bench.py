@@ -1,0 +1,440 @@
+"""Benchmark of the cell-wise matrix-free operator library on GB300.
+
+Default workload (one step): Laplace + mass apply with assembly (y = S A x) of degree 4 on a
+64^3-cell curved unit cube (sinusoidal vertex displacement of amplitude 0.1 h, metric stored as
+7 FP64 values per quadrature point), FP64 storage. The step is the apply kernel followed by the
+three DSS axis passes. Inputs (x 262 MB, metric 1.84 GB, y 262 MB) exceed the 129 MB L2, so no
+flush is needed between steps.
+
+Extra measurements in the same JSON line: the same workload in FP32 / BF16-metric / BF16, a
+degree sweep p=1..7 at ~2^27 cell-wise values (FP64 and FP32 Laplace), and the Poisson CG
+time-to-1e-10 (plain FP64 Jacobi-PCG vs FP64 iterative refinement around an FP32 inner CG).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-sweep] [--no-cg]
+
+--impl reference times the FP64 CPU oracle (explicit element matrices) on a bounded cell sample of
+the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+P, NCELL, KIND = 4, 64, 3
+WORKLOAD = "laplace+mass apply+DSS, Q4 (125 DoFs/cell), 5 Gauss pts/dir, 64^3 curved cells, metric 7xFP64/qp"
+METRIC = "cell-wise DoF/s of apply at p=2..7 (FP64 vs mixed); CG time-to-1e-10 on 1 GB300"
+SWEEP_N = {1: 256, 2: 171, 3: 128, 4: 102, 5: 85, 6: 73, 7: 64}
+
+
+def flops_per_value(n, kind):
+    """Algorithmic FP64-equivalent flops per cell-wise value of the collocation apply on curved
+    cells: K: 12n+9 MADs + 2 adds; M: 6n+1 MADs; K+M: 12n+10 MADs + 3 adds."""
+    return {1: 24 * n + 20, 2: 12 * n + 2, 3: 24 * n + 23}[kind]
+
+
+def bytes_per_value(prec, kind):
+    """Algorithmic HBM bytes per cell-wise value: read x, write y, read the metric once."""
+    vs = {0: 8, 1: 8, 2: 4, 3: 4, 4: 2}[prec]
+    gs = {0: 8, 1: 8, 2: 4, 3: 2, 4: 2}[prec]
+    nc = {1: 6, 2: 1, 3: 7}[kind]
+    return 2 * vs + nc * gs
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# FP32 issue-rate roofline for double-float arithmetic: 152 SMs x 128 FP32 lanes x 2.07 GHz,
+# 12 FP32 instructions per emulated FP64 multiply-add (2 flops).
+DF64_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 12 * 2 / 1e12
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running (for the timed region)."""
+
+    def __init__(self, index=0):
+        self.index, self.proc, self.lines = index, None, []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return rank, local, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------- GPU arm ----
+def event_pair():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def time_apply(cw, op, x, y, steps, warmup, stream, assemble=True):
+    """Times `steps` steps (LOCAL apply kernel, then the DSS passes when assemble) with events on
+    the launching stream; returns (ms per step, ms per apply kernel)."""
+    import torch
+    for _ in range(warmup):
+        cw.cw_apply(op.handle, x, y, cw.CW_APPLY_LOCAL, stream=stream.cuda_stream)
+        if assemble:
+            cw.cw_dss(op.handle, y, cw.CW_DSS_SUM, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    ev = [event_pair() for _ in range(steps)]
+    t0, t1 = event_pair()
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        for a, b in ev:
+            a.record(stream)
+            cw.cw_apply(op.handle, x, y, cw.CW_APPLY_LOCAL, stream=stream.cuda_stream)
+            b.record(stream)
+            if assemble:
+                cw.cw_dss(op.handle, y, cw.CW_DSS_SUM, stream=stream.cuda_stream)
+        t1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = t0.elapsed_time(t1) / steps
+    kern_ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    return step_ms, kern_ms
+
+
+def gpu_arm(args, rank, local, world):
+    import torch
+
+    import paper_2607_03413_gb300 as cw
+    torch.cuda.set_device(local)
+    cw.load()
+    hbm, hbm_src = peaks()
+    stream = torch.cuda.Stream()
+    mesh = synth.box_mesh(args.cells, perturb=0.1)
+    M = cw.Mesh.from_synth(mesh)
+    op = cw.Operator(M, P, KIND, cw.CW_GEOM_METRIC, args.prec)
+    n = P + 1
+    ug = torch.from_numpy(synth.global_vector(mesh, P, seed=rank)).cuda()
+    x = op.gather(ug)
+    y = op.empty()
+    if args.tune:
+        op.autotune(x, y, reps=3)  # picks cells-per-CTA and TMA staging (before the timed region)
+    variant = op.variant()
+    torch.cuda.synchronize()
+
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        step_ms, kern_ms = time_apply(cw, op, x, y, args.steps, args.warmup, stream)
+    barrier(world)
+    torch.cuda.synchronize()
+    step_ms = max_over_ranks(step_ms, world)
+    clocks = clk.summary()
+    units = op.L * world
+    value = units / (step_ms * 1e-3)
+
+    out = {"metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": step_ms, "apply_kernel_ms": kern_ms}
+    if not args.e2e:
+        return out
+    # end to end through the C ABI with host buffers: H2D of x, apply + DSS, D2H of y per step
+    xh = torch.empty(op.L, dtype=torch.float64, pin_memory=True)
+    xh.copy_(x.cpu())
+    yh = torch.empty(op.L, dtype=torch.float64, pin_memory=True)
+    xd, yd = op.empty(), op.empty()
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            xd.copy_(xh, non_blocking=True)
+            cw.cw_apply(op.handle, xd, yd, cw.CW_APPLY_ASSEMBLE, stream=stream.cuda_stream)
+            yh.copy_(yd, non_blocking=True)
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    a, b = event_pair()
+    a.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(a.elapsed_time(b) / args.steps, world)
+
+    fl = flops_per_value(n, KIND) * op.L
+    achieved_tflops = fl / (kern_ms * 1e-3) / 1e12
+    by = bytes_per_value(0, KIND) * op.L
+    roof = {"bound": "alu", "achieved": round(achieved_tflops, 3), "peak": round(DF64_PEAK_TFLOPS, 3),
+            "unit": "TFLOP/s", "frac": round(achieved_tflops / DF64_PEAK_TFLOPS, 4), "traffic": None,
+            "kernel": f"apply_metric_kernel<N=5, cells/CTA={variant[0]}, staged={variant[1]}, double-float>",
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 12 instructions per double-float MAD",
+            "hbm": {"achieved": round(by / (kern_ms * 1e-3) / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(by / (kern_ms * 1e-3) / 1e9 / hbm, 4), "peak_source": hbm_src}}
+    out = {
+        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 storage, double-float (f32 pair) arithmetic",
+        "data": "synthetic: seeded uniform[-1,1] continuous global vector gathered to cells; curved "
+                "64^3 unit-cube mesh (0.1h sinusoidal displacement)",
+        "config": {"workload": WORKLOAD, "degree": P, "cells": args.cells ** 3, "cellwise_values": op.L,
+                   "kind": "laplace+mass", "assemble": True, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (2.4 GB per step), no flush"},
+        "apply_kernel_ms": kern_ms,
+        "unique_dofs_per_s": (args.cells * P + 1) ** 3 * world / (step_ms * 1e-3),
+        "roofline": roof,
+        "clocks": clocks,
+        "e2e": {"value": units / (e2e_ms * 1e-3), "unit": "DoF/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": op.L * 8, "d2h_bytes_per_step": op.L * 8},
+        "gpu_launches": 4 * args.steps,
+    }
+    del x, y, xd, yd
+    op.close()
+
+    if not args.mixed:
+        return out
+    # mixed precision on the same workload
+    mixed = {}
+    for name, prec in [("f64_native", cw.CW_PREC_F64_NATIVE), ("f32", cw.CW_PREC_F32),
+                       ("f32_bf16metric", cw.CW_PREC_F32_BF16G), ("bf16", cw.CW_PREC_BF16)]:
+        o = cw.Operator(M, P, KIND, cw.CW_GEOM_METRIC, prec)
+        xx = o.gather(ug)
+        yy = o.empty()
+        o.autotune(xx, yy, reps=3)
+        sm, km = time_apply(cw, o, xx, yy, args.steps, args.warmup, stream)
+        gbs = bytes_per_value(prec, KIND) * o.L / (km * 1e-3) / 1e9
+        mixed[name] = {"dofs_per_s": o.L / (sm * 1e-3), "ms_per_step": sm, "apply_kernel_ms": km,
+                       "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+        o.close()
+    out["mixed"] = mixed
+
+    if args.sweep:
+        out["sweep"] = degree_sweep(cw, stream, hbm, args)
+    if args.cg:
+        out["cg"] = cg_bench(cw, args)
+    return out
+
+
+def degree_sweep(cw, stream, hbm, args):
+    import torch
+    res = {}
+    for p, N in SWEEP_N.items():
+        mesh = synth.box_mesh(N, perturb=0.1)
+        M = cw.Mesh.from_synth(mesh)
+        ug = torch.from_numpy(synth.global_vector(mesh, p, seed=0)).cuda()
+        row = {}
+        for name, prec in [("f64", cw.CW_PREC_F64), ("f32", cw.CW_PREC_F32), ("bf16", cw.CW_PREC_BF16)]:
+            o = cw.Operator(M, p, cw.CW_LAPLACE, cw.CW_GEOM_METRIC, prec)
+            x = o.gather(ug)
+            y = o.empty()
+            o.autotune(x, y, reps=2)
+            sm, km = time_apply(cw, o, x, y, max(3, args.steps // 2), 2, stream, assemble=False)
+            gbs = bytes_per_value(prec, 1) * o.L / (km * 1e-3) / 1e9
+            row[name] = {"dofs_per_s": o.L / (km * 1e-3), "hbm_frac": round(gbs / hbm, 4)}
+            del x, y
+            o.close()
+        res[f"p{p}"] = {"cells": N ** 3, "values": N ** 3 * (p + 1) ** 3, **row}
+        del ug
+        M.close()
+    return res
+
+
+def cg_bench(cw, args):
+    """Poisson -Laplace u = f, u = sin(pi x) sin(pi y) sin(pi z), homogeneous Dirichlet, Q3 on the
+    128^3 curved mesh (134,217,728 cell-wise values): time to relative residual 1e-10 (measured
+    with the native-FP64 operator) from u = 0, for each solver mode; one warm-up solve at a
+    loose tolerance first."""
+    import torch
+    N, p = 128, 3
+    mesh = synth.box_mesh(N, perturb=0.1)
+    M = cw.Mesh.from_synth(mesh)
+    op = cw.Operator(M, p, cw.CW_LAPLACE, cw.CW_GEOM_METRIC, cw.CW_PREC_F64, cw.CW_BC_DIRICHLET0)
+    b = op.load_vector(0)
+    u = torch.empty_like(b)
+    res = {"workload": f"Poisson Q{p}, {N}^3 curved cells, {op.L} cell-wise values, Jacobi-PCG, rtol 1e-10",
+           "unit": "s"}
+    names = [("ir_f32", cw.CW_CG_IR_F32), ("ir_bf16_metric", cw.CW_CG_IR_BF16), ("f64_doublefloat", cw.CW_CG_F64),
+             ("f64_native", cw.CW_CG_F64_NATIVE)]
+    for name, mode in names:
+        op.cg_solve(b, u, rtol=1e-3, maxit=200, mode=mode, check=False)  # warm-up: allocations, graphs
+        torch.cuda.synchronize()
+        _, st, rc = op.cg_solve(b, u, rtol=1e-10, maxit=20000, mode=mode, check=False)
+        res[name] = {"seconds": st.seconds, "iterations": st.iterations, "outer": st.outer_iterations,
+                     "rel_residual": st.rel_residual, "status": int(rc),
+                     "ms_per_iteration": 1e3 * st.seconds / max(1, st.iterations)}
+    res["speedup_ir_f32_vs_f64_native"] = res["f64_native"]["seconds"] / res["ir_f32"]["seconds"]
+    res["speedup_ir_f32_vs_f64_doublefloat"] = res["f64_doublefloat"]["seconds"] / res["ir_f32"]["seconds"]
+    op.close()
+    M.close()
+    return res
+
+
+# ------------------------------------------------------------------------- CPU oracle ----
+def oracle_sample_rate(target_s, seed=0):
+    """Times the oracle apply (explicit element matrices, K+M, p=4) on a cell sample of the 64^3
+    curved workload; the sample grows until one timing takes about target_s seconds."""
+    import oracle
+    oracle.build()
+    mesh = synth.box_mesh(NCELL, perturb=0.1)
+    rng = np.random.default_rng(seed)
+    x = synth.cellwise_random(mesh, P, seed=seed)
+    ncell = 16
+    while True:
+        cells = np.sort(rng.choice(mesh.ncells, ncell, replace=False))
+        t0 = time.perf_counter()
+        oracle.apply_local(mesh, P, KIND, x, cells)
+        dt = time.perf_counter() - t0
+        if dt >= target_s or ncell >= mesh.ncells:
+            return ncell * (P + 1) ** 3 / dt, ncell, dt
+        ncell = min(mesh.ncells, int(ncell * max(2.0, min(8.0, target_s / max(dt, 1e-3)))))
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return None
+    # calibrate a per-step sample of about 2 s, then time warmup + steps of it
+    import oracle
+    rate, ncell, dt = oracle_sample_rate(2.0)
+    mesh = synth.box_mesh(NCELL, perturb=0.1)
+    x = synth.cellwise_random(mesh, P, seed=1)
+    rng = np.random.default_rng(1)
+    times = []
+    for s in range(args.warmup + args.steps):
+        cells = np.sort(rng.choice(mesh.ncells, ncell, replace=False))
+        t0 = time.perf_counter()
+        oracle.apply_local(mesh, P, KIND, x, cells)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    value = ncell * (P + 1) ** 3 / (ms * 1e-3)
+    samp = f"{ncell} random cells of the 64^3 mesh per step (element matrices built per cell), OpenMP"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "degree": P, "cells": NCELL ** 3, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": cores(), "kind": "oracle",
+                             "sample": samp},
+            "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300")
+    ap.add_argument("--no-sweep", dest="sweep", action="store_false")
+    ap.add_argument("--no-cg", dest="cg", action="store_false")
+    ap.add_argument("--no-mixed", dest="mixed", action="store_false")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu", dest="cpu", action="store_false")
+    ap.add_argument("--no-tune", dest="tune", action="store_false", help="default kernel variant, no autotuning")
+    ap.add_argument("--cells", type=int, default=NCELL, help="cells per direction (profiling cases)")
+    ap.add_argument("--prec", type=int, default=0, help="CW_PREC_* of the main step (profiling cases)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        # rank 0 alone times the oracle; other ranks exit without work
+        rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+        out = reference_arm(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    rank, local, world = dist_init(args)
+    if False:
+        pass
+    else:
+        out = gpu_arm(args, rank, local, world)
+        if rank == 0 and world == 1 and args.cpu:
+            rate, ncell, dt = oracle_sample_rate(args.cpu_seconds)
+            out["cpu_baseline"] = {"value": rate, "unit": "DoF/s", "cores": cores(), "kind": "oracle",
+                                   "sample": f"{ncell} random cells of the 64^3 curved mesh, K+M p=4, "
+                                             f"element matrices built and applied per cell ({dt:.1f} s)"}
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

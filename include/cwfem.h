@@ -89,10 +89,12 @@ typedef enum {
 #define CW_DSS_SUM 0     /* v <- S v = G G^T v */
 #define CW_DSS_AVERAGE 1 /* v <- S_bar v = G (G^T G)^-1 G^T v */
 
-/* cg modes */
-#define CW_CG_F64 0     /* Jacobi-PCG, everything FP64 (double-float apply) */
-#define CW_CG_IR_F32 1  /* FP64 iterative refinement around an FP32 Jacobi-PCG */
-#define CW_CG_IR_BF16 2 /* as IR_F32 with the inner metric stored in BF16 */
+/* cg modes: every mode keeps u, b and the outer residual b - A u in FP64 (the residual evaluated
+   with the native-FP64 operator) and refines u += d with an inner Jacobi-PCG for A d = S_bar r */
+#define CW_CG_F64 0        /* inner CG in FP64 with the double-float operator */
+#define CW_CG_IR_F32 1     /* inner CG in FP32 (FP32 vectors and metric, FP64-accumulated dots) */
+#define CW_CG_IR_BF16 2    /* inner CG in FP32 with the metric stored in BF16 */
+#define CW_CG_F64_NATIVE 3 /* inner CG in FP64 with the native-FP64 operator (plain FP64 CG) */
 
 typedef struct {
     int iterations;        /* total CG iterations (inner iterations summed for IR modes) */
@@ -128,6 +130,23 @@ int64_t cw_op_global_len(cw_op op);   /* (nx p + 1)(ny p + 1)(nz p + 1), or -1 *
 /* Bytes of device memory the operator owns (geometry, tables, diagonal, solver scratch). */
 int64_t cw_op_device_bytes(cw_op op);
 
+/*
+ * Apply-kernel variant (the tuning knobs): cells per CTA -- 0 for the degree's default or one of
+ * the two choices cw_op_get_variant reports -- and stage = 1 to move each CTA's input and metric
+ * tiles into shared memory with bulk asynchronous copies (TMA) at kernel entry, 0 for direct
+ * loads. Results do not depend on the variant beyond rounding order. CW_PREC_F64_NATIVE has only
+ * the default variant (CW_ERR_UNSUPPORTED otherwise).
+ */
+cw_status cw_op_set_variant(cw_op op, int cells_per_cta, int stage);
+/* Current variant; choices2 (may be NULL) receives the two cells-per-CTA choices of the degree. */
+cw_status cw_op_get_variant(cw_op op, int *cells_per_cta, int *stage, int *choices2);
+/*
+ * Autotuner: times every variant of the LOCAL apply on the caller's x, y (device, op vector
+ * type, length cw_op_cellwise_len; y is overwritten) with `reps` launches each on `stream`, keeps
+ * the fastest on the op and returns its time per launch in *best_ms (may be NULL). Synchronises.
+ */
+cw_status cw_op_autotune(cw_op op, const void *x, void *y, int reps, void *stream, float *best_ms);
+
 /* x = G u: replicate a device global FP64 vector into cell-wise storage of the op's precision. */
 cw_status cw_gather(cw_op op, const double *u_global, void *x, void *stream);
 
@@ -162,9 +181,12 @@ cw_status cw_load_vector(cw_op op, int which, double *b, void *stream);
  * (op bc must be CW_BC_DIRICHLET0, precision CW_PREC_F64), by Jacobi-preconditioned CG on
  * cell-wise data from u = 0 (Sec. 4.1 Eq. (jacobi_recap); Sec. 4.4). b: FP64 cell-wise dual;
  * u: FP64 cell-wise primal output. Stops when rel_residual <= rtol or after maxit iterations
- * (CW_ERR_NOT_CONVERGED; u then holds the last iterate). mode selects FP64 CG or FP64 iterative
- * refinement around an FP32 (or BF16-metric) inner CG. The first IR call on an op allocates the
- * inner operator and its vectors. Synchronises `stream`. stats may be NULL.
+ * (CW_ERR_NOT_CONVERGED; u then holds the last iterate). mode selects the inner solver (see the
+ * CW_CG_* modes); the relative residual is always measured with the native-FP64 operator. The
+ * inner right-hand side is the averaged residual S_bar r (same assembly G^T r, every copy small),
+ * so that rounding it to FP32 keeps the assembled residual. The first call on an op allocates the
+ * solver vectors (and, for the CW_CG_IR_* modes, the FP32 inner operator). Synchronises `stream`.
+ * stats may be NULL.
  */
 cw_status cw_cg_solve(cw_op op, const double *b, double *u, double rtol, int maxit, int mode,
                       cw_cg_stats *stats, void *stream);

@@ -24,13 +24,14 @@ CW_PREC_F64, CW_PREC_F64_NATIVE, CW_PREC_F32, CW_PREC_F32_BF16G, CW_PREC_BF16 = 
 CW_BC_NONE, CW_BC_DIRICHLET0 = 0, 1
 CW_APPLY_LOCAL, CW_APPLY_ASSEMBLE = 0, 1
 CW_DSS_SUM, CW_DSS_AVERAGE = 0, 1
-CW_CG_F64, CW_CG_IR_F32, CW_CG_IR_BF16 = 0, 1, 2
+CW_CG_F64, CW_CG_IR_F32, CW_CG_IR_BF16, CW_CG_F64_NATIVE = 0, 1, 2, 3
 
 # exported symbols declared in include/cwfem.h (checked by the CPU test suite)
 EXPORTED = [
     "cw_status_string", "cw_last_error", "cw_mesh_create", "cw_mesh_destroy", "cw_op_create",
     "cw_op_destroy", "cw_op_cellwise_len", "cw_op_global_len", "cw_op_device_bytes", "cw_gather",
-    "cw_apply", "cw_dss", "cw_diagonal", "cw_load_vector", "cw_cg_solve",
+    "cw_apply", "cw_dss", "cw_diagonal", "cw_load_vector", "cw_cg_solve", "cw_op_set_variant",
+    "cw_op_get_variant", "cw_op_autotune",
 ]
 
 
@@ -76,6 +77,9 @@ def load(path: str = LIB_PATH):
         "cw_diagonal": ([vp, vp, vp], i32),
         "cw_load_vector": ([vp, i32, vp, vp], i32),
         "cw_cg_solve": ([vp, vp, vp, dbl, i32, i32, ctypes.POINTER(cw_cg_stats), vp], i32),
+        "cw_op_set_variant": ([vp, i32, i32], i32),
+        "cw_op_get_variant": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+        "cw_op_autotune": ([vp, vp, vp, i32, vp, ctypes.POINTER(ctypes.c_float)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -174,6 +178,22 @@ def cw_cg_solve(op, b, u, rtol=1e-10, maxit=10000, mode=CW_CG_F64, stream=None, 
     return rc, st
 
 
+def cw_op_set_variant(op, cells_per_cta, stage):
+    _check(load().cw_op_set_variant(op, cells_per_cta, stage), "cw_op_set_variant")
+
+
+def cw_op_get_variant(op):
+    c, s, ch = ctypes.c_int(), ctypes.c_int(), (ctypes.c_int * 2)()
+    _check(load().cw_op_get_variant(op, ctypes.byref(c), ctypes.byref(s), ch), "cw_op_get_variant")
+    return c.value, s.value, (ch[0], ch[1])
+
+
+def cw_op_autotune(op, x, y, reps=5, stream=None):
+    ms = ctypes.c_float()
+    _check(load().cw_op_autotune(op, _ptr(x), _ptr(y), reps, _stream(stream), ctypes.byref(ms)), "cw_op_autotune")
+    return ms.value
+
+
 # ------------------------------------------------------------------ convenience ----
 _VEC_DTYPE = {CW_PREC_F64: "float64", CW_PREC_F64_NATIVE: "float64", CW_PREC_F32: "float32",
               CW_PREC_F32_BF16G: "float32", CW_PREC_BF16: "bfloat16"}
@@ -231,6 +251,15 @@ class Operator:
         y = self.empty() if y is None else y
         cw_apply(self.handle, x, y, CW_APPLY_ASSEMBLE if assemble else CW_APPLY_LOCAL)
         return y
+
+    def set_variant(self, cells_per_cta=0, stage=1):
+        cw_op_set_variant(self.handle, cells_per_cta, stage)
+
+    def variant(self):
+        return cw_op_get_variant(self.handle)
+
+    def autotune(self, x, y, reps=5):
+        return cw_op_autotune(self.handle, x, y, reps)
 
     def dss(self, v, average=False):
         cw_dss(self.handle, v, CW_DSS_AVERAGE if average else CW_DSS_SUM)

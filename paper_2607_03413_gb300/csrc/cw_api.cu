@@ -11,6 +11,7 @@
 
 #include "cw_apply.cuh"
 #include "cw_internal.h"
+#include "cw_launch.cuh"
 
 namespace cw {
 
@@ -639,6 +640,95 @@ cw_status cw_load_vector(cw_op oh, int which, double *b, void *stream)
     load_kernel<<<(unsigned)op->E, n3 < 128 ? 128 : (n3 > 512 ? 512 : n3), n3 * sizeof(double), s>>>(
         op->mesh->d_verts, op->mesh->nx, op->mesh->ny, op->n, which, rule, b);
     CW_CUDA_TRY(cudaGetLastError());
+    return CW_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+cw_status cw_op_set_variant(cw_op oh, int cells_per_cta, int stage)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    if (!op) return fail(CW_ERR_ARG, "cw_op_set_variant: NULL handle");
+    int ch[2];
+    cpb_choices(op->p, ch);
+    if (cells_per_cta != 0 && cells_per_cta != ch[0] && cells_per_cta != ch[1])
+        return fail(CW_ERR_ARG, "cw_op_set_variant: cells_per_cta must be 0 or one of cw_op_get_variant's choices");
+    if (stage != 0 && stage != 1) return fail(CW_ERR_ARG, "cw_op_set_variant: stage must be 0 or 1");
+    if (op->prec == CW_PREC_F64_NATIVE && (cells_per_cta != 0 || stage != 0))
+        return fail(CW_ERR_UNSUPPORTED, "cw_op_set_variant: CW_PREC_F64_NATIVE has only the default variant");
+    op->cpb = cells_per_cta == ch[0] ? 0 : cells_per_cta;
+    op->stage = stage;
+    return CW_OK;
+}
+
+cw_status cw_op_get_variant(cw_op oh, int *cells_per_cta, int *stage, int *choices2)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    if (!op) return fail(CW_ERR_ARG, "cw_op_get_variant: NULL handle");
+    int ch[2];
+    cpb_choices(op->p, ch);
+    if (cells_per_cta) *cells_per_cta = op->cpb == 0 ? ch[0] : op->cpb;
+    if (stage) *stage = op->stage;
+    if (choices2) {
+        choices2[0] = ch[0];
+        choices2[1] = ch[1];
+    }
+    return CW_OK;
+}
+
+cw_status cw_op_autotune(cw_op oh, const void *x, void *y, int reps, void *stream, float *best_ms)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    if (!op || !x || !y || x == y) return fail(CW_ERR_ARG, "cw_op_autotune: NULL or aliasing argument");
+    if (reps < 1) return fail(CW_ERR_ARG, "cw_op_autotune: reps must be >= 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (op->prec == CW_PREC_F64_NATIVE) {
+        op->cpb = 0;
+        op->stage = 0;
+        if (best_ms) *best_ms = -1.0f;
+        return CW_OK;
+    }
+    int ch[2];
+    cpb_choices(op->p, ch);
+    cudaEvent_t e0, e1;
+    CW_CUDA_TRY(cudaEventCreate(&e0));
+    CW_CUDA_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bc = 0, bs = op->stage;
+    const int nstage = op->geom == CW_GEOM_METRIC ? 2 : 1;
+    for (int ci = 0; ci < 2; ++ci)
+        for (int st = 0; st < nstage; ++st) {
+            op->cpb = ci == 0 ? 0 : ch[1];
+            op->stage = st;
+            if (apply_local(*op, x, y, s) != cudaSuccess) {  // variant not launchable (smem)
+                cudaGetLastError();
+                continue;
+            }
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps; ++r) apply_local(*op, x, y, s);
+            cudaEventRecord(e1, s);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return cuda_fail(e, "cw_op_autotune");
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            if (ms < best) {
+                best = ms;
+                bc = op->cpb;
+                bs = st;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    op->cpb = bc;
+    op->stage = bs;
+    if (best_ms) *best_ms = best;
     return CW_OK;
 }
 

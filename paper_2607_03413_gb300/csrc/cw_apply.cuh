@@ -19,6 +19,7 @@
 // evaluated as two x-contractions, three y-contractions and two z-contractions.
 #pragma once
 #include "cw_arith.cuh"
+#include "cw_tma.cuh"
 
 namespace cw {
 
@@ -80,31 +81,85 @@ __host__ __device__ constexpr int metric_ncomp(int kind) { return kind == 1 ? 6 
 
 // ------------------------------------------------------------------------ curved kernel ----
 // geo layout: [cell][comp][qp] with qp = a + N(b + N c); comps (xx, yy, zz, xy, xz, yz, mass)
-// for KIND 3, the first six for KIND 1, the mass coefficient alone for KIND 2.
-template <int N, int CPB, class Ar, class VS, class GS, int KIND>
+// for kind 3, the first six for kind 1, the mass coefficient alone for kind 2.
+//
+// STAGE: the CTA's input tile and metric tile are moved into shared memory by two 1D bulk copies
+// issued at entry (x on barrier 0, metric on barrier 1), so the metric stream overlaps the
+// interpolation and gradient sweeps. Tiles that cannot use a bulk copy (ragged last tile,
+// misaligned span) and copies that do not complete within the wait bound are read with ordinary
+// global loads instead.
+template <int N, int CPB, class T, class GS>
+__host__ __device__ constexpr size_t metric_smem_bytes(int nc, bool stage)
+{
+    return stage ? ((3 * CPB * Lines<N>::CS * sizeof(T) + 15) / 16 * 16 + (CPB * nc * N * N * N * sizeof(GS) + 15) / 16 * 16 + 16)
+                 : 3 * CPB * Lines<N>::CS * sizeof(T);
+}
+
+template <int N, int CPB, class Ar, class VS, class GS, bool STAGE>
 __global__ void __launch_bounds__(N *N *CPB) apply_metric_kernel(const VS *__restrict__ x, VS *__restrict__ y,
                                                                   const GS *__restrict__ geo, int64_t ncells,
-                                                                  TabMetric<N, typename Ar::C> tab)
+                                                                  int kind, TabMetric<N, typename Ar::C> tab)
 {
     using T = typename Ar::T;
     using L = Lines<N>;
-    constexpr int N2 = N * N, N3 = N2 * N, CS = L::CS, NC = metric_ncomp(KIND);
-    constexpr bool HAS_K = (KIND & 1) != 0, HAS_M = (KIND & 2) != 0;
+    constexpr int N2 = N * N, N3 = N2 * N, CS = L::CS;
+    const bool HAS_K = (kind & 1) != 0, HAS_M = (kind & 2) != 0;
+    const int NC = metric_ncomp(kind);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *S0 = reinterpret_cast<T *>(smem_raw);
     const int t = threadIdx.x, c = t / N2, r = t - c * N2, ra = r % N, rb = r / N;
-    const int64_t cell = static_cast<int64_t>(blockIdx.x) * CPB + c;
+    const int64_t cell0 = static_cast<int64_t>(blockIdx.x) * CPB;
+    const int64_t cell = cell0 + c;
     const bool act = cell < ncells;
     T *s0 = S0 + c * CS;
     T *s1 = S0 + (CPB + c) * CS;
     T *s2 = S0 + (2 * CPB + c) * CS;
 
+    // ---- tile staging
+    bool x_smem = false, g_smem = false;
+    const VS *xs = nullptr;
+    const GS *gs = nullptr;
+    uint64_t *bar = nullptr;
+    if constexpr (STAGE) {
+        const size_t offg = (3 * CPB * CS * sizeof(T) + 15) / 16 * 16;
+        GS *sG = reinterpret_cast<GS *>(smem_raw + offg);
+        bar = reinterpret_cast<uint64_t *>(smem_raw + offg + (CPB * NC * N3 * sizeof(GS) + 15) / 16 * 16);
+        VS *sX = reinterpret_cast<VS *>(S0 + CPB * CS);  // the S1 region is free until the gradients
+        const VS *xsrc = x + cell0 * N3;
+        const GS *gsrc = geo + cell0 * NC * N3;
+        const uint32_t xb = CPB * N3 * sizeof(VS), gb = CPB * NC * N3 * sizeof(GS);
+        const bool ok = (cell0 + CPB <= ncells) && aligned16(xsrc) && aligned16(gsrc) && aligned16(sX) &&
+                        aligned16(sG) && (xb % 16 == 0) && (gb % 16 == 0);
+        if (ok) {  // block-uniform
+            if (t == 0) {
+                mbar_init(bar, 1);
+                mbar_init(bar + 1, 1);
+            }
+            __syncthreads();
+            if (t == 0) {
+                mbar_expect_tx(bar, xb);
+                bulk_g2s(sX, xsrc, xb, bar);
+                mbar_expect_tx(bar + 1, gb);
+                bulk_g2s(sG, gsrc, gb, bar + 1);
+            }
+            x_smem = mbar_wait_bounded(bar, 0);
+            xs = sX + c * N3;
+            gs = sG + c * NC * N3;
+            g_smem = true;  // decided at the physics step
+        }
+    }
+
     T v[N], w[N];
     // (1) x-line (j,k) = (ra, rb): N contiguous values of the cell, contracted with B along x
     {
-        const VS *xc = x + (act ? cell : 0) * N3 + N * r;
+        if (x_smem) {
 #pragma unroll
-        for (int m = 0; m < N; ++m) v[m] = act ? Ar::from(ldg_nc(xc + m)) : Ar::zero();
+            for (int m = 0; m < N; ++m) v[m] = Ar::from(xs[N * r + m]);
+        } else {
+            const VS *xc = x + (act ? cell : 0) * N3 + N * r;
+#pragma unroll
+            for (int m = 0; m < N; ++m) v[m] = act ? Ar::from(ldg_nc(xc + m)) : Ar::zero();
+        }
         contract<N, false, Ar>(tab.B, v, w);
         CW_STX(s0, w);
     }
@@ -119,7 +174,7 @@ __global__ void __launch_bounds__(N *N *CPB) apply_metric_kernel(const VS *__res
     CW_LDZ(s0, v);
     contract<N, false, Ar>(tab.B, v, u);
     T gx[N], gy[N], gz[N];
-    if constexpr (HAS_K) {
+    if (HAS_K) {
         contract<N, false, Ar>(tab.D, u, gz);
         CW_STZ(s0, u);
         __syncthreads();
@@ -135,15 +190,18 @@ __global__ void __launch_bounds__(N *N *CPB) apply_metric_kernel(const VS *__res
         CW_LDZ(s2, gy);
     }
     // (4) quadrature-point physics on the owned pencil, qp = (ra, rb, k)
+    if constexpr (STAGE) {
+        if (g_smem) g_smem = mbar_wait_bounded(bar + 1, 0);
+    }
     {
-        const GS *gc = geo + (act ? cell : 0) * (NC * N3) + r;
+        const GS *gc = g_smem ? gs + r : geo + (act ? cell : 0) * (NC * N3) + r;
 #pragma unroll
         for (int k = 0; k < N; ++k) {
             const GS *g = gc + N2 * k;
-            if constexpr (HAS_K) {
-                const T gxx = Ar::from(ldg_nc(g + 0 * N3)), gyy = Ar::from(ldg_nc(g + 1 * N3));
-                const T gzz = Ar::from(ldg_nc(g + 2 * N3)), gxy = Ar::from(ldg_nc(g + 3 * N3));
-                const T gxz = Ar::from(ldg_nc(g + 4 * N3)), gyz = Ar::from(ldg_nc(g + 5 * N3));
+            if (HAS_K) {
+                const T gxx = Ar::from(g[0 * N3]), gyy = Ar::from(g[1 * N3]);
+                const T gzz = Ar::from(g[2 * N3]), gxy = Ar::from(g[3 * N3]);
+                const T gxz = Ar::from(g[4 * N3]), gyz = Ar::from(g[5 * N3]);
                 T hx = Ar::mul(gx[k], gxx), hy = Ar::mul(gx[k], gxy), hz = Ar::mul(gx[k], gxz);
                 Ar::mad(hx, gy[k], gxy);
                 Ar::mad(hy, gy[k], gyy);
@@ -155,13 +213,13 @@ __global__ void __launch_bounds__(N *N *CPB) apply_metric_kernel(const VS *__res
                 gy[k] = Ar::norm(hy);
                 gz[k] = Ar::norm(hz);
             }
-            if constexpr (HAS_M) {
-                const T cm = Ar::from(ldg_nc(g + (NC - 1) * N3));
+            if (HAS_M) {
+                const T cm = Ar::from(g[(NC - 1) * N3]);
                 acc[k] = Ar::norm(Ar::mul(u[k], cm));
             }
         }
     }
-    if constexpr (HAS_K) {
+    if (HAS_K) {
         // z-part of the transposed derivative in registers, x/y parts as line owners
         contract<N, true, Ar>(tab.D, gz, v);
 #pragma unroll
@@ -196,20 +254,27 @@ __global__ void __launch_bounds__(N *N *CPB) apply_metric_kernel(const VS *__res
 #pragma unroll
         for (int m = 0; m < N; ++m) Ar::to(yc[m], w[m]);
     }
+    if constexpr (STAGE) {
+        // a copy that missed its wait bound must not land in shared memory after exit
+        if (xs != nullptr && (!x_smem || !g_smem)) {
+            mbar_wait_bounded(bar, 0);
+            mbar_wait_bounded(bar + 1, 0);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------- Cartesian kernel ----
 // geo layout: [cell][4] doubles (a_x, a_y, a_z, a_m) = (hy hz/hx, hx hz/hy, hx hy/hz, hx hy hz),
-// already multiplied by the kind mask (a_m = 0 for KIND 1, a_x = a_y = a_z = 0 for KIND 2).
-template <int N, int CPB, class Ar, class VS, int KIND>
+// already multiplied by the kind mask (a_m = 0 for kind 1, a_x = a_y = a_z = 0 for kind 2).
+template <int N, int CPB, class Ar, class VS>
 __global__ void __launch_bounds__(N *N *CPB) apply_affine_kernel(const VS *__restrict__ x, VS *__restrict__ y,
                                                                   const double *__restrict__ geo, int64_t ncells,
-                                                                  TabAffine<N, typename Ar::C> tab)
+                                                                  int kind, TabAffine<N, typename Ar::C> tab)
 {
     using T = typename Ar::T;
     using L = Lines<N>;
     constexpr int N2 = N * N, N3 = N2 * N, CS = L::CS;
-    constexpr bool HAS_K = (KIND & 1) != 0, HAS_M = (KIND & 2) != 0;
+    const bool HAS_K = (kind & 1) != 0, HAS_M = (kind & 2) != 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *S0 = reinterpret_cast<T *>(smem_raw);
     const int t = threadIdx.x, c = t / N2, r = t - c * N2, ra = r % N, rb = r / N;
@@ -225,7 +290,7 @@ __global__ void __launch_bounds__(N *N *CPB) apply_affine_kernel(const VS *__res
         for (int m = 0; m < N; ++m) v[m] = act ? Ar::from(ldg_nc(xc + m)) : Ar::zero();
         contract<N, false, Ar>(tab.M, v, P);
         CW_STX(s0, P);
-        if constexpr (HAS_K) {
+        if (HAS_K) {
             contract<N, false, Ar>(tab.K, v, Q);
             CW_STX(s1, Q);
         }
@@ -239,7 +304,7 @@ __global__ void __launch_bounds__(N *N *CPB) apply_affine_kernel(const VS *__res
         T R1[N], W[N];
         CW_LDY(s0, v);
         contract<N, false, Ar>(tab.M, v, R1);
-        if constexpr (HAS_K) {
+        if (HAS_K) {
             T R2[N], R3[N];
             contract<N, false, Ar>(tab.K, v, R2);
             CW_LDY(s1, v);
@@ -248,7 +313,7 @@ __global__ void __launch_bounds__(N *N *CPB) apply_affine_kernel(const VS *__res
             for (int m = 0; m < N; ++m) {
                 T s = Ar::mul(R3[m], ax);
                 Ar::mad(s, R2[m], ay);
-                if constexpr (HAS_M) Ar::mad(s, R1[m], am);
+                if (HAS_M) Ar::mad(s, R1[m], am);
                 W[m] = Ar::norm(s);
                 R1[m] = Ar::norm(Ar::mul(R1[m], az));
             }
@@ -265,7 +330,7 @@ __global__ void __launch_bounds__(N *N *CPB) apply_affine_kernel(const VS *__res
         T out[N];
         CW_LDZ(s0, v);
         contract<N, false, Ar>(tab.M, v, out);
-        if constexpr (HAS_K) {
+        if (HAS_K) {
             T R[N], KR[N];
             CW_LDZ(s1, R);
             contract<N, false, Ar>(tab.K, R, KR);

@@ -21,7 +21,8 @@ struct df64 {
 
 // Split a double into hi + lo floats using integer operations only. |x| < 2^-126 maps to 0 and
 // the low part is dropped when it would be subnormal (|x| < 2^-80); both are far below the
-// precision the operator needs relative to the vector norm.
+// precision the operator needs relative to the vector norm. Infinities, NaNs and finite values
+// beyond the float range map to +-inf / NaN in hi (lo = 0), so non-finite data stays non-finite.
 __device__ __forceinline__ df64 split_f64(double x)
 {
     const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
@@ -36,26 +37,37 @@ __device__ __forceinline__ df64 split_f64(double x)
         r.lo = 0.0f;
         return r;
     }
-    r.hi = __uint_as_float(sign | (static_cast<unsigned>(min(fe, 255)) << 23) | (fe >= 255 ? 0u : mhi));
+    if (fe >= 255) {
+        const bool nan = (e == 2047) && (((h32 & 0xFFFFFu) | l32) != 0u);
+        r.hi = __uint_as_float(sign | 0x7F800000u | (nan ? 0x400000u : 0u));
+        r.lo = 0.0f;
+        return r;
+    }
+    r.hi = __uint_as_float(sign | (static_cast<unsigned>(fe) << 23) | mhi);
     // remainder: the low 29 mantissa bits, worth rem * 2^(e-1075); keep its top 23 bits
     const unsigned r23 = (l32 & 0x1FFFFFFFu) >> 6;
     const float f = __fsub_rn(__uint_as_float(0x4B000000u | r23), 8388608.0f);  // exact
-    const int se = e - 942;  // biased exponent of 2^(e-1069)
+    const int se = e - 942;  // biased exponent of 2^(e-1069), in [1, 254] when fe in [1, 254] and se >= 1
     const float scale = __uint_as_float(static_cast<unsigned>(max(se, 1)) << 23);
     const float lo = __fmul_rn(f, scale);
     r.lo = (se >= 1) ? __uint_as_float(__float_as_uint(lo) | sign) : 0.0f;
     return r;
 }
 
-// Exact widening float -> double with integer operations (zero and subnormals map to +-0).
+// Exact widening float -> double with integer operations (zero and subnormals map to +-0,
+// infinities and NaNs stay infinities and NaNs).
 __device__ __forceinline__ double widen_f32(float f)
 {
     const unsigned u = __float_as_uint(f);
     const unsigned sign = u & 0x80000000u;
     const unsigned e = (u >> 23) & 0xFFu;
     const unsigned m = u & 0x7FFFFFu;
-    const unsigned hi = (e == 0u) ? sign : (sign | ((e + 896u) << 20) | (m >> 3));
-    const unsigned lo = (e == 0u) ? 0u : (m << 29);
+    unsigned hi = (e == 0u) ? sign : (sign | ((e + 896u) << 20) | (m >> 3));
+    unsigned lo = (e == 0u) ? 0u : (m << 29);
+    if (e == 255u) {
+        hi = sign | 0x7FF00000u | (m ? 0x80000u : 0u);
+        lo = 0u;
+    }
     return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(hi) << 32) | lo));
 }
 
@@ -160,9 +172,5 @@ struct ArF32 {  // FP32
     static __device__ __forceinline__ void to(__nv_bfloat16 &d, T a) { d = __float2bfloat16_rn(a); }
     static __device__ __forceinline__ double to_f64(T a) { return static_cast<double>(a); }
 };
-
-// host-side construction of table constants for each trait
-template <class Ar>
-struct ConstMaker;
 
 }  // namespace cw

@@ -1,10 +1,621 @@
-// cw_cg.cu -- cell-wise Jacobi-preconditioned CG (placeholder until the solver lands).
+// cw_cg.cu -- Jacobi-preconditioned conjugate gradients on cell-wise data, and FP64 iterative
+// refinement around a reduced-precision inner CG.
+//
+// Primal-dual CG (Sec. 4.4; Sec. 2.1, Eq. (pairing_global)): iterate u and search direction p are
+// continuous primal vectors, the residual r = b - A u is an unassembled dual vector. Every inner
+// product pairs one dual with one primal vector, so it needs no assembly. The preconditioner is
+// z = D_cell^-1 S r (Sec. 4.1, Eq. (jacobi_recap)) with the Dirichlet rows zeroed in the stored
+// inverse diagonal (Sec. 5, "Constraints baked into the diagonal"), which also keeps u and p zero
+// on the boundary. With a consistent preconditioner the iterates equal those of Jacobi-PCG on the
+// assembled interior system, iteration by iteration.
+//
+// Convergence: ||m G^T r|| / ||m G^T b|| <= rtol, evaluated cell-wise as <m S r, r> (m = interior
+// mask), since <S r, r> = ||G^T r||^2.
+//
+// Device-side control: every scalar (rho, <p,q>, alpha, beta, residual) lives in device memory;
+// one small kernel per reduction turns block partials into the scalars and raises a `done` flag
+// on convergence, breakdown or maxit, after which the update kernels leave u untouched. The host
+// replays a CUDA graph of `kBatch` iterations and reads the flag once per replay.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "cw_arith.cuh"
 #include "cw_internal.h"
-using namespace cw;
+
 namespace cw {
-void cg_release(Op *op) { (void)op; }
-}  // namespace cw
-extern "C" cw_status cw_cg_solve(cw_op, const double *, double *, double, int, int, cw_cg_stats *, void *)
+
+constexpr int kRedBlocks = 1216;  // 152 SMs x 8
+constexpr int kRedThreads = 256;
+constexpr int kBatch = 16;
+
+// device scalar slots
+enum : int { S_RHO = 0, S_PQ, S_ALPHA, S_BETA, S_RES0, S_RES, S_RHO_NEW, S_TOL2, S_ENERGY, S_NSCAL = 16 };
+// device flag slots
+enum : int { F_DONE = 0, F_ITER, F_STATUS, F_MAXIT, F_NFLAG = 8 };
+enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_MAXIT = 3 };
+
+struct CgLevel {  // vectors of one precision level
+    void *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *dinv = nullptr;
+    cudaGraphExec_t graph = nullptr;  // kBatch iterations; kernel arguments baked in
+    const void *graph_u = nullptr;    // iterate pointer the graph was captured with
+    const Op *graph_op = nullptr;     // operator the graph was captured with
+    int graph_ak = -1;                // operator evaluation the graph was captured with
+};
+
+struct CgScratch {
+    CgLevel lv64, lv32;      // FP64 inner level / FP32 inner level
+    double *rout = nullptr;  // outer FP64 residual b - A u
+    double *q64b = nullptr;  // FP64 apply output / work in outer steps
+    double *d64 = nullptr;   // FP64 inner correction
+    float *d32 = nullptr;    // FP32 inner correction
+    double *partials = nullptr;
+    double *scal = nullptr;
+    int *flags = nullptr;
+    uint8_t *kappa = nullptr;  // valence of every cell-wise entry (1, 2, 4 or 8)
+    double *h_scal = nullptr;
+    int *h_flags = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int64_t bytes = 0;
+};
+
+// ---------------------------------------------------------------------------- kernels ----
+template <class V>
+__device__ __forceinline__ df64 as_df(V v);
+template <>
+__device__ __forceinline__ df64 as_df<double>(double v) { return split_f64(v); }
+template <>
+__device__ __forceinline__ df64 as_df<float>(float v) { return df64{v, 0.0f}; }
+
+// block-level sum of a double into partial slot (blockIdx.x) of `out`
+__device__ __forceinline__ void block_sum_store(double v, double *out)
 {
-    return fail(CW_ERR_UNSUPPORTED, "cw_cg_solve: not built yet");
+    __shared__ double sh[kRedThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < kRedThreads / 32 ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) out[blockIdx.x] = v;
+    }
+    __syncthreads();
+}
+
+// partial <a, b> with double-float accumulation (products exact in the FP32-pair format)
+template <class V>
+__global__ void __launch_bounds__(kRedThreads) k_dot(const V *__restrict__ a, const V *__restrict__ b, int64_t n,
+                                                     double *__restrict__ part)
+{
+    df64 acc{0.0f, 0.0f};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        df_mad(acc, as_df(a[i]), as_df(b[i]));
+    block_sum_store(df_to_double(acc), part);
+}
+
+// valence (number of cells sharing the DoF) of cell-wise entry t
+__device__ __host__ __forceinline__ int entry_valence(int64_t t, int nx, int ny, int nz, int p)
+{
+    const int n = p + 1, n3 = n * n * n;
+    const int64_t e = t / n3;
+    const int loc = (int)(t - e * n3), i = loc % n, j = (loc / n) % n, k = loc / (n * n);
+    const int64_t cx = e % nx, cy = (e / nx) % ny, cz = e / ((int64_t)nx * ny);
+    int v = 1;
+    if ((i == 0 && cx > 0) || (i == p && cx < nx - 1)) v *= 2;
+    if ((j == 0 && cy > 0) || (j == p && cy < ny - 1)) v *= 2;
+    if ((k == 0 && cz > 0) || (k == p && cz < nz - 1)) v *= 2;
+    return v;
+}
+
+
+// Given w = S r: z = dinv * w (in place on w), r <- w / kappa (the averaged dual S_bar r, which has
+// the same assembly G^T r, so every later use of r is unchanged, but each copy now carries 1/kappa
+// of the assembled value instead of a partial integral with cancellation), and partials
+// <r, z> and <m w, r> (m = dinv != 0) = ||m G^T r||^2.
+template <class V>
+__global__ void __launch_bounds__(kRedThreads) k_precond(V *__restrict__ r, V *__restrict__ w,
+                                                         const V *__restrict__ dinv, int64_t n,
+                                                         const uint8_t *__restrict__ kappa,
+                                                         double *__restrict__ part, const int *__restrict__ flags)
+{
+    if (flags[F_DONE]) return;
+    df64 a1{0.0f, 0.0f}, a2{0.0f, 0.0f};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const V d = dinv[i], wi = w[i];
+        const V zi = d * wi;
+        const V ri = wi / V(kappa[i]);
+        w[i] = zi;
+        r[i] = ri;
+        df_mad(a1, as_df(ri), as_df(zi));
+        if (d != V(0)) df_mad(a2, as_df(wi), as_df(ri));
+    }
+    block_sum_store(df_to_double(a1), part);
+    block_sum_store(df_to_double(a2), part + gridDim.x);
+}
+
+// u += alpha p ; r -= alpha q
+template <class V, class U>
+__global__ void k_update(U *__restrict__ u, const V *__restrict__ p, V *__restrict__ r, const V *__restrict__ q,
+                         int64_t n, const double *__restrict__ scal, const int *__restrict__ flags)
+{
+    if (flags[F_DONE]) return;
+    const double alpha = scal[S_ALPHA];
+    const V a = static_cast<V>(alpha);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        u[i] = u[i] + static_cast<U>(a) * static_cast<U>(p[i]);
+        r[i] = r[i] - a * q[i];
+    }
+}
+
+// p = z + beta p
+template <class V>
+__global__ void k_pupdate(V *__restrict__ p, const V *__restrict__ z, int64_t n, const double *__restrict__ scal,
+                          const int *__restrict__ flags)
+{
+    if (flags[F_DONE]) return;
+    const V beta = static_cast<V>(scal[S_BETA]);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = z[i] + beta * p[i];
+}
+
+template <class D, class S>
+__global__ void k_copy(D *__restrict__ dst, const S *__restrict__ src, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = static_cast<D>(src[i]);
+}
+
+// dst = a - b (FP64 residual of the outer refinement step)
+__global__ void k_sub(double *__restrict__ dst, const double *__restrict__ a, const double *__restrict__ b, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = a[i] - b[i];
+}
+
+__global__ void k_add_correction_f64(double *__restrict__ u, const double *__restrict__ d, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        u[i] += d[i];
+}
+
+// u += d (FP64 iterate, reduced-precision correction)
+__global__ void k_add_correction(double *__restrict__ u, const float *__restrict__ d, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        u[i] += static_cast<double>(d[i]);
+}
+
+__global__ void k_make_kappa(uint8_t *__restrict__ kappa, int nx, int ny, int nz, int p, int64_t L)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < L; t += (int64_t)gridDim.x * blockDim.x)
+        kappa[t] = static_cast<uint8_t>(entry_valence(t, nx, ny, nz, p));
+}
+
+// masked inverse diagonal: 0 on DoFs of the block boundary (homogeneous Dirichlet), 1/d elsewhere
+template <class V>
+__global__ void k_make_dinv(const double *__restrict__ d, V *__restrict__ dinv, int nx, int ny, int nz, int p,
+                            int64_t L, int dirichlet)
+{
+    const int n = p + 1, n3 = n * n * n;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < L; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = t / n3;
+        const int loc = (int)(t - e * n3), i = loc % n, j = (loc / n) % n, k = loc / (n * n);
+        const int64_t cx = e % nx, cy = (e / nx) % ny, cz = e / ((int64_t)nx * ny);
+        const bool bnd = (cx == 0 && i == 0) || (cx == nx - 1 && i == p) || (cy == 0 && j == 0) ||
+                         (cy == ny - 1 && j == p) || (cz == 0 && k == 0) || (cz == nz - 1 && k == p);
+        dinv[t] = (dirichlet && bnd) ? V(0) : static_cast<V>(1.0 / d[t]);
+    }
+}
+
+__device__ __forceinline__ double sum_partials(const double *part, int nb)
+{
+    __shared__ double sh[kRedThreads];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) v += part[i];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+enum : int { STAGE_INIT = 0, STAGE_PQ = 1, STAGE_RHO = 2, STAGE_RES = 3, STAGE_ENERGY = 4 };
+
+// turns block partials into scalars and runs the CG scalar logic for one stage (one block)
+__global__ void __launch_bounds__(kRedThreads) k_finalize(const double *__restrict__ part, int nb,
+                                                          double *__restrict__ scal, int *__restrict__ flags,
+                                                          int stage)
+{
+    if (stage != STAGE_INIT && stage != STAGE_RES && stage != STAGE_ENERGY && flags[F_DONE]) return;
+    const double s0 = sum_partials(part, nb);
+    const double s1 = (stage == STAGE_INIT || stage == STAGE_RHO || stage == STAGE_RES) ? sum_partials(part + nb, nb) : 0.0;
+    if (threadIdx.x != 0) return;
+    if (stage == STAGE_INIT) {
+        scal[S_RHO] = s0;
+        scal[S_RES0] = s1;
+        scal[S_RES] = s1;
+        flags[F_ITER] = 0;
+        flags[F_STATUS] = ST_RUNNING;
+        flags[F_DONE] = 0;
+        if (!(s1 > 0.0)) {  // zero right-hand side: u = 0 is the solution
+            flags[F_STATUS] = ST_CONVERGED;
+            flags[F_DONE] = 1;
+        }
+    } else if (stage == STAGE_PQ) {
+        if (!(s0 > 0.0) || !isfinite(s0)) {
+            flags[F_STATUS] = ST_BREAKDOWN;
+            flags[F_DONE] = 1;
+            return;
+        }
+        scal[S_PQ] = s0;
+        scal[S_ALPHA] = scal[S_RHO] / s0;
+    } else if (stage == STAGE_RHO) {
+        const double rho_new = s0;
+        scal[S_RES] = s1;
+        flags[F_ITER] += 1;
+        if (!isfinite(rho_new) || !isfinite(s1)) {
+            flags[F_STATUS] = ST_BREAKDOWN;
+            flags[F_DONE] = 1;
+            return;
+        }
+        if (s1 <= scal[S_TOL2] * scal[S_RES0]) {
+            flags[F_STATUS] = ST_CONVERGED;
+            flags[F_DONE] = 1;
+        } else if (flags[F_ITER] >= flags[F_MAXIT]) {
+            flags[F_STATUS] = ST_MAXIT;
+            flags[F_DONE] = 1;
+        }
+        scal[S_BETA] = rho_new / scal[S_RHO];
+        scal[S_RHO] = rho_new;
+    } else if (stage == STAGE_RES) {
+        scal[S_RES] = s1;
+    } else {
+        scal[S_ENERGY] = s0;
+    }
+}
+
+// --------------------------------------------------------------------------- host side ----
+static unsigned vec_grid() { return kRedBlocks; }
+
+// which operator evaluation an inner level uses
+enum ApplyKind : int { AK_DF = 0, AK_NATIVE = 1, AK_OP = 2 };
+
+static cudaError_t apply_by_kind(const Op &op, int ak, const void *x, void *y, cudaStream_t s)
+{
+    if (ak == AK_NATIVE) return apply_launch_f64n(op, x, y, s);  // same FP64 metric layout
+    return apply_local(op, x, y, s);
+}
+
+template <class V>
+static cudaError_t alloc_level(CgLevel &lv, int64_t L, int64_t &bytes)
+{
+    void **ptrs[5] = {&lv.r, &lv.p, &lv.q, &lv.z, &lv.dinv};
+    for (void **pp : ptrs) {
+        cudaError_t e = cudaMalloc(pp, L * sizeof(V));
+        if (e != cudaSuccess) return e;
+        bytes += L * sizeof(V);
+    }
+    return cudaSuccess;
+}
+
+static void free_level(CgLevel &lv)
+{
+    cudaFree(lv.r);
+    cudaFree(lv.p);
+    cudaFree(lv.q);
+    cudaFree(lv.z);
+    cudaFree(lv.dinv);
+    if (lv.graph) cudaGraphExecDestroy(lv.graph);
+    lv = CgLevel();
+}
+
+void cg_release(Op *op)
+{
+    CgScratch *c = op->cg;
+    if (!c) return;
+    free_level(c->lv64);
+    free_level(c->lv32);
+    cudaFree(c->rout);
+    cudaFree(c->q64b);
+    cudaFree(c->d64);
+    cudaFree(c->d32);
+    cudaFree(c->partials);
+    cudaFree(c->scal);
+    cudaFree(c->flags);
+    cudaFree(c->kappa);
+    cudaFreeHost(c->h_scal);
+    cudaFreeHost(c->h_flags);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+    op->cg = nullptr;
+}
+
+// one CG iteration on level `lv` of operator `aop` with vector type V, iterate U* u
+template <class V, class U>
+static cudaError_t cg_iteration(const Op &aop, int ak, CgLevel &lv, U *u, CgScratch &c, cudaStream_t s)
+{
+    const int64_t L = aop.L;
+    V *r = static_cast<V *>(lv.r), *p = static_cast<V *>(lv.p), *q = static_cast<V *>(lv.q),
+      *z = static_cast<V *>(lv.z), *dinv = static_cast<V *>(lv.dinv);
+    cudaError_t e = apply_by_kind(aop, ak, p, q, s);
+    if (e != cudaSuccess) return e;
+    k_dot<V><<<vec_grid(), kRedThreads, 0, s>>>(p, q, L, c.partials);
+    k_finalize<<<1, kRedThreads, 0, s>>>(c.partials, kRedBlocks, c.scal, c.flags, STAGE_PQ);
+    k_update<V, U><<<vec_grid(), 256, 0, s>>>(u, p, r, q, L, c.scal, c.flags);
+    k_copy<V, V><<<vec_grid(), 256, 0, s>>>(z, r, L);
+    if ((e = dss_launch(aop, z, CW_DSS_SUM, s)) != cudaSuccess) return e;
+    k_precond<V><<<vec_grid(), kRedThreads, 0, s>>>(r, z, dinv, L, c.kappa, c.partials, c.flags);
+    k_finalize<<<1, kRedThreads, 0, s>>>(c.partials, kRedBlocks, c.scal, c.flags, STAGE_RHO);
+    k_pupdate<V><<<vec_grid(), 256, 0, s>>>(p, z, L, c.scal, c.flags);
+    return cudaGetLastError();
+}
+
+// CG on A u = rhs for level lv (rhs already in lv.r), u zeroed here. Returns the final status.
+template <class V, class U>
+static cw_status cg_run(const Op &aop, int ak, CgLevel &lv, U *u, CgScratch &c, double rtol, int maxit, int *iters)
+{
+    cudaStream_t s = c.stream;
+    const int64_t L = aop.L;
+    V *r = static_cast<V *>(lv.r), *p = static_cast<V *>(lv.p), *z = static_cast<V *>(lv.z),
+      *dinv = static_cast<V *>(lv.dinv);
+    CW_CUDA_TRY(cudaMemsetAsync(u, 0, L * sizeof(U), s));
+    c.h_scal[0] = rtol * rtol;
+    c.h_flags[0] = 0;
+    c.h_flags[1] = maxit;
+    CW_CUDA_TRY(cudaMemcpyAsync(c.scal + S_TOL2, c.h_scal, sizeof(double), cudaMemcpyHostToDevice, s));
+    CW_CUDA_TRY(cudaMemcpyAsync(c.flags + F_DONE, &c.h_flags[0], sizeof(int), cudaMemcpyHostToDevice, s));
+    CW_CUDA_TRY(cudaMemcpyAsync(c.flags + F_MAXIT, &c.h_flags[1], sizeof(int), cudaMemcpyHostToDevice, s));
+    // z = D^-1 S r, r <- S_bar r, rho = <r, z>, res0 = <m S r, r>, p = z
+    k_copy<V, V><<<vec_grid(), 256, 0, s>>>(z, r, L);
+    CW_CUDA_TRY(dss_launch(aop, z, CW_DSS_SUM, s));
+    k_precond<V><<<vec_grid(), kRedThreads, 0, s>>>(r, z, dinv, L, c.kappa, c.partials, c.flags);
+    k_finalize<<<1, kRedThreads, 0, s>>>(c.partials, kRedBlocks, c.scal, c.flags, STAGE_INIT);
+    k_copy<V, V><<<vec_grid(), 256, 0, s>>>(p, z, L);
+    CW_CUDA_TRY(cudaGetLastError());
+    // one eager iteration (first-use initialisation of the kernels), then graph batches
+    CW_CUDA_TRY((cg_iteration<V, U>(aop, ak, lv, u, c, s)));
+    if (lv.graph && (lv.graph_u != u || lv.graph_op != &aop || lv.graph_ak != ak)) {
+        cudaGraphExecDestroy(lv.graph);
+        lv.graph = nullptr;
+    }
+    if (!lv.graph) {
+        cudaGraph_t g;
+        CW_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int b = 0; b < kBatch && e == cudaSuccess; ++b) e = cg_iteration<V, U>(aop, ak, lv, u, c, s);
+        cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        if (e != cudaSuccess) return cuda_fail(e, "cg capture");
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cg capture end");
+        e = cudaGraphInstantiate(&lv.graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "cg graph instantiate");
+        lv.graph_u = u;
+        lv.graph_op = &aop;
+        lv.graph_ak = ak;
+    }
+    for (;;) {
+        CW_CUDA_TRY(cudaMemcpyAsync(c.h_flags, c.flags, F_NFLAG * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CW_CUDA_TRY(cudaStreamSynchronize(s));
+        if (c.h_flags[F_DONE]) break;
+        CW_CUDA_TRY(cudaGraphLaunch(lv.graph, s));
+    }
+    *iters = c.h_flags[F_ITER];
+    switch (c.h_flags[F_STATUS]) {
+    case ST_CONVERGED: return CW_OK;
+    case ST_BREAKDOWN: return fail(CW_ERR_BREAKDOWN, "cw_cg_solve: breakdown (<p,Ap> <= 0 or non-finite)");
+    default: return fail(CW_ERR_NOT_CONVERGED, "cw_cg_solve: maxit reached");
+    }
+}
+
+static cw_status ensure_scratch(Op *op, int mode)
+{
+    CgScratch *c = op->cg;
+    const int64_t L = op->L;
+    if (!c) {
+        c = new CgScratch;
+        op->cg = c;
+        CW_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        CW_CUDA_TRY(cudaEventCreate(&c->ev0));
+        CW_CUDA_TRY(cudaEventCreate(&c->ev1));
+        CW_CUDA_TRY(cudaMalloc(&c->partials, 2 * kRedBlocks * sizeof(double)));
+        CW_CUDA_TRY(cudaMalloc(&c->scal, S_NSCAL * sizeof(double)));
+        CW_CUDA_TRY(cudaMalloc(&c->flags, F_NFLAG * sizeof(int)));
+        CW_CUDA_TRY(cudaMemset(c->scal, 0, S_NSCAL * sizeof(double)));
+        CW_CUDA_TRY(cudaMemset(c->flags, 0, F_NFLAG * sizeof(int)));
+        CW_CUDA_TRY(cudaMallocHost(&c->h_scal, S_NSCAL * sizeof(double)));
+        CW_CUDA_TRY(cudaMallocHost(&c->h_flags, F_NFLAG * sizeof(int)));
+        CW_CUDA_TRY((alloc_level<double>(c->lv64, L, c->bytes)));
+        CW_CUDA_TRY(cudaMalloc(&c->rout, L * sizeof(double)));
+        CW_CUDA_TRY(cudaMalloc(&c->q64b, L * sizeof(double)));
+        CW_CUDA_TRY(cudaMalloc(&c->kappa, L));
+        c->bytes += 2 * L * sizeof(double) + L + 2 * kRedBlocks * sizeof(double);
+        k_make_kappa<<<vec_grid(), 256, 0, c->stream>>>(c->kappa, op->mesh->nx, op->mesh->ny, op->mesh->nz, op->p, L);
+        // FP64 masked inverse diagonal
+        double *d = static_cast<double *>(c->lv64.q);  // borrow q as the diagonal buffer
+        cw_status st = cw_diagonal(reinterpret_cast<cw_op>(op), d, c->stream);
+        if (st != CW_OK) return st;
+        k_make_dinv<double><<<vec_grid(), 256, 0, c->stream>>>(d, static_cast<double *>(c->lv64.dinv), op->mesh->nx,
+                                                               op->mesh->ny, op->mesh->nz, op->p, L, 1);
+        CW_CUDA_TRY(cudaGetLastError());
+        CW_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        op->owned_bytes += c->bytes;
+    }
+    const bool fp64_inner = (mode == CW_CG_F64 || mode == CW_CG_F64_NATIVE);
+    if (fp64_inner && !c->d64) {
+        CW_CUDA_TRY(cudaMalloc(&c->d64, L * sizeof(double)));
+        op->owned_bytes += L * sizeof(double);
+    }
+    if (!fp64_inner) {
+        const int iprec = (mode == CW_CG_IR_BF16) ? CW_PREC_F32_BF16G : CW_PREC_F32;
+        if (op->inner && op->inner->prec != iprec) {  // switch inner metric precision
+            op->owned_bytes -= op->inner->owned_bytes;
+            cw_op_destroy(reinterpret_cast<cw_op>(op->inner));
+            op->inner = nullptr;
+            if (c->lv32.graph) {
+                cudaGraphExecDestroy(c->lv32.graph);
+                c->lv32.graph = nullptr;
+            }
+        }
+        if (!op->inner) {
+            cw_op inner;
+            cw_status st = cw_op_create(reinterpret_cast<cw_mesh>(op->mesh), op->p, op->kind, op->geom, iprec, op->bc, &inner);
+            if (st != CW_OK) return st;
+            op->inner = reinterpret_cast<Op *>(inner);
+        }
+        if (!c->d32) {
+            int64_t b = 0;
+            CW_CUDA_TRY((alloc_level<float>(c->lv32, L, b)));
+            CW_CUDA_TRY(cudaMalloc(&c->d32, L * sizeof(float)));
+            b += L * sizeof(float);
+            k_copy<float, double><<<vec_grid(), 256, 0, c->stream>>>(static_cast<float *>(c->lv32.dinv),
+                                                                     static_cast<const double *>(c->lv64.dinv), L);
+            CW_CUDA_TRY(cudaGetLastError());
+            CW_CUDA_TRY(cudaStreamSynchronize(c->stream));
+            op->owned_bytes += b;
+        }
+    }
+    return CW_OK;
+}
+
+// ||m G^T r||^2 = <m S r, r> of an FP64 dual vector r (work buffer w); r is left unchanged
+static cw_status residual_norm2(const Op &op, const double *r, double *w, CgScratch &c, double *out)
+{
+    cudaStream_t s = c.stream;
+    const int64_t L = op.L;
+    double *rr = static_cast<double *>(c.lv64.r);  // scratch copy: k_precond averages it in place
+    k_copy<double, double><<<vec_grid(), 256, 0, s>>>(w, r, L);
+    k_copy<double, double><<<vec_grid(), 256, 0, s>>>(rr, r, L);
+    CW_CUDA_TRY(dss_launch(op, w, CW_DSS_SUM, s));
+    CW_CUDA_TRY(cudaMemsetAsync(c.flags + F_DONE, 0, sizeof(int), s));
+    k_precond<double><<<vec_grid(), kRedThreads, 0, s>>>(rr, w, static_cast<double *>(c.lv64.dinv), L, c.kappa,
+                                                         c.partials, c.flags);
+    k_finalize<<<1, kRedThreads, 0, s>>>(c.partials, kRedBlocks, c.scal, c.flags, STAGE_RES);
+    CW_CUDA_TRY(cudaMemcpyAsync(c.h_scal, c.scal + S_RES, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CW_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = c.h_scal[0];
+    return CW_OK;
+}
+
+static cw_status energy(const Op &op, const double *r, const double *u, CgScratch &c, double *out)
+{
+    cudaStream_t s = c.stream;
+    k_dot<double><<<vec_grid(), kRedThreads, 0, s>>>(r, u, op.L, c.partials);
+    k_finalize<<<1, kRedThreads, 0, s>>>(c.partials, kRedBlocks, c.scal, c.flags, STAGE_ENERGY);
+    CW_CUDA_TRY(cudaMemcpyAsync(c.h_scal, c.scal + S_ENERGY, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CW_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = c.h_scal[0];
+    return CW_OK;
+}
+
+// S_bar r (averaging DSS, Eq. (averaging_dss)) of the FP64 residual into the inner level's rhs
+static cw_status averaged_rhs(const Op &op, const double *r, double *work, void *dst, bool to_f32, cudaStream_t s)
+{
+    k_copy<double, double><<<vec_grid(), 256, 0, s>>>(work, r, op.L);
+    CW_CUDA_TRY(dss_launch(op, work, CW_DSS_AVERAGE, s));
+    if (to_f32)
+        k_copy<float, double><<<vec_grid(), 256, 0, s>>>(static_cast<float *>(dst), work, op.L);
+    else
+        k_copy<double, double><<<vec_grid(), 256, 0, s>>>(static_cast<double *>(dst), work, op.L);
+    CW_CUDA_TRY(cudaGetLastError());
+    return CW_OK;
+}
+
+}  // namespace cw
+
+using namespace cw;
+
+// Every mode runs the same outer loop: r = b - A u with the native-FP64 operator (the accurate
+// residual), stop when ||m G^T r|| <= rtol ||m G^T b||, else solve A d = S_bar r approximately with
+// an inner Jacobi-PCG and set u += d. The inner solver is FP64 with the double-float operator
+// (CW_CG_F64), FP64 with the native operator (CW_CG_F64_NATIVE), or FP32 with the FP32 / BF16-metric
+// operator (CW_CG_IR_*). The inner tolerance is the reduction still needed (FP64 inner levels) or
+// that reduction clamped to at least 1e-4 (FP32 inner levels, whose attainable accuracy is lower).
+extern "C" cw_status cw_cg_solve(cw_op oh, const double *b, double *u, double rtol, int maxit, int mode,
+                                 cw_cg_stats *stats, void *stream)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    if (!op || !b || !u) return fail(CW_ERR_ARG, "cw_cg_solve: NULL argument");
+    if (op->prec != CW_PREC_F64) return fail(CW_ERR_ARG, "cw_cg_solve: the operator must be CW_PREC_F64");
+    if (op->bc != CW_BC_DIRICHLET0) return fail(CW_ERR_ARG, "cw_cg_solve: the operator must use CW_BC_DIRICHLET0");
+    if (mode < CW_CG_F64 || mode > CW_CG_F64_NATIVE) return fail(CW_ERR_ARG, "cw_cg_solve: bad mode");
+    if (!(rtol > 0.0) || maxit < 1) return fail(CW_ERR_ARG, "cw_cg_solve: rtol must be > 0 and maxit >= 1");
+    if (b == u) return fail(CW_ERR_ARG, "cw_cg_solve: b and u must not alias");
+    cudaStream_t us = static_cast<cudaStream_t>(stream);
+    cw_status st = ensure_scratch(op, mode);
+    if (st != CW_OK) return st;
+    CgScratch &c = *op->cg;
+    cudaStream_t s = c.stream;
+    const int64_t L = op->L;
+    // order the solve after the caller's stream
+    CW_CUDA_TRY(cudaEventRecord(c.ev0, us));
+    CW_CUDA_TRY(cudaStreamWaitEvent(s, c.ev0, 0));
+    CW_CUDA_TRY(cudaEventRecord(c.ev0, s));
+    const bool fp64_inner = (mode == CW_CG_F64 || mode == CW_CG_F64_NATIVE);
+    const int ak = mode == CW_CG_F64 ? AK_DF : (mode == CW_CG_F64_NATIVE ? AK_NATIVE : AK_OP);
+    const double floor_tol = fp64_inner ? 1e-15 : 1e-4;
+    double *r = c.rout, *w = c.q64b;
+    int iters = 0, outer = 0;
+    double res0 = 0.0, res = 0.0;
+    CW_CUDA_TRY(cudaMemsetAsync(u, 0, L * sizeof(double), s));
+    k_copy<double, double><<<vec_grid(), 256, 0, s>>>(r, b, L);
+    if ((st = residual_norm2(*op, r, w, c, &res0)) != CW_OK) return st;
+    if (!std::isfinite(res0)) return fail(CW_ERR_BREAKDOWN, "cw_cg_solve: non-finite right-hand side");
+    res = res0;
+    st = res0 > 0.0 ? CW_ERR_NOT_CONVERGED : CW_OK;
+    while (res0 > 0.0 && iters < maxit && outer < 50) {
+        if (res <= rtol * rtol * res0) {
+            st = CW_OK;
+            break;
+        }
+        const double need = rtol * std::sqrt(res0 / res);
+        const double itol = std::min(0.5, std::max(floor_tol, 0.5 * need));
+        int it = 0;
+        cw_status ist;
+        if (fp64_inner) {
+            if ((ist = averaged_rhs(*op, r, w, c.lv64.r, false, s)) != CW_OK) return ist;
+            ist = cg_run<double, double>(*op, ak, c.lv64, c.d64, c, itol, maxit - iters, &it);
+            k_add_correction_f64<<<vec_grid(), 256, 0, s>>>(u, c.d64, L);
+        } else {
+            if ((ist = averaged_rhs(*op, r, w, c.lv32.r, true, s)) != CW_OK) return ist;
+            ist = cg_run<float, float>(*op->inner, AK_OP, c.lv32, c.d32, c, itol, maxit - iters, &it);
+            k_add_correction<<<vec_grid(), 256, 0, s>>>(u, c.d32, L);
+        }
+        if (ist == CW_ERR_BREAKDOWN) return ist;
+        iters += it;
+        ++outer;
+        // accurate residual with the native FP64 operator
+        CW_CUDA_TRY(apply_launch_f64n(*op, u, w, s));
+        k_sub<<<vec_grid(), 256, 0, s>>>(r, b, w, L);
+        if ((st = residual_norm2(*op, r, w, c, &res)) != CW_OK) return st;
+        if (!std::isfinite(res)) return fail(CW_ERR_BREAKDOWN, "cw_cg_solve: non-finite residual");
+        st = CW_ERR_NOT_CONVERGED;
+    }
+    if (res <= rtol * rtol * res0) st = CW_OK;
+    if (st == CW_ERR_NOT_CONVERGED) set_error("cw_cg_solve: maxit reached before rtol");
+    CW_CUDA_TRY(cudaEventRecord(c.ev1, s));
+    CW_CUDA_TRY(cudaEventSynchronize(c.ev1));
+    float ms = 0.0f;
+    CW_CUDA_TRY(cudaEventElapsedTime(&ms, c.ev0, c.ev1));
+    double eta = 0.0;
+    cw_status s3 = energy(*op, r, u, c, &eta);  // r = b - A u of the returned u
+    if (s3 != CW_OK) return s3;
+    CW_CUDA_TRY(cudaEventRecord(c.ev0, s));
+    CW_CUDA_TRY(cudaStreamWaitEvent(us, c.ev0, 0));
+    if (stats) {
+        stats->iterations = iters;
+        stats->outer_iterations = outer;
+        stats->rel_residual = res0 > 0.0 ? std::sqrt(res / res0) : 0.0;
+        stats->energy = eta;
+        stats->seconds = ms * 1e-3;
+    }
+    return st;
 }

@@ -3,6 +3,6 @@
 namespace cw {
 cudaError_t apply_launch_f64n(const Op &op, const void *x, void *y, cudaStream_t s)
 {
-    return launch_degree<ArF64, double, double>(op, x, y, s);
+    return launch_degree<ArF64, double, double, false>(op, x, y, s);
 }
 }  // namespace cw

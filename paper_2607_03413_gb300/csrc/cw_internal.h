@@ -45,6 +45,8 @@ struct Op {
     double *d_dinv = nullptr;  // cell-wise masked inverse diagonal (solver), lazily
     CgScratch *cg = nullptr;
     Op *inner = nullptr;  // reduced-precision twin used by iterative refinement
+    int cpb = 0;          // apply kernel variant: cells per CTA (0 = default for the degree)
+    int stage = 1;        // apply kernel variant: TMA staging of the input and metric tiles
     int64_t owned_bytes = 0;
 };
 

@@ -1,5 +1,5 @@
 // cw_launch.cuh -- host launchers for the apply kernels: table conversion, tile size per degree,
-// shared-memory opt-in, and the (degree, kind, geometry) dispatch used by the cw_inst_*.cu units.
+// shared-memory opt-in, and the (degree, tile, staging) dispatch used by the cw_inst_*.cu units.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -27,44 +27,52 @@ struct MakeC<ArF32> {
     static float from(double v) { return static_cast<float>(v); }
 };
 
-// cells per CTA: about 128-200 threads per CTA
+// cells per CTA: the default (about 128-200 threads) and the alternative the tuner can pick
 template <int N>
-constexpr int cells_per_cta()
+constexpr int cpb_default()
 {
     return N == 2 ? 32 : N == 3 ? 16 : N == 4 ? 8 : N == 5 ? 8 : N == 6 ? 4 : N == 7 ? 4 : 2;
+}
+template <int N>
+constexpr int cpb_alt()
+{
+    return cpb_default<N>() / 2;
 }
 
 template <class K>
 static cudaError_t opt_in_smem(K kernel, size_t smem)
 {
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     if (smem <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <int N, class Ar, class VS, class GS, int KIND>
+template <int N, int CPB, class Ar, class VS, class GS, bool STAGE>
 cudaError_t launch_metric(const Op &op, const void *x, void *y, cudaStream_t s)
 {
-    constexpr int CPB = cells_per_cta<N>();
     TabMetric<N, typename Ar::C> tab;
     for (int a = 0; a < N; ++a)
         for (int b = 0; b < N; ++b) {
             tab.B[a][b] = MakeC<Ar>::from(op.tab.B[a][b]);
             tab.D[a][b] = MakeC<Ar>::from(op.tab.D[a][b]);
         }
-    const size_t smem = 3 * CPB * Lines<N>::CS * sizeof(typename Ar::T);
-    auto kern = apply_metric_kernel<N, CPB, Ar, VS, GS, KIND>;
-    static cudaError_t attr = opt_in_smem(kern, smem);
-    if (attr != cudaSuccess) return attr;
+    const size_t smem = metric_smem_bytes<N, CPB, typename Ar::T, GS>(metric_ncomp(op.kind), STAGE);
+    auto kern = apply_metric_kernel<N, CPB, Ar, VS, GS, STAGE>;
+    static size_t opted = 0;  // largest size opted in so far for this instantiation
+    if (smem > opted) {
+        cudaError_t e = opt_in_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        opted = smem;
+    }
     const unsigned grid = (unsigned)((op.E + CPB - 1) / CPB);
     kern<<<grid, N * N * CPB, smem, s>>>(static_cast<const VS *>(x), static_cast<VS *>(y),
-                                         static_cast<const GS *>(op.d_geo), op.E, tab);
+                                         static_cast<const GS *>(op.d_geo), op.E, op.kind, tab);
     return cudaGetLastError();
 }
 
-template <int N, class Ar, class VS, int KIND>
+template <int N, int CPB, class Ar, class VS>
 cudaError_t launch_affine(const Op &op, const void *x, void *y, cudaStream_t s)
 {
-    constexpr int CPB = cells_per_cta<N>();
     TabAffine<N, typename Ar::C> tab;
     for (int a = 0; a < N; ++a)
         for (int b = 0; b < N; ++b) {
@@ -72,45 +80,60 @@ cudaError_t launch_affine(const Op &op, const void *x, void *y, cudaStream_t s)
             tab.K[a][b] = MakeC<Ar>::from(op.tab.K1[a][b]);
         }
     const size_t smem = 2 * CPB * Lines<N>::CS * sizeof(typename Ar::T);
-    auto kern = apply_affine_kernel<N, CPB, Ar, VS, KIND>;
-    static cudaError_t attr = opt_in_smem(kern, smem);
-    if (attr != cudaSuccess) return attr;
+    auto kern = apply_affine_kernel<N, CPB, Ar, VS>;
+    static size_t opted = 0;
+    if (smem > opted) {
+        cudaError_t e = opt_in_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        opted = smem;
+    }
     const unsigned grid = (unsigned)((op.E + CPB - 1) / CPB);
     kern<<<grid, N * N * CPB, smem, s>>>(static_cast<const VS *>(x), static_cast<VS *>(y),
-                                         static_cast<const double *>(op.d_geo), op.E, tab);
+                                         static_cast<const double *>(op.d_geo), op.E, op.kind, tab);
     return cudaGetLastError();
 }
 
-template <int N, class Ar, class VS, class GS>
-cudaError_t launch_kind(const Op &op, const void *x, void *y, cudaStream_t s)
+// variant selection: op.cpb (0 = default, else cpb_default or cpb_alt), op.stage (0/1)
+template <int N, class Ar, class VS, class GS, bool ALL_VARIANTS>
+cudaError_t launch_variant(const Op &op, const void *x, void *y, cudaStream_t s)
 {
+    constexpr int D = cpb_default<N>(), A = cpb_alt<N>();
     if (op.geom == CW_GEOM_AFFINE) {
-        switch (op.kind) {
-        case 1: return launch_affine<N, Ar, VS, 1>(op, x, y, s);
-        case 2: return launch_affine<N, Ar, VS, 2>(op, x, y, s);
-        default: return launch_affine<N, Ar, VS, 3>(op, x, y, s);
-        }
+        if constexpr (ALL_VARIANTS)
+            if (op.cpb == A) return launch_affine<N, A, Ar, VS>(op, x, y, s);
+        return launch_affine<N, D, Ar, VS>(op, x, y, s);
     }
-    switch (op.kind) {
-    case 1: return launch_metric<N, Ar, VS, GS, 1>(op, x, y, s);
-    case 2: return launch_metric<N, Ar, VS, GS, 2>(op, x, y, s);
-    default: return launch_metric<N, Ar, VS, GS, 3>(op, x, y, s);
+    if constexpr (ALL_VARIANTS) {
+        const bool alt = (op.cpb == A);
+        if (op.stage) return alt ? launch_metric<N, A, Ar, VS, GS, true>(op, x, y, s)
+                                 : launch_metric<N, D, Ar, VS, GS, true>(op, x, y, s);
+        return alt ? launch_metric<N, A, Ar, VS, GS, false>(op, x, y, s)
+                   : launch_metric<N, D, Ar, VS, GS, false>(op, x, y, s);
     }
+    return launch_metric<N, D, Ar, VS, GS, false>(op, x, y, s);
 }
 
-template <class Ar, class VS, class GS>
+template <class Ar, class VS, class GS, bool ALL_VARIANTS = true>
 cudaError_t launch_degree(const Op &op, const void *x, void *y, cudaStream_t s)
 {
     switch (op.n) {
-    case 2: return launch_kind<2, Ar, VS, GS>(op, x, y, s);
-    case 3: return launch_kind<3, Ar, VS, GS>(op, x, y, s);
-    case 4: return launch_kind<4, Ar, VS, GS>(op, x, y, s);
-    case 5: return launch_kind<5, Ar, VS, GS>(op, x, y, s);
-    case 6: return launch_kind<6, Ar, VS, GS>(op, x, y, s);
-    case 7: return launch_kind<7, Ar, VS, GS>(op, x, y, s);
-    case 8: return launch_kind<8, Ar, VS, GS>(op, x, y, s);
+    case 2: return launch_variant<2, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s);
+    case 3: return launch_variant<3, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s);
+    case 4: return launch_variant<4, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s);
+    case 5: return launch_variant<5, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s);
+    case 6: return launch_variant<6, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s);
+    case 7: return launch_variant<7, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s);
+    case 8: return launch_variant<8, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s);
     }
     return cudaErrorInvalidValue;
+}
+
+// the two cells-per-CTA choices of degree p
+inline void cpb_choices(int p, int out[2])
+{
+    static const int d[8] = {0, 32, 16, 8, 8, 4, 4, 2};
+    out[0] = d[p];
+    out[1] = d[p] / 2;
 }
 
 }  // namespace cw

@@ -131,3 +131,41 @@ def test_load_vector(cw, orc, p, which):
     op = cw.Operator(M, p, 1, cw.CW_GEOM_METRIC, cw.CW_PREC_F64)
     b = to_np(op.load_vector(which))
     assert rel_err(b, orc.load_vector(mesh, p, which)) <= TOL64
+
+
+@pytest.mark.parametrize("prec", [0, 2, 4], ids=["df64", "f32", "bf16"])
+@pytest.mark.parametrize("p", [1, 3, 4, 7])
+def test_apply_all_variants(cw, orc, p, prec):
+    """Every kernel variant (two tile sizes x TMA-staged or direct loads) gives the oracle's result;
+    the mesh has a ragged last tile for both tile sizes."""
+    import torch
+    mesh = synth.box_mesh(3, 3, 5, perturb=0.2) if p < 7 else synth.box_mesh(3, 1, 3, perturb=0.2)
+    x = orc.gather(mesh, p, synth.global_vector(mesh, p, seed=40 + p))
+    ref = orc.apply_local(mesh, p, 3, x)
+    M = cw.Mesh.from_synth(mesh)
+    op = cw.Operator(M, p, 3, cw.CW_GEOM_METRIC, prec)
+    _, _, choices = op.variant()
+    xd = torch.from_numpy(x).cuda().to(op.vec_dtype)
+    tol = {0: TOL64, 2: 2e-6, 4: 3e-2}[prec]
+    for cpb in choices:
+        for stage in (0, 1):
+            op.set_variant(cpb, stage)
+            y = op.apply(xd)
+            torch.cuda.synchronize()
+            assert rel_err(to_np(y), ref) <= tol, (cpb, stage)
+
+
+def test_autotune_keeps_a_valid_variant(cw, orc):
+    import torch
+    p = 4
+    mesh = synth.box_mesh(8, perturb=0.1)
+    M = cw.Mesh.from_synth(mesh)
+    op = cw.Operator(M, p, 3, cw.CW_GEOM_METRIC, cw.CW_PREC_F64)
+    x = op.gather(torch.from_numpy(synth.global_vector(mesh, p, seed=1)).cuda())
+    y = op.empty()
+    ms = op.autotune(x, y, reps=2)
+    cpb, stage, choices = op.variant()
+    assert ms > 0 and cpb in choices and stage in (0, 1)
+    y2 = op.apply(x)
+    ref = orc.apply_local(mesh, p, 3, to_np(x))
+    assert rel_err(to_np(y2), ref) <= TOL64

@@ -1,0 +1,129 @@
+"""GPU Jacobi-PCG on cell-wise data (Sec. 4.4; Eq. (jacobi_recap)) and FP64 iterative refinement
+around an FP32 / BF16-metric inner CG, checked against the oracle's assembled PCG and direct solve."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import rel_err, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cw():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2607_03413_gb300 as cw
+    from paper_2607_03413_gb300 import build
+    build.build()
+    cw.load()
+    return cw
+
+
+def make(cw, mesh, p, kind=1, geom=None):
+    M = cw.Mesh.from_synth(mesh)
+    geom = cw.CW_GEOM_METRIC if geom is None else geom
+    return M, cw.Operator(M, p, kind, geom, cw.CW_PREC_F64, cw.CW_BC_DIRICHLET0)
+
+
+@pytest.mark.parametrize("kind", [1, 3])
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_iterates_equal_assembled_pcg(cw, orc, p, kind):
+    """Primal-dual CG with the consistent preconditioner D^-1 S is iterate-identical to Jacobi-PCG
+    on the assembled interior system (Sec. 4.4)."""
+    import torch
+    mesh = synth.box_mesh(3, 4, 3, perturb=0.2)
+    M, op = make(cw, mesh, p, kind)
+    b = orc.load_vector(mesh, p, orc.PROBLEM_SINE)
+    A = orc.assemble_global(mesh, p, kind)
+    bg = orc.scatter_add(mesh, p, b)
+    mask = orc.boundary_mask_global(mesh, p)
+    _, _, _, its = orc.pcg_assembled(A, bg, mask, tol=1e-30, maxit=6, record=True)
+    bd = torch.from_numpy(b).cuda()
+    for k in (1, 3, 6):
+        u, st, rc = op.cg_solve(bd, rtol=1e-30, maxit=k, check=False)
+        assert rc == cw.CW_ERR_NOT_CONVERGED and st.iterations == k
+        assert rel_err(to_np(u), orc.gather(mesh, p, its[k])) <= 1e-10
+
+
+@pytest.mark.parametrize("p,perturb", [(2, 0.2), (3, 0.0)])
+def test_converges_to_direct_solve(cw, orc, p, perturb):
+    import torch
+    mesh = synth.box_mesh(4, 3, 5, perturb=perturb)
+    M, op = make(cw, mesh, p)
+    b = orc.load_vector(mesh, p, orc.PROBLEM_SINE)
+    A = orc.assemble_global(mesh, p, 1)
+    ud = orc.direct_solve(A, orc.scatter_add(mesh, p, b), orc.boundary_mask_global(mesh, p))
+    u, st, rc = op.cg_solve(torch.from_numpy(b).cuda(), rtol=1e-12, maxit=2000)
+    assert st.rel_residual <= 1e-12
+    assert rel_err(to_np(u), orc.gather(mesh, p, ud)) <= 1e-10
+    # energy measure eta(u) = <b - A u, u> vanishes at the discrete solution (Eq. (energy_measure))
+    assert abs(st.energy) <= 1e-10 * abs(float(b @ orc.gather(mesh, p, ud)))
+
+
+def test_bubble_is_reproduced(cw, orc):
+    """u = x(1-x)y(1-y)z(1-z) is in Q_2: the solve returns its interpolant (affine mesh, Cartesian
+    operator)."""
+    import torch
+    p = 2
+    mesh = synth.box_mesh(3, 4, 2)
+    M, op = make(cw, mesh, p, geom=cw.CW_GEOM_AFFINE)
+    b = op.load_vector(which=1)
+    u, st, rc = op.cg_solve(b, rtol=1e-13, maxit=500)
+    xyz = orc.node_coords(mesh, p)
+    assert np.abs(to_np(u) - np.prod(xyz * (1 - xyz), axis=1)).max() < 1e-11
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3], ids=["ir_f32", "ir_bf16metric", "f64_native"])
+def test_iterative_refinement_reaches_fp64_accuracy(cw, orc, mode):
+    import torch
+    p = 3
+    mesh = synth.box_mesh(6, 5, 4, perturb=0.1)
+    M, op = make(cw, mesh, p)
+    b = op.load_vector(which=0)
+    u64, s64, _ = op.cg_solve(b, rtol=1e-10, maxit=5000, mode=cw.CW_CG_F64)
+    uir, sir, _ = op.cg_solve(b, rtol=1e-10, maxit=5000, mode=mode)
+    print(f"fp64: {s64.iterations} it {s64.seconds*1e3:.2f} ms res {s64.rel_residual:.2e}; "
+          f"ir mode {mode}: {sir.iterations} it in {sir.outer_iterations} outer, res {sir.rel_residual:.2e}")
+    assert s64.rel_residual <= 1e-10 and sir.rel_residual <= 1e-10
+    if mode != cw.CW_CG_F64_NATIVE:
+        assert sir.outer_iterations >= 2
+    assert rel_err(to_np(uir), to_np(u64)) <= 1e-8
+
+
+def test_discretisation_error_matches_oracle(cw, orc):
+    import torch
+    p = 2
+    mesh = synth.box_mesh(6, perturb=0.1)
+    M, op = make(cw, mesh, p)
+    b = torch.from_numpy(orc.load_vector(mesh, p)).cuda()
+    u, st, rc = op.cg_solve(b, rtol=1e-12, maxit=3000)
+    A = orc.assemble_global(mesh, p, 1)
+    ud = orc.direct_solve(A, orc.scatter_add(mesh, p, orc.load_vector(mesh, p)), orc.boundary_mask_global(mesh, p))
+    e_gpu = orc.error_norms(mesh, p, to_np(u))
+    e_ref = orc.error_norms(mesh, p, orc.gather(mesh, p, ud))
+    assert abs(e_gpu[0] - e_ref[0]) <= 1e-8 * e_ref[0] and abs(e_gpu[1] - e_ref[1]) <= 1e-8 * e_ref[1]
+
+
+def test_failures_are_reported_not_raised_on_device(cw):
+    """Host-injected failures: a NaN right-hand side ends the solve with CW_ERR_BREAKDOWN (the
+    device detects the non-finite scalar and stops the iteration); bad arguments are rejected on
+    the host before any launch."""
+    import torch
+    p = 2
+    mesh = synth.box_mesh(3, perturb=0.1)
+    M, op = make(cw, mesh, p)
+    for idx in (5, 27 * 13 + 13):  # a boundary copy and an interior entry
+        b = op.load_vector(0)
+        b[idx] = float("nan")
+        u, st, rc = op.cg_solve(b, rtol=1e-10, maxit=100, check=False)
+        assert rc == cw.CW_ERR_BREAKDOWN, (idx, rc)
+    b = op.load_vector(0)
+    u = torch.empty_like(b)
+    assert cw.load().cw_cg_solve(op.handle, cw._ptr(b), cw._ptr(u), -1.0, 10, 0, None, None) == cw.CW_ERR_ARG
+    op32 = cw.Operator(M, p, 1, cw.CW_GEOM_METRIC, cw.CW_PREC_F32, cw.CW_BC_DIRICHLET0)
+    assert cw.load().cw_cg_solve(op32.handle, cw._ptr(b), cw._ptr(u), 1e-8, 10, 0, None, None) == cw.CW_ERR_ARG
+    # the context is still usable
+    u, st, rc = op.cg_solve(op.load_vector(0), rtol=1e-10, maxit=500)
+    assert st.rel_residual <= 1e-10
