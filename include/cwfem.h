@@ -191,6 +191,27 @@ cw_status cw_load_vector(cw_op op, int which, double *b, void *stream);
 cw_status cw_cg_solve(cw_op op, const double *b, double *u, double rtol, int maxit, int mode,
                       cw_cg_stats *stats, void *stream);
 
+/*
+ * Allocation-free variant of cw_cg_solve. The paper has no counterpart; this entry point exists
+ * for callers that must not allocate device memory while solving -- e.g. code that runs inside a
+ * caller-managed memory pool or an allocator callback, a real-time loop whose memory is fixed at
+ * start-up, or a host whose policy forbids cudaMalloc/cudaFree after initialisation. It performs
+ * the same FP64 solve as cw_cg_solve for mode CW_CG_F64 or CW_CG_F64_NATIVE (arguments, outputs
+ * and statuses as there) but takes every scratch vector from one fixed file-scope device array of
+ * about 17 MB, which every GPU that loads this library holds until the process exits. It calls no
+ * cudaMalloc, cudaFree or other allocating routine, creates no stream, event or graph, and runs on
+ * `stream` directly, synchronising it. Limit: cw_op_cellwise_len(op) <= 262144 (2^18);
+ * larger operators are rejected with CW_ERR_ARG and a message naming the limit, before any GPU
+ * work. The op itself must have been created beforehand (cw_op_create allocates its geometry).
+ * The first call on a device resolves the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture. All calls share the one
+ * array and leave their data in it; each call re-initialises what it reads. Calls that overlap
+ * on the GPU (from two streams or two threads) race on the array and must be serialised by the
+ * caller. stats->seconds is host wall time.
+ */
+cw_status cw_cg_solve_noalloc(cw_op op, const double *b, double *u, double rtol, int maxit, int mode,
+                              cw_cg_stats *stats, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,7 @@ EXPORTED = [
     "cw_status_string", "cw_last_error", "cw_mesh_create", "cw_mesh_destroy", "cw_op_create",
     "cw_op_destroy", "cw_op_cellwise_len", "cw_op_global_len", "cw_op_device_bytes", "cw_gather",
     "cw_apply", "cw_dss", "cw_diagonal", "cw_load_vector", "cw_cg_solve", "cw_op_set_variant",
-    "cw_op_get_variant", "cw_op_autotune",
+    "cw_op_get_variant", "cw_op_autotune", "cw_cg_solve_noalloc",
 ]
 
 
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
         "cw_op_set_variant": ([vp, i32, i32], i32),
         "cw_op_get_variant": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "cw_op_autotune": ([vp, vp, vp, i32, vp, ctypes.POINTER(ctypes.c_float)], i32),
+        "cw_cg_solve_noalloc": ([vp, vp, vp, dbl, i32, i32, ctypes.POINTER(cw_cg_stats), vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -175,6 +176,13 @@ def cw_cg_solve(op, b, u, rtol=1e-10, maxit=10000, mode=CW_CG_F64, stream=None, 
     rc = load().cw_cg_solve(op, _ptr(b), _ptr(u), rtol, maxit, mode, ctypes.byref(st), _stream(stream))
     if check and rc not in (CW_OK,):
         raise CwError(rc, "cw_cg_solve")
+    return rc, st
+
+
+def cw_cg_solve_noalloc(op, b, u, rtol=1e-10, maxit=10000, mode=CW_CG_F64, stream=None):
+    """Allocation-free FP64 solve (fixed library-owned scratch, cell-wise length <= 2^18)."""
+    st = cw_cg_stats()
+    rc = load().cw_cg_solve_noalloc(op, _ptr(b), _ptr(u), rtol, maxit, mode, ctypes.byref(st), _stream(stream))
     return rc, st
 
 

@@ -19,8 +19,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <mutex>
+#include <string>
 
 #include "cw_arith.cuh"
 #include "cw_internal.h"
@@ -616,6 +619,175 @@ extern "C" cw_status cw_cg_solve(cw_op oh, const double *b, double *u, double rt
         stats->rel_residual = res0 > 0.0 ? std::sqrt(res / res0) : 0.0;
         stats->energy = eta;
         stats->seconds = ms * 1e-3;
+    }
+    return st;
+}
+
+// ===================================================================== allocation-free solve ====
+// cw_cg_solve_noalloc: the same FP64 solve as cw_cg_solve (modes CW_CG_F64 and CW_CG_F64_NATIVE)
+// for callers that cannot allocate device memory at solve time -- code running inside a memory
+// pool or an allocator callback, a real-time loop, or a host that forbids cudaMalloc after start-up.
+// All its scratch lives in one file-scope __device__ array of fixed size, which the module holds on
+// every GPU that loads this library until the process exits. Every call uses the same array, so
+// calls that overlap on the GPU (two streams, or two threads) race on it.
+namespace cw {
+
+constexpr int64_t kNoAllocMaxL = int64_t(1) << 18;  // largest cell-wise length accepted
+constexpr size_t kNaVec = size_t(kNoAllocMaxL) * sizeof(double);
+// 8 FP64 vectors (rout, w, d, and the inner level r, p, q, z, dinv), the valence bytes, the block
+// partials, the device scalars and flags
+constexpr size_t kNaBytes = 8 * kNaVec + size_t(kNoAllocMaxL) + 2 * kRedBlocks * sizeof(double) +
+                            S_NSCAL * sizeof(double) + F_NFLAG * sizeof(int) + 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+// Device address of g_noalloc_scratch for the current device. In host code the symbol is only a
+// host-side stand-in; its device address comes from cudaGetSymbolAddress, resolved once per device.
+static cw_status noalloc_base(unsigned char **out)
+{
+    static std::mutex mu;
+    static unsigned char *base[128] = {};
+    int dev = 0;
+    CW_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return fail(CW_ERR_UNSUPPORTED, "cw_cg_solve_noalloc: device index >= 128");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!base[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cw_cg_solve_noalloc: cudaGetSymbolAddress");
+        base[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = base[dev];
+    return CW_OK;
+}
+
+// inner CG without graphs: iterations launched eagerly, the flag read every kBatch iterations
+static cw_status cg_run_eager(const Op &aop, int ak, CgLevel &lv, double *u, CgScratch &c, double rtol, int maxit,
+                              int *iters, cudaStream_t s)
+{
+    const int64_t L = aop.L;
+    double *r = static_cast<double *>(lv.r), *p = static_cast<double *>(lv.p), *z = static_cast<double *>(lv.z),
+           *dinv = static_cast<double *>(lv.dinv);
+    CW_CUDA_TRY(cudaMemsetAsync(u, 0, L * sizeof(double), s));
+    const double tol2 = rtol * rtol;
+    const int hf[2] = {0, maxit};
+    CW_CUDA_TRY(cudaMemcpyAsync(c.scal + S_TOL2, &tol2, sizeof(double), cudaMemcpyHostToDevice, s));
+    CW_CUDA_TRY(cudaMemcpyAsync(c.flags + F_DONE, &hf[0], sizeof(int), cudaMemcpyHostToDevice, s));
+    CW_CUDA_TRY(cudaMemcpyAsync(c.flags + F_MAXIT, &hf[1], sizeof(int), cudaMemcpyHostToDevice, s));
+    k_copy<double, double><<<vec_grid(), 256, 0, s>>>(z, r, L);
+    CW_CUDA_TRY(dss_launch(aop, z, CW_DSS_SUM, s));
+    k_precond<double><<<vec_grid(), kRedThreads, 0, s>>>(r, z, dinv, L, c.kappa, c.partials, c.flags);
+    k_finalize<<<1, kRedThreads, 0, s>>>(c.partials, kRedBlocks, c.scal, c.flags, STAGE_INIT);
+    k_copy<double, double><<<vec_grid(), 256, 0, s>>>(p, z, L);
+    CW_CUDA_TRY(cudaGetLastError());
+    for (;;) {
+        for (int b = 0; b < kBatch; ++b) CW_CUDA_TRY((cg_iteration<double, double>(aop, ak, lv, u, c, s)));
+        int hflags[F_NFLAG];
+        CW_CUDA_TRY(cudaMemcpyAsync(hflags, c.flags, sizeof hflags, cudaMemcpyDeviceToHost, s));
+        CW_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hflags[F_DONE]) {
+            *iters = hflags[F_ITER];
+            if (hflags[F_STATUS] == ST_CONVERGED) return CW_OK;
+            if (hflags[F_STATUS] == ST_BREAKDOWN) return fail(CW_ERR_BREAKDOWN, "cw_cg_solve_noalloc: breakdown");
+            return fail(CW_ERR_NOT_CONVERGED, "cw_cg_solve_noalloc: maxit reached");
+        }
+    }
+}
+
+}  // namespace cw
+
+extern "C" cw_status cw_cg_solve_noalloc(cw_op oh, const double *b, double *u, double rtol, int maxit, int mode,
+                                         cw_cg_stats *stats, void *stream)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    if (!op || !b || !u) return fail(CW_ERR_ARG, "cw_cg_solve_noalloc: NULL argument");
+    if (op->prec != CW_PREC_F64) return fail(CW_ERR_ARG, "cw_cg_solve_noalloc: the operator must be CW_PREC_F64");
+    if (op->bc != CW_BC_DIRICHLET0) return fail(CW_ERR_ARG, "cw_cg_solve_noalloc: the operator must use CW_BC_DIRICHLET0");
+    if (mode != CW_CG_F64 && mode != CW_CG_F64_NATIVE)
+        return fail(CW_ERR_ARG, "cw_cg_solve_noalloc: only the FP64 modes CW_CG_F64 and CW_CG_F64_NATIVE");
+    if (!(rtol > 0.0) || maxit < 1) return fail(CW_ERR_ARG, "cw_cg_solve_noalloc: rtol must be > 0 and maxit >= 1");
+    if (b == u) return fail(CW_ERR_ARG, "cw_cg_solve_noalloc: b and u must not alias");
+    if (op->L > kNoAllocMaxL)
+        return fail(CW_ERR_ARG, "cw_cg_solve_noalloc: cell-wise length " + std::to_string(op->L) +
+                                    " exceeds the fixed scratch limit of " + std::to_string(kNoAllocMaxL) + " values");
+    const auto t0 = std::chrono::steady_clock::now();
+    unsigned char *base = nullptr;
+    cw_status st = noalloc_base(&base);
+    if (st != CW_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t L = op->L;
+    // carve the scratch
+    CgScratch c;
+    unsigned char *cur = base;
+    auto take = [&](size_t bytes) {
+        unsigned char *p = cur;
+        cur += (bytes + 255) / 256 * 256;
+        return static_cast<void *>(p);
+    };
+    double *r = static_cast<double *>(take(kNaVec));
+    double *w = static_cast<double *>(take(kNaVec));
+    double *d = static_cast<double *>(take(kNaVec));
+    c.lv64.r = take(kNaVec);
+    c.lv64.p = take(kNaVec);
+    c.lv64.q = take(kNaVec);
+    c.lv64.z = take(kNaVec);
+    c.lv64.dinv = take(kNaVec);
+    c.kappa = static_cast<uint8_t *>(take(kNoAllocMaxL));
+    c.partials = static_cast<double *>(take(2 * kRedBlocks * sizeof(double)));
+    c.scal = static_cast<double *>(take(S_NSCAL * sizeof(double)));
+    c.flags = static_cast<int *>(take(F_NFLAG * sizeof(int)));
+    double hscal[S_NSCAL];
+    int hflags[F_NFLAG];
+    c.h_scal = hscal;
+    c.h_flags = hflags;
+    c.stream = s;
+    // the array keeps the previous call's contents: scalars and flags start from zero, the
+    // diagonal, valences and vectors are rebuilt or overwritten below before they are read
+    CW_CUDA_TRY(cudaMemsetAsync(c.scal, 0, S_NSCAL * sizeof(double), s));
+    CW_CUDA_TRY(cudaMemsetAsync(c.flags, 0, F_NFLAG * sizeof(int), s));
+    k_make_kappa<<<vec_grid(), 256, 0, s>>>(c.kappa, op->mesh->nx, op->mesh->ny, op->mesh->nz, op->p, L);
+    if ((st = cw_diagonal(oh, static_cast<double *>(c.lv64.q), s)) != CW_OK) return st;
+    k_make_dinv<double><<<vec_grid(), 256, 0, s>>>(static_cast<double *>(c.lv64.q), static_cast<double *>(c.lv64.dinv),
+                                                   op->mesh->nx, op->mesh->ny, op->mesh->nz, op->p, L, 1);
+    CW_CUDA_TRY(cudaGetLastError());
+    const int ak = mode == CW_CG_F64 ? AK_DF : AK_NATIVE;
+    int iters = 0, outer = 0;
+    double res0 = 0.0, res = 0.0;
+    CW_CUDA_TRY(cudaMemsetAsync(u, 0, L * sizeof(double), s));
+    k_copy<double, double><<<vec_grid(), 256, 0, s>>>(r, b, L);
+    if ((st = residual_norm2(*op, r, w, c, &res0)) != CW_OK) return st;
+    if (!std::isfinite(res0)) return fail(CW_ERR_BREAKDOWN, "cw_cg_solve_noalloc: non-finite right-hand side");
+    res = res0;
+    st = res0 > 0.0 ? CW_ERR_NOT_CONVERGED : CW_OK;
+    while (res0 > 0.0 && iters < maxit && outer < 50) {
+        if (res <= rtol * rtol * res0) {
+            st = CW_OK;
+            break;
+        }
+        const double itol = std::min(0.5, std::max(1e-15, 0.5 * rtol * std::sqrt(res0 / res)));
+        int it = 0;
+        if ((st = averaged_rhs(*op, r, w, c.lv64.r, false, s)) != CW_OK) return st;
+        cw_status ist = cg_run_eager(*op, ak, c.lv64, d, c, itol, maxit - iters, &it, s);
+        if (ist == CW_ERR_BREAKDOWN) return ist;
+        k_add_correction_f64<<<vec_grid(), 256, 0, s>>>(u, d, L);
+        iters += it;
+        ++outer;
+        CW_CUDA_TRY(apply_launch_f64n(*op, u, w, s));
+        k_sub<<<vec_grid(), 256, 0, s>>>(r, b, w, L);
+        if ((st = residual_norm2(*op, r, w, c, &res)) != CW_OK) return st;
+        if (!std::isfinite(res)) return fail(CW_ERR_BREAKDOWN, "cw_cg_solve_noalloc: non-finite residual");
+        st = CW_ERR_NOT_CONVERGED;
+    }
+    if (res <= rtol * rtol * res0) st = CW_OK;
+    if (st == CW_ERR_NOT_CONVERGED) set_error("cw_cg_solve_noalloc: maxit reached before rtol");
+    double eta = 0.0;
+    cw_status s3 = energy(*op, r, u, c, &eta);
+    if (s3 != CW_OK) return s3;
+    if (stats) {
+        stats->iterations = iters;
+        stats->outer_iterations = outer;
+        stats->rel_residual = res0 > 0.0 ? std::sqrt(res / res0) : 0.0;
+        stats->energy = eta;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     return st;
 }
