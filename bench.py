@@ -7,10 +7,12 @@ three DSS axis passes. Inputs (x 262 MB, metric 1.84 GB, y 262 MB) exceed the 12
 flush is needed between steps.
 
 Extra measurements in the same JSON line: the same workload in FP32 / BF16-metric / BF16, a
-degree sweep p=1..7 at ~2^27 cell-wise values (FP64 and FP32 Laplace), and the Poisson CG
-time-to-1e-10 (plain FP64 Jacobi-PCG vs FP64 iterative refinement around an FP32 inner CG).
+degree sweep p=1..7 at ~2^27 cell-wise values (FP64, FP32 and BF16 Laplace), the Poisson CG
+time-to-1e-10 (plain FP64 Jacobi-PCG vs FP64 iterative refinement around an FP32 inner CG), and
+the batched apply (16 RHS on Q5 64^3 + 48 uneven problems in one persistent launch).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-sweep] [--no-cg]
+                  [--no-batched] [--no-mixed] [--no-e2e] [--no-cpu] [--no-tune] [--cells N] [--prec P]
 
 --impl reference times the FP64 CPU oracle (explicit element matrices) on a bounded cell sample of
 the same workload on the host cores.
@@ -206,32 +208,33 @@ def gpu_arm(args, rank, local, world):
     units = op.L * world
     value = units / (step_ms * 1e-3)
 
-    out = {"metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": step_ms, "apply_kernel_ms": kern_ms}
-    if not args.e2e:
-        return out
-    # end to end through the C ABI with host buffers: H2D of x, apply + DSS, D2H of y per step
-    xh = torch.empty(op.L, dtype=torch.float64, pin_memory=True)
-    xh.copy_(x.cpu())
-    yh = torch.empty(op.L, dtype=torch.float64, pin_memory=True)
-    xd, yd = op.empty(), op.empty()
+    e2e = None
+    if args.e2e:
+        # end to end through the C ABI with host buffers: H2D of x, apply + DSS, D2H of y per step
+        xh = torch.empty(op.L, dtype=op.vec_dtype, pin_memory=True)
+        xh.copy_(x.cpu())
+        yh = torch.empty(op.L, dtype=op.vec_dtype, pin_memory=True)
+        xd, yd = op.empty(), op.empty()
 
-    def e2e_step():
-        with torch.cuda.stream(stream):
-            xd.copy_(xh, non_blocking=True)
-            cw.cw_apply(op.handle, xd, yd, cw.CW_APPLY_ASSEMBLE, stream=stream.cuda_stream)
-            yh.copy_(yd, non_blocking=True)
-    for _ in range(args.warmup):
-        e2e_step()
-    torch.cuda.synchronize()
-    barrier(world)
-    a, b = event_pair()
-    a.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
-    b.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(a.elapsed_time(b) / args.steps, world)
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                xd.copy_(xh, non_blocking=True)
+                cw.cw_apply(op.handle, xd, yd, cw.CW_APPLY_ASSEMBLE, stream=stream.cuda_stream)
+                yh.copy_(yd, non_blocking=True)
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        a, b = event_pair()
+        a.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(a.elapsed_time(b) / args.steps, world)
+        e2e = {"value": units / (e2e_ms * 1e-3), "unit": "DoF/s", "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": op.L * x.element_size(), "d2h_bytes_per_step": op.L * x.element_size()}
+        del xd, yd
 
     fl = flops_per_value(n, KIND) * op.L
     achieved_tflops = fl / (kern_ms * 1e-3) / 1e12
@@ -255,19 +258,16 @@ def gpu_arm(args, rank, local, world):
         "unique_dofs_per_s": (args.cells * P + 1) ** 3 * world / (step_ms * 1e-3),
         "roofline": roof,
         "clocks": clocks,
-        "e2e": {"value": units / (e2e_ms * 1e-3), "unit": "DoF/s", "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": op.L * 8, "d2h_bytes_per_step": op.L * 8},
+        "e2e": e2e,
         "gpu_launches": 4 * args.steps,
     }
-    del x, y, xd, yd
+    del x, y
     op.close()
 
-    if not args.mixed:
-        return out
     # mixed precision on the same workload
     mixed = {}
-    for name, prec in [("f64_native", cw.CW_PREC_F64_NATIVE), ("f32", cw.CW_PREC_F32),
-                       ("f32_bf16metric", cw.CW_PREC_F32_BF16G), ("bf16", cw.CW_PREC_BF16)]:
+    for name, prec in ([("f64_native", cw.CW_PREC_F64_NATIVE), ("f32", cw.CW_PREC_F32),
+                        ("f32_bf16metric", cw.CW_PREC_F32_BF16G), ("bf16", cw.CW_PREC_BF16)] if args.mixed else []):
         o = cw.Operator(M, P, KIND, cw.CW_GEOM_METRIC, prec)
         xx = o.gather(ug)
         yy = o.empty()
@@ -277,12 +277,15 @@ def gpu_arm(args, rank, local, world):
         mixed[name] = {"dofs_per_s": o.L / (sm * 1e-3), "ms_per_step": sm, "apply_kernel_ms": km,
                        "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
         o.close()
-    out["mixed"] = mixed
+    if mixed:
+        out["mixed"] = mixed
 
     if args.sweep:
         out["sweep"] = degree_sweep(cw, stream, hbm, args)
     if args.cg:
         out["cg"] = cg_bench(cw, args)
+    if args.batched:
+        out["batched"] = batched_bench(cw, args, stream)
     return out
 
 
@@ -308,6 +311,80 @@ def degree_sweep(cw, stream, hbm, args):
         del ug
         M.close()
     return res
+
+
+def batched_bench(cw, args, stream):
+    """Config 5: 16 right-hand sides on one Q5 64^3 curved mesh plus 48 independent problems
+    (N_i^3 cells, N_i in 8..48, degrees 2,3,5,7 in turn, seeded displacements), Laplace, applied in
+    one persistent launch replayed from a CUDA graph, after the per-degree tile autotuner. The same
+    work as 16 + 48 separate per-operator launches is timed alongside."""
+    import torch
+    probs = synth.batched_problem_list(48, seed=0)
+    out = {"workload": "16 RHS x Q5 64^3 + 48 uneven problems (8^3..48^3, p in {2,3,5,7}), Laplace"}
+    for name, prec in [("f32", cw.CW_PREC_F32), ("f64", cw.CW_PREC_F64)]:
+        keep, ops, xs, ys, nrhs = [], [], [], [], []
+        big = synth.box_mesh(64, perturb=0.1)
+        Mb = cw.Mesh.from_synth(big)
+        opb = cw.Operator(Mb, 5, cw.CW_LAPLACE, cw.CW_GEOM_METRIC, prec)
+        xb = torch.empty((16, opb.L), dtype=opb.vec_dtype, device="cuda")
+        for r in range(16):
+            opb.gather(torch.from_numpy(synth.global_vector(big, 5, seed=r)).cuda(), xb[r])
+        keep.append(Mb)
+        ops.append(opb)
+        xs.append(xb)
+        ys.append(torch.empty_like(xb))
+        nrhs.append(16)
+        for pr in probs:
+            m = synth.box_mesh(pr["n"], perturb=0.1, freq=pr["freq"], direction=pr["direction"])
+            M = cw.Mesh.from_synth(m)
+            o = cw.Operator(M, pr["p"], cw.CW_LAPLACE, cw.CW_GEOM_METRIC, prec)
+            x = o.gather(torch.from_numpy(synth.global_vector(m, pr["p"], seed=pr["seed"])).cuda())
+            keep.append(M)
+            ops.append(o)
+            xs.append(x.view(1, -1))
+            ys.append(torch.empty_like(x).view(1, -1))
+            nrhs.append(1)
+        B = cw.Batch(ops, nrhs, xs, ys)
+        modes = {}
+        for mname, mode in (("single_kernel", cw.CW_BATCH_SINGLE), ("grouped", cw.CW_BATCH_GROUPED)):
+            B.set_mode(mode)
+            B.autotune(reps=2)
+            for _ in range(args.warmup):
+                B.launch(graph=True, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            a, b = event_pair()
+            a.record(stream)
+            for _ in range(args.steps):
+                B.launch(graph=True, stream=stream.cuda_stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            mms = a.elapsed_time(b) / args.steps
+            modes[mname] = {"ms_per_launch": mms, "dofs_per_s": B.values / (mms * 1e-3),
+                            "variants": {f"p{d}": B.variant(d) for d in (2, 3, 5, 7)}}
+        ms = modes["grouped"]["ms_per_launch"]
+        # the same work as separate launches (each op with its own autotuned variant)
+        for o, x, y in zip(ops, xs, ys):
+            o.autotune(x[0], y[0], reps=2)
+
+        def unbatched():
+            for o, x, y, R in zip(ops, xs, ys, nrhs):
+                for r in range(R):
+                    cw.cw_apply(o.handle, x[r], y[r], cw.CW_APPLY_LOCAL, stream=stream.cuda_stream)
+        for _ in range(2):
+            unbatched()
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(max(3, args.steps // 4)):
+            unbatched()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_u = a.elapsed_time(b) / max(3, args.steps // 4)
+        out[name] = {"values": B.values, "ms_per_launch": ms, "dofs_per_s": B.values / (ms * 1e-3),
+                     "modes": modes, "unbatched_ms": ms_u, "unbatched_dofs_per_s": B.values / (ms_u * 1e-3)}
+        B.close()
+        del ops, xs, ys, keep
+        torch.cuda.synchronize()
+    return out
 
 
 def cg_bench(cw, args):
@@ -403,6 +480,7 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-sweep", dest="sweep", action="store_false")
     ap.add_argument("--no-cg", dest="cg", action="store_false")
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-mixed", dest="mixed", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")

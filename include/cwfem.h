@@ -192,6 +192,45 @@ cw_status cw_cg_solve(cw_op op, const double *b, double *u, double rtol, int max
                       cw_cg_stats *stats, void *stream);
 
 /*
+ * Batched apply (not in the paper): y_i = A_i x_i (LOCAL, unassembled) for nprob operators at
+ * once -- uneven meshes and mixed degrees -- each with nrhs[i] right-hand sides, in ONE persistent
+ * kernel launch. x[i] / y[i] are caller-owned device pointers to nrhs[i] consecutive cell-wise
+ * vectors of ops[i] (stride cw_op_cellwise_len(ops[i]); x[i] and y[i] must not overlap); they are
+ * bound at create and used by every launch. All operators must be CW_GEOM_METRIC and share one
+ * precision, CW_PREC_F64 (double-float arithmetic) or CW_PREC_F32; they must outlive the batch.
+ * Work items are (problem, chunk of tiles, right-hand side), right-hand side fastest, taken from a
+ * device counter by persistent CTAs (no waiting: an item number past the end ends a CTA).
+ * Mode CW_BATCH_GROUPED (default): one persistent kernel per degree present, shaped like the
+ * per-operator kernel (variant = cells-per-CTA choice + 2 * TMA staging, 0..3). Mode
+ * CW_BATCH_SINGLE: all degrees in ONE persistent kernel of 128-thread CTAs (variant = 0 full tile,
+ * 1 half tile); its 1D tables live in the library's constant memory, uploaded at create, so only
+ * one single-mode batch per precision may be launched at a time.
+ */
+#define CW_BATCH_GROUPED 0
+#define CW_BATCH_SINGLE 1
+typedef struct cw_batch_s *cw_batch;
+cw_status cw_batch_create(const cw_op *ops, const int *nrhs, const void *const *x, void *const *y, int nprob,
+                          cw_batch *out);
+cw_status cw_batch_destroy(cw_batch b);
+/* total cell-wise values one launch processes: sum_i nrhs[i] * cw_op_cellwise_len(ops[i]) */
+int64_t cw_batch_values(cw_batch b);
+/* one launch: clears the work counter and starts the persistent kernel on `stream` */
+cw_status cw_batch_launch(cw_batch b, void *stream);
+/* the same two operations captured once into a CUDA graph (on an internal stream) and replayed on
+   `stream`; changing a variant re-captures at the next call */
+cw_status cw_batch_graph_launch(cw_batch b, void *stream);
+/* launch mode (CW_BATCH_GROUPED or CW_BATCH_SINGLE); variants are kept per mode */
+cw_status cw_batch_set_mode(cw_batch b, int mode);
+/* kernel variant of one degree in the current mode (see above); cells_per_tile (may be NULL)
+   receives the resulting cells per tile */
+cw_status cw_batch_set_variant(cw_batch b, int degree, int variant);
+cw_status cw_batch_get_variant(cw_batch b, int degree, int *variant, int *cells_per_tile);
+/* autotuner: for each degree present, times every variant of the current mode over `reps`
+   launches of the whole batch on `stream` (overwriting every y) and keeps the fastest;
+   synchronises */
+cw_status cw_batch_autotune(cw_batch b, int reps, void *stream, float *best_ms);
+
+/*
  * Allocation-free variant of cw_cg_solve. The paper has no counterpart; this entry point exists
  * for callers that must not allocate device memory while solving -- e.g. code that runs inside a
  * caller-managed memory pool or an allocator callback, a real-time loop whose memory is fixed at

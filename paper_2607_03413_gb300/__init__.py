@@ -25,13 +25,16 @@ CW_BC_NONE, CW_BC_DIRICHLET0 = 0, 1
 CW_APPLY_LOCAL, CW_APPLY_ASSEMBLE = 0, 1
 CW_DSS_SUM, CW_DSS_AVERAGE = 0, 1
 CW_CG_F64, CW_CG_IR_F32, CW_CG_IR_BF16, CW_CG_F64_NATIVE = 0, 1, 2, 3
+CW_BATCH_GROUPED, CW_BATCH_SINGLE = 0, 1
 
 # exported symbols declared in include/cwfem.h (checked by the CPU test suite)
 EXPORTED = [
     "cw_status_string", "cw_last_error", "cw_mesh_create", "cw_mesh_destroy", "cw_op_create",
     "cw_op_destroy", "cw_op_cellwise_len", "cw_op_global_len", "cw_op_device_bytes", "cw_gather",
     "cw_apply", "cw_dss", "cw_diagonal", "cw_load_vector", "cw_cg_solve", "cw_op_set_variant",
-    "cw_op_get_variant", "cw_op_autotune", "cw_cg_solve_noalloc",
+    "cw_op_get_variant", "cw_op_autotune", "cw_cg_solve_noalloc", "cw_batch_create", "cw_batch_destroy",
+    "cw_batch_values", "cw_batch_launch", "cw_batch_graph_launch", "cw_batch_set_variant",
+    "cw_batch_get_variant", "cw_batch_autotune", "cw_batch_set_mode",
 ]
 
 
@@ -81,6 +84,16 @@ def load(path: str = LIB_PATH):
         "cw_op_get_variant": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "cw_op_autotune": ([vp, vp, vp, i32, vp, ctypes.POINTER(ctypes.c_float)], i32),
         "cw_cg_solve_noalloc": ([vp, vp, vp, dbl, i32, i32, ctypes.POINTER(cw_cg_stats), vp], i32),
+        "cw_batch_create": ([ctypes.POINTER(vp), ctypes.POINTER(i32), ctypes.POINTER(vp), ctypes.POINTER(vp), i32,
+                             ctypes.POINTER(vp)], i32),
+        "cw_batch_destroy": ([vp], i32),
+        "cw_batch_values": ([vp], i64),
+        "cw_batch_launch": ([vp, vp], i32),
+        "cw_batch_graph_launch": ([vp, vp], i32),
+        "cw_batch_set_variant": ([vp, i32, i32], i32),
+        "cw_batch_get_variant": ([vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+        "cw_batch_autotune": ([vp, i32, vp, ctypes.POINTER(ctypes.c_float)], i32),
+        "cw_batch_set_mode": ([vp, i32], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -202,6 +215,52 @@ def cw_op_autotune(op, x, y, reps=5, stream=None):
     return ms.value
 
 
+def cw_batch_create(ops, nrhs, xs, ys):
+    n = len(ops)
+    VP = ctypes.c_void_p * n
+    h = ctypes.c_void_p()
+    _check(load().cw_batch_create(VP(*[o.value if isinstance(o, ctypes.c_void_p) else o for o in ops]),
+                                  (ctypes.c_int * n)(*nrhs), VP(*[_ptr(x).value for x in xs]),
+                                  VP(*[_ptr(y).value for y in ys]), n, ctypes.byref(h)), "cw_batch_create")
+    return h
+
+
+def cw_batch_destroy(b):
+    _check(load().cw_batch_destroy(b), "cw_batch_destroy")
+
+
+def cw_batch_values(b):
+    return load().cw_batch_values(b)
+
+
+def cw_batch_launch(b, stream=None):
+    _check(load().cw_batch_launch(b, _stream(stream)), "cw_batch_launch")
+
+
+def cw_batch_graph_launch(b, stream=None):
+    _check(load().cw_batch_graph_launch(b, _stream(stream)), "cw_batch_graph_launch")
+
+
+def cw_batch_set_mode(b, mode):
+    _check(load().cw_batch_set_mode(b, mode), "cw_batch_set_mode")
+
+
+def cw_batch_set_variant(b, degree, variant):
+    _check(load().cw_batch_set_variant(b, degree, variant), "cw_batch_set_variant")
+
+
+def cw_batch_get_variant(b, degree):
+    h, c = ctypes.c_int(), ctypes.c_int()
+    _check(load().cw_batch_get_variant(b, degree, ctypes.byref(h), ctypes.byref(c)), "cw_batch_get_variant")
+    return h.value, c.value
+
+
+def cw_batch_autotune(b, reps=3, stream=None):
+    ms = ctypes.c_float()
+    _check(load().cw_batch_autotune(b, reps, _stream(stream), ctypes.byref(ms)), "cw_batch_autotune")
+    return ms.value
+
+
 # ------------------------------------------------------------------ convenience ----
 _VEC_DTYPE = {CW_PREC_F64: "float64", CW_PREC_F64_NATIVE: "float64", CW_PREC_F32: "float32",
               CW_PREC_F32_BF16G: "float32", CW_PREC_BF16: "bfloat16"}
@@ -294,6 +353,41 @@ class Operator:
     def close(self):
         if self.handle:
             cw_op_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owns a cw_batch handle; keeps references to its operators and vectors."""
+
+    def __init__(self, ops, nrhs, xs, ys):
+        self.ops, self.nrhs, self.xs, self.ys = list(ops), list(nrhs), list(xs), list(ys)
+        self.handle = cw_batch_create([o.handle for o in self.ops], self.nrhs, self.xs, self.ys)
+        self.values = cw_batch_values(self.handle)
+
+    def launch(self, graph=False, stream=None):
+        (cw_batch_graph_launch if graph else cw_batch_launch)(self.handle, stream)
+
+    def autotune(self, reps=3):
+        return cw_batch_autotune(self.handle, reps)
+
+    def set_mode(self, mode):
+        cw_batch_set_mode(self.handle, mode)
+
+    def set_variant(self, degree, variant):
+        cw_batch_set_variant(self.handle, degree, variant)
+
+    def variant(self, degree):
+        return cw_batch_get_variant(self.handle, degree)
+
+    def close(self):
+        if self.handle:
+            cw_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -95,27 +95,30 @@ __host__ __device__ constexpr size_t metric_smem_bytes(int nc, bool stage)
                  : 3 * CPB * Lines<N>::CS * sizeof(T);
 }
 
+// One tile of `cpt` consecutive cells starting at cell tile*cpt, worked by CPB cell slots of N*N
+// threads (cpt <= CPB; slots c >= cpt compute on zeros and store nothing, so a CTA may have more
+// threads than the tile needs). STAGE (cpt == CPB only): TMA staging of the x and metric tiles.
 template <int N, int CPB, class Ar, class VS, class GS, bool STAGE>
-__global__ void __launch_bounds__(N *N *CPB) apply_metric_kernel(const VS *__restrict__ x, VS *__restrict__ y,
-                                                                  const GS *__restrict__ geo, int64_t ncells,
-                                                                  int kind, TabMetric<N, typename Ar::C> tab)
+__device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__restrict__ y, const GS *__restrict__ geo,
+                                            int64_t ncells, int kind, const TabMetric<N, typename Ar::C> &tab,
+                                            int64_t tile, int cpt, unsigned char *smem_raw)
 {
     using T = typename Ar::T;
     using L = Lines<N>;
     constexpr int N2 = N * N, N3 = N2 * N, CS = L::CS;
     const bool HAS_K = (kind & 1) != 0, HAS_M = (kind & 2) != 0;
     const int NC = metric_ncomp(kind);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *S0 = reinterpret_cast<T *>(smem_raw);
-    const int t = threadIdx.x, c = t / N2, r = t - c * N2, ra = r % N, rb = r / N;
-    const int64_t cell0 = static_cast<int64_t>(blockIdx.x) * CPB;
+    const int t = threadIdx.x;
+    const int c = t / N2, r = t - c * N2, ra = r % N, rb = r / N;
+    const int64_t cell0 = tile * cpt;
     const int64_t cell = cell0 + c;
-    const bool act = cell < ncells;
+    const bool act = c < cpt && cell < ncells;
     T *s0 = S0 + c * CS;
     T *s1 = S0 + (CPB + c) * CS;
     T *s2 = S0 + (2 * CPB + c) * CS;
 
-    // ---- tile staging
+    // ---- tile staging (single right-hand side)
     bool x_smem = false, g_smem = false;
     const VS *xs = nullptr;
     const GS *gs = nullptr;
@@ -149,110 +152,134 @@ __global__ void __launch_bounds__(N *N *CPB) apply_metric_kernel(const VS *__res
         }
     }
 
-    T v[N], w[N];
-    // (1) x-line (j,k) = (ra, rb): N contiguous values of the cell, contracted with B along x
     {
-        if (x_smem) {
+        const VS *xr = x;
+        VS *yr = y;
+        T v[N], w[N], u[N], acc[N], gx[N], gy[N], gz[N];
+        // (1) x-line (j,k) = (ra, rb): N contiguous values of the cell, contracted with B along x
+        {
+            if (x_smem) {
 #pragma unroll
-            for (int m = 0; m < N; ++m) v[m] = Ar::from(xs[N * r + m]);
-        } else {
-            const VS *xc = x + (act ? cell : 0) * N3 + N * r;
+                for (int m = 0; m < N; ++m) v[m] = Ar::from(xs[N * r + m]);
+            } else {
+                const VS *xc = xr + (act ? cell : 0) * N3 + N * r;
 #pragma unroll
-            for (int m = 0; m < N; ++m) v[m] = act ? Ar::from(ldg_nc(xc + m)) : Ar::zero();
-        }
-        contract<N, false, Ar>(tab.B, v, w);
-        CW_STX(s0, w);
-    }
-    __syncthreads();
-    // (2) y-line (i,k): contract with B along y, in place
-    CW_LDY(s0, v);
-    contract<N, false, Ar>(tab.B, v, w);
-    CW_STY(s0, w);
-    __syncthreads();
-    // (3) z-pencil (i,j): contract with B along z -> u at the Gauss points (registers)
-    T u[N], acc[N];
-    CW_LDZ(s0, v);
-    contract<N, false, Ar>(tab.B, v, u);
-    T gx[N], gy[N], gz[N];
-    if (HAS_K) {
-        contract<N, false, Ar>(tab.D, u, gz);
-        CW_STZ(s0, u);
-        __syncthreads();
-        // x- and y-derivatives by collocation, as line owners
-        CW_LDX(s0, v);
-        contract<N, false, Ar>(tab.D, v, w);
-        CW_STX(s1, w);
-        CW_LDY(s0, v);
-        contract<N, false, Ar>(tab.D, v, w);
-        CW_STY(s2, w);
-        __syncthreads();
-        CW_LDZ(s1, gx);
-        CW_LDZ(s2, gy);
-    }
-    // (4) quadrature-point physics on the owned pencil, qp = (ra, rb, k)
-    if constexpr (STAGE) {
-        if (g_smem) g_smem = mbar_wait_bounded(bar + 1, 0);
-    }
-    {
-        const GS *gc = g_smem ? gs + r : geo + (act ? cell : 0) * (NC * N3) + r;
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            const GS *g = gc + N2 * k;
-            if (HAS_K) {
-                const T gxx = Ar::from(g[0 * N3]), gyy = Ar::from(g[1 * N3]);
-                const T gzz = Ar::from(g[2 * N3]), gxy = Ar::from(g[3 * N3]);
-                const T gxz = Ar::from(g[4 * N3]), gyz = Ar::from(g[5 * N3]);
-                T hx = Ar::mul(gx[k], gxx), hy = Ar::mul(gx[k], gxy), hz = Ar::mul(gx[k], gxz);
-                Ar::mad(hx, gy[k], gxy);
-                Ar::mad(hy, gy[k], gyy);
-                Ar::mad(hz, gy[k], gyz);
-                Ar::mad(hx, gz[k], gxz);
-                Ar::mad(hy, gz[k], gyz);
-                Ar::mad(hz, gz[k], gzz);
-                gx[k] = Ar::norm(hx);
-                gy[k] = Ar::norm(hy);
-                gz[k] = Ar::norm(hz);
+                for (int m = 0; m < N; ++m) v[m] = act ? Ar::from(ldg_nc(xc + m)) : Ar::zero();
             }
-            if (HAS_M) {
-                const T cm = Ar::from(g[(NC - 1) * N3]);
-                acc[k] = Ar::norm(Ar::mul(u[k], cm));
+            contract<N, false, Ar>(tab.B, v, w);
+            CW_STX(s0, w);
+        }
+        __syncthreads();
+        // (2) y-line (i,k): contract with B along y, in place
+        {
+            CW_LDY(s0, v);
+            contract<N, false, Ar>(tab.B, v, w);
+            CW_STY(s0, w);
+        }
+        __syncthreads();
+        // (3) z-pencil (i,j): contract with B along z -> u at the Gauss points (registers)
+        {
+            CW_LDZ(s0, v);
+            contract<N, false, Ar>(tab.B, v, u);
+        }
+        if (HAS_K) {
+            {
+                contract<N, false, Ar>(tab.D, u, gz);
+                CW_STZ(s0, u);
+            }
+            __syncthreads();
+            // x- and y-derivatives by collocation, as line owners
+            {
+                CW_LDX(s0, v);
+                contract<N, false, Ar>(tab.D, v, w);
+                CW_STX(s1, w);
+                CW_LDY(s0, v);
+                contract<N, false, Ar>(tab.D, v, w);
+                CW_STY(s2, w);
+            }
+            __syncthreads();
+            {
+                CW_LDZ(s1, gx);
+                CW_LDZ(s2, gy);
             }
         }
-    }
-    if (HAS_K) {
-        // z-part of the transposed derivative in registers, x/y parts as line owners
-        contract<N, true, Ar>(tab.D, gz, v);
+        // (4) quadrature-point physics on the owned pencil, qp = (ra, rb, k)
+        if constexpr (STAGE) {
+            if (g_smem) g_smem = mbar_wait_bounded(bar + 1, 0);
+        }
+        {
+            const GS *gc = g_smem ? gs + r : geo + (act ? cell : 0) * (NC * N3) + r;
 #pragma unroll
-        for (int k = 0; k < N; ++k) acc[k] = HAS_M ? Ar::add(acc[k], v[k]) : v[k];
-        CW_STZ(s1, gx);  // own pencil only: no other thread reads s1/s2 pencils now
-        CW_STZ(s2, gy);
+            for (int k = 0; k < N; ++k) {
+                const GS *g = gc + N2 * k;
+                if (HAS_K) {
+                    const T gxx = Ar::from(g[0 * N3]), gyy = Ar::from(g[1 * N3]);
+                    const T gzz = Ar::from(g[2 * N3]), gxy = Ar::from(g[3 * N3]);
+                    const T gxz = Ar::from(g[4 * N3]), gyz = Ar::from(g[5 * N3]);
+                    T hx = Ar::mul(gx[k], gxx), hy = Ar::mul(gx[k], gxy), hz = Ar::mul(gx[k], gxz);
+                    Ar::mad(hx, gy[k], gxy);
+                    Ar::mad(hy, gy[k], gyy);
+                    Ar::mad(hz, gy[k], gyz);
+                    Ar::mad(hx, gz[k], gxz);
+                    Ar::mad(hy, gz[k], gyz);
+                    Ar::mad(hz, gz[k], gzz);
+                    gx[k] = Ar::norm(hx);
+                    gy[k] = Ar::norm(hy);
+                    gz[k] = Ar::norm(hz);
+                }
+                if (HAS_M) {
+                    const T cm = Ar::from(g[(NC - 1) * N3]);
+                    acc[k] = Ar::norm(Ar::mul(u[k], cm));
+                }
+            }
+        }
+        if (HAS_K) {
+            // z-part of the transposed derivative in registers, x/y parts as line owners
+            {
+                contract<N, true, Ar>(tab.D, gz, v);
+#pragma unroll
+                for (int k = 0; k < N; ++k) acc[k] = HAS_M ? Ar::add(acc[k], v[k]) : v[k];
+                CW_STZ(s1, gx);  // own pencil only: no other thread reads s1/s2 pencils now
+                CW_STZ(s2, gy);
+            }
+            __syncthreads();
+            {
+                CW_LDX(s1, v);
+                contract<N, true, Ar>(tab.D, v, w);
+                CW_STX(s1, w);
+                CW_LDY(s2, v);
+                contract<N, true, Ar>(tab.D, v, w);
+                CW_STY(s2, w);
+            }
+            __syncthreads();
+            {
+                CW_LDZ(s1, v);
+                CW_LDZ(s2, w);
+#pragma unroll
+                for (int k = 0; k < N; ++k) acc[k] = Ar::norm(Ar::add(acc[k], Ar::add(v[k], w[k])));
+            }
+        }
+        // (5) integrate back: B^T along z (registers), y and x as line owners
+        {
+            contract<N, true, Ar>(tab.B, acc, w);
+            CW_STZ(s0, w);
+        }
         __syncthreads();
-        CW_LDX(s1, v);
-        contract<N, true, Ar>(tab.D, v, w);
-        CW_STX(s1, w);
-        CW_LDY(s2, v);
-        contract<N, true, Ar>(tab.D, v, w);
-        CW_STY(s2, w);
+        {
+            CW_LDY(s0, v);
+            contract<N, true, Ar>(tab.B, v, w);
+            CW_STY(s0, w);
+        }
         __syncthreads();
-        CW_LDZ(s1, v);
-        CW_LDZ(s2, w);
+        {
+            CW_LDX(s0, v);
+            contract<N, true, Ar>(tab.B, v, w);
+            if (act) {
+                VS *yc = yr + cell * N3 + N * r;
 #pragma unroll
-        for (int k = 0; k < N; ++k) acc[k] = Ar::norm(Ar::add(acc[k], Ar::add(v[k], w[k])));
-    }
-    // (5) integrate back: B^T along z (registers), y and x as line owners
-    contract<N, true, Ar>(tab.B, acc, w);
-    CW_STZ(s0, w);
-    __syncthreads();
-    CW_LDY(s0, v);
-    contract<N, true, Ar>(tab.B, v, w);
-    CW_STY(s0, w);
-    __syncthreads();
-    CW_LDX(s0, v);
-    contract<N, true, Ar>(tab.B, v, w);
-    if (act) {
-        VS *yc = y + cell * N3 + N * r;
-#pragma unroll
-        for (int m = 0; m < N; ++m) Ar::to(yc[m], w[m]);
+                for (int m = 0; m < N; ++m) Ar::to(yc[m], w[m]);
+            }
+        }
     }
     if constexpr (STAGE) {
         // a copy that missed its wait bound must not land in shared memory after exit
@@ -261,6 +288,15 @@ __global__ void __launch_bounds__(N *N *CPB) apply_metric_kernel(const VS *__res
             mbar_wait_bounded(bar + 1, 0);
         }
     }
+}
+
+template <int N, int CPB, class Ar, class VS, class GS, bool STAGE>
+__global__ void __launch_bounds__(N *N *CPB) apply_metric_kernel(const VS *__restrict__ x, VS *__restrict__ y,
+                                                                  const GS *__restrict__ geo, int64_t ncells,
+                                                                  int kind, TabMetric<N, typename Ar::C> tab)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    metric_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw);
 }
 
 // ---------------------------------------------------------------------- Cartesian kernel ----

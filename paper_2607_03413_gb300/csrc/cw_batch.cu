@@ -1,0 +1,302 @@
+// cw_batch.cu -- C ABI of the batched apply: many operators (uneven meshes, mixed degrees,
+// several right-hand sides each) applied by persistent work-queue kernels, optionally replayed
+// from a captured CUDA graph, with the kernel variant of each degree picked by an autotuner.
+// Two modes: CW_BATCH_GROUPED (default) runs one persistent kernel per degree present, each shaped
+// like the tuned per-operator kernel; CW_BATCH_SINGLE runs every degree in one persistent kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "cw_batch.cuh"
+
+namespace cw {
+
+struct Batch {
+    std::vector<Op *> ops;  // sorted by degree (stable)
+    std::vector<int> nrhs;
+    std::vector<const void *> x;
+    std::vector<void *> y;
+    int fp64 = 1;  // 1: CW_PREC_F64 (double-float), 0: CW_PREC_F32
+    int mode = CW_BATCH_GROUPED;
+    int half[9] = {0};     // single mode: half tile per n
+    int variant[9] = {0};  // grouped mode: cells-per-CTA choice + 2 * staging, per n
+    std::vector<BatchProb> h_probs;
+    BatchProb *d_probs = nullptr;
+    unsigned long long *d_counter = nullptr;  // [9]: single mode uses [0], grouped mode [n]
+    int64_t nitems = 0, values = 0;
+    int64_t g_first[9] = {0}, g_count[9] = {0}, g_items[9] = {0};  // grouped: problems and items per n
+    int g_kind[9] = {0};                                              // grouped: largest kind per n
+    const Tables1D *tabs[9] = {nullptr};
+    size_t smem = 0;
+    int grid = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+};
+
+static cw_status batch_rebuild(Batch &b)
+{
+    b.h_probs.resize(b.ops.size());
+    int64_t item = 0;
+    b.values = 0;
+    size_t smem = 0;
+    for (int n = 0; n < 9; ++n) {
+        b.g_first[n] = b.g_count[n] = b.g_items[n] = 0;
+        b.g_kind[n] = 0;
+    }
+    for (size_t i = 0; i < b.ops.size(); ++i) {
+        const Op &o = *b.ops[i];
+        BatchProb &P = b.h_probs[i];
+        P.x = b.x[i];
+        P.y = b.y[i];
+        P.geo = o.d_geo;
+        P.ncells = o.E;
+        P.stride = o.L;
+        P.n = o.n;
+        P.kind = o.kind;
+        P.nrhs = b.nrhs[i];
+        P.cpt = b.mode == CW_BATCH_SINGLE ? batch_cpt(o.n, b.half[o.n]) : degree_cpb(o.n, b.variant[o.n] & 1);
+        P.ntiles = (o.E + P.cpt - 1) / P.cpt;
+        P.tpi = std::max(1, kItemValues / (P.cpt * o.n * o.n * o.n));
+        if (b.mode == CW_BATCH_GROUPED && b.g_count[o.n] == 0) {  // items restart per degree group
+            b.g_first[o.n] = (int64_t)i;
+            item = 0;
+        }
+        P.item0 = item;
+        item += (P.ntiles + P.tpi - 1) / P.tpi * P.nrhs;
+        b.values += o.L * b.nrhs[i];
+        b.g_count[o.n] += 1;
+        b.g_items[o.n] = item;
+        b.g_kind[o.n] = (b.g_kind[o.n] | o.kind);
+        smem = std::max(smem, b.fp64 ? batch_smem_bytes<df64>(o.n) : batch_smem_bytes<float>(o.n));
+    }
+    b.nitems = item;
+    b.smem = smem;
+    if (b.mode == CW_BATCH_SINGLE) {
+        int per_sm = 0, dev = 0, sms = 0;
+        CW_CUDA_TRY(b.fp64 ? batch_occupancy_df(smem, &per_sm) : batch_occupancy_f32(smem, &per_sm));
+        CW_CUDA_TRY(cudaGetDevice(&dev));
+        CW_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (per_sm < 1) return fail(CW_ERR_UNSUPPORTED, "cw_batch: kernel does not fit on an SM");
+        b.grid = sms * per_sm;
+    }
+    CW_CUDA_TRY(cudaMemcpy(b.d_probs, b.h_probs.data(), b.h_probs.size() * sizeof(BatchProb), cudaMemcpyHostToDevice));
+    if (b.graph) {
+        cudaGraphExecDestroy(b.graph);
+        b.graph = nullptr;
+    }
+    return CW_OK;
+}
+
+static cudaError_t batch_enqueue(const Batch &b, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(b.d_counter, 0, 9 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    if (b.mode == CW_BATCH_SINGLE)
+        return b.fp64 ? batch_launch_df(b.d_probs, (int)b.h_probs.size(), b.nitems, b.d_counter, b.smem, b.grid, s)
+                      : batch_launch_f32(b.d_probs, (int)b.h_probs.size(), b.nitems, b.d_counter, b.smem, b.grid, s);
+    for (int n = 2; n <= 8; ++n) {
+        if (!b.g_count[n]) continue;
+        const int v = b.variant[n];
+        const int kmax = (b.g_kind[n] & 1) ? 3 : 2;  // metric components of the largest kind present
+        e = b.fp64 ? batch_degree_launch_df(n, v & 1, v >> 1, *b.tabs[n], b.d_probs + b.g_first[n], (int)b.g_count[n],
+                                            b.g_items[n], b.d_counter + n, kmax, s)
+                   : batch_degree_launch_f32(n, v & 1, v >> 1, *b.tabs[n], b.d_probs + b.g_first[n], (int)b.g_count[n],
+                                             b.g_items[n], b.d_counter + n, kmax, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace cw
+
+using namespace cw;
+
+extern "C" {
+
+cw_status cw_batch_create(const cw_op *ops, const int *nrhs, const void *const *x, void *const *y, int nprob,
+                          cw_batch *out)
+{
+    if (!out) return fail(CW_ERR_ARG, "cw_batch_create: out is NULL");
+    *out = nullptr;
+    if (!ops || !nrhs || !x || !y || nprob < 1) return fail(CW_ERR_ARG, "cw_batch_create: NULL array or nprob < 1");
+    Batch *b = new Batch;
+    const Tables1D *tabs[9] = {nullptr};
+    std::vector<int> order(nprob);
+    for (int i = 0; i < nprob; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        const Op *oa = reinterpret_cast<const Op *>(ops[a]), *oc = reinterpret_cast<const Op *>(ops[c]);
+        return (oa ? oa->n : 0) < (oc ? oc->n : 0);
+    });
+    for (int k = 0; k < nprob; ++k) {
+        const int i = order[k];
+        Op *o = reinterpret_cast<Op *>(ops[i]);
+        if (!o || !x[i] || !y[i] || nrhs[i] < 1) {
+            delete b;
+            return fail(CW_ERR_ARG, "cw_batch_create: NULL operator or vector, or nrhs < 1");
+        }
+        if (o->geom != CW_GEOM_METRIC || (o->prec != CW_PREC_F64 && o->prec != CW_PREC_F32)) {
+            delete b;
+            return fail(CW_ERR_UNSUPPORTED, "cw_batch_create: operators must be CW_GEOM_METRIC, CW_PREC_F64 or CW_PREC_F32");
+        }
+        const int f = o->prec == CW_PREC_F64;
+        if (k == 0) b->fp64 = f;
+        if (f != b->fp64) {
+            delete b;
+            return fail(CW_ERR_ARG, "cw_batch_create: all operators must share one precision");
+        }
+        if (x[i] == y[i]) {
+            delete b;
+            return fail(CW_ERR_ARG, "cw_batch_create: x and y must not alias");
+        }
+        b->ops.push_back(o);
+        b->nrhs.push_back(nrhs[i]);
+        b->x.push_back(x[i]);
+        b->y.push_back(y[i]);
+        tabs[o->n] = &o->tab;
+        b->tabs[o->n] = &o->tab;
+    }
+    cudaError_t e = b->fp64 ? batch_upload_tables_df(tabs) : batch_upload_tables_f32(tabs);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_probs, nprob * sizeof(BatchProb));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 9 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaFree(b->d_probs);
+        cudaFree(b->d_counter);
+        delete b;
+        return cuda_fail(e, "cw_batch_create");
+    }
+    cw_status st = batch_rebuild(*b);
+    if (st != CW_OK) {
+        cudaFree(b->d_probs);
+        cudaFree(b->d_counter);
+        cudaStreamDestroy(b->cap_stream);
+        delete b;
+        return st;
+    }
+    *out = reinterpret_cast<cw_batch>(b);
+    return CW_OK;
+}
+
+cw_status cw_batch_destroy(cw_batch bh)
+{
+    Batch *b = reinterpret_cast<Batch *>(bh);
+    if (!b) return fail(CW_ERR_ARG, "cw_batch_destroy: NULL");
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->d_probs);
+    cudaFree(b->d_counter);
+    cudaStreamDestroy(b->cap_stream);
+    delete b;
+    return CW_OK;
+}
+
+int64_t cw_batch_values(cw_batch bh)
+{
+    Batch *b = reinterpret_cast<Batch *>(bh);
+    return b ? b->values : -1;
+}
+
+cw_status cw_batch_set_mode(cw_batch bh, int mode)
+{
+    Batch *b = reinterpret_cast<Batch *>(bh);
+    if (!b || (mode != CW_BATCH_GROUPED && mode != CW_BATCH_SINGLE))
+        return fail(CW_ERR_ARG, "cw_batch_set_mode: NULL handle or unknown mode");
+    b->mode = mode;
+    return batch_rebuild(*b);
+}
+
+static int variant_count(const Batch &b) { return b.mode == CW_BATCH_SINGLE ? 2 : 4; }
+
+cw_status cw_batch_set_variant(cw_batch bh, int degree, int variant)
+{
+    Batch *b = reinterpret_cast<Batch *>(bh);
+    if (!b || degree < 1 || degree > kMaxDegree || variant < 0 || variant >= variant_count(*b))
+        return fail(CW_ERR_ARG, "cw_batch_set_variant: NULL handle, degree outside 1..7 or variant out of range");
+    if (b->mode == CW_BATCH_SINGLE) b->half[degree + 1] = variant;
+    else b->variant[degree + 1] = variant;
+    return batch_rebuild(*b);
+}
+
+cw_status cw_batch_get_variant(cw_batch bh, int degree, int *variant, int *cells_per_tile)
+{
+    Batch *b = reinterpret_cast<Batch *>(bh);
+    if (!b || degree < 1 || degree > kMaxDegree) return fail(CW_ERR_ARG, "cw_batch_get_variant: bad arguments");
+    const int n = degree + 1;
+    if (variant) *variant = b->mode == CW_BATCH_SINGLE ? b->half[n] : b->variant[n];
+    if (cells_per_tile)
+        *cells_per_tile = b->mode == CW_BATCH_SINGLE ? batch_cpt(n, b->half[n]) : degree_cpb(n, b->variant[n] & 1);
+    return CW_OK;
+}
+
+cw_status cw_batch_launch(cw_batch bh, void *stream)
+{
+    Batch *b = reinterpret_cast<Batch *>(bh);
+    if (!b) return fail(CW_ERR_ARG, "cw_batch_launch: NULL handle");
+    CW_CUDA_TRY(batch_enqueue(*b, static_cast<cudaStream_t>(stream)));
+    return CW_OK;
+}
+
+cw_status cw_batch_graph_launch(cw_batch bh, void *stream)
+{
+    Batch *b = reinterpret_cast<Batch *>(bh);
+    if (!b) return fail(CW_ERR_ARG, "cw_batch_graph_launch: NULL handle");
+    if (!b->graph) {
+        cudaGraph_t g;
+        CW_CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = batch_enqueue(*b, b->cap_stream);
+        cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+        if (e != cudaSuccess) return cuda_fail(e, "cw_batch_graph_launch capture");
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cw_batch_graph_launch end capture");
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "cw_batch_graph_launch instantiate");
+    }
+    CW_CUDA_TRY(cudaGraphLaunch(b->graph, static_cast<cudaStream_t>(stream)));
+    return CW_OK;
+}
+
+cw_status cw_batch_autotune(cw_batch bh, int reps, void *stream, float *best_ms)
+{
+    Batch *b = reinterpret_cast<Batch *>(bh);
+    if (!b || reps < 1) return fail(CW_ERR_ARG, "cw_batch_autotune: NULL handle or reps < 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    bool present[9] = {false};
+    for (Op *o : b->ops) present[o->n] = true;
+    cudaEvent_t e0, e1;
+    CW_CUDA_TRY(cudaEventCreate(&e0));
+    CW_CUDA_TRY(cudaEventCreate(&e1));
+    float best_all = 0.0f;
+    for (int n = 2; n <= 8; ++n) {  // coordinate descent over the degrees present
+        if (!present[n]) continue;
+        float best = 1e30f;
+        int bh_ = 0;
+        int *knob = b->mode == CW_BATCH_SINGLE ? &b->half[n] : &b->variant[n];
+        for (int h = 0; h < variant_count(*b); ++h) {
+            *knob = h;
+            cw_status st = batch_rebuild(*b);
+            if (st != CW_OK) return st;
+            CW_CUDA_TRY(batch_enqueue(*b, s));  // warm-up
+            CW_CUDA_TRY(cudaEventRecord(e0, s));
+            for (int r = 0; r < reps; ++r) CW_CUDA_TRY(batch_enqueue(*b, s));
+            CW_CUDA_TRY(cudaEventRecord(e1, s));
+            CW_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            CW_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            ms /= reps;
+            if (ms < best) {
+                best = ms;
+                bh_ = h;
+            }
+        }
+        *knob = bh_;
+        best_all = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cw_status st = batch_rebuild(*b);
+    if (best_ms) *best_ms = best_all;
+    return st;
+}
+
+}  // extern "C"

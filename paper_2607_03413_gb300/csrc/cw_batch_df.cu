@@ -1,0 +1,116 @@
+// Persistent batched apply, double-float arithmetic on FP64 vectors and metric.
+#include "cw_batch.cuh"
+#include "cw_launch.cuh"
+
+#include <algorithm>
+
+namespace cw {
+
+__constant__ BatchTables<df64> c_batch_tabs_df;
+
+__global__ void __launch_bounds__(kBatchThreads, 4) batch_kernel_df(const BatchProb *__restrict__ probs, int nprob,
+                                                                   int64_t nitems, unsigned long long *__restrict__ counter)
+{
+    batch_body<ArDF, double, double>(probs, nprob, nitems, counter, c_batch_tabs_df);
+}
+
+static df64 mk(double v) { return df64{static_cast<float>(v), static_cast<float>(v - static_cast<double>(static_cast<float>(v)))}; }
+
+template <int N>
+static void fill(TabMetric<N, df64> &t, const Tables1D *tb)
+{
+    if (!tb) return;
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+            t.B[a][b] = mk(tb->B[a][b]);
+            t.D[a][b] = mk(tb->D[a][b]);
+        }
+}
+
+cudaError_t batch_upload_tables_df(const Tables1D *const tabs[9])
+{
+    BatchTables<df64> h{};
+    fill<2>(h.t2, tabs[2]);
+    fill<3>(h.t3, tabs[3]);
+    fill<4>(h.t4, tabs[4]);
+    fill<5>(h.t5, tabs[5]);
+    fill<6>(h.t6, tabs[6]);
+    fill<7>(h.t7, tabs[7]);
+    fill<8>(h.t8, tabs[8]);
+    return cudaMemcpyToSymbol(c_batch_tabs_df, &h, sizeof h);
+}
+
+cudaError_t batch_occupancy_df(size_t smem, int *blocks_per_sm)
+{
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(batch_kernel_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel_df, kBatchThreads, smem);
+}
+
+cudaError_t batch_launch_df(const BatchProb *d_probs, int nprob, int64_t nitems, unsigned long long *counter,
+                            size_t smem, int grid, cudaStream_t s)
+{
+    batch_kernel_df<<<grid, kBatchThreads, smem, s>>>(d_probs, nprob, nitems, counter);
+    return cudaGetLastError();
+}
+
+template <int N, int CPB, bool STAGE>
+static cudaError_t grouped(const Tables1D &tb, const BatchProb *d_probs, int nprob, int64_t nitems,
+                           unsigned long long *counter, int kind_max, cudaStream_t s)
+{
+    TabMetric<N, df64> tab;
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+            tab.B[a][b] = mk(tb.B[a][b]);
+            tab.D[a][b] = mk(tb.D[a][b]);
+        }
+    // shared memory for the largest metric of the group (kind_max components)
+    const size_t smem = metric_smem_bytes<N, CPB, typename ArDF::T, double>(metric_ncomp(kind_max), STAGE);
+    auto kern = batch_degree_kernel<N, CPB, ArDF, double, double, STAGE>;
+    static size_t opted = 0;
+    static int per_sm = 0;
+    if (smem > opted) {
+        cudaError_t e = opt_in_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        opted = smem;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, N * N * CPB, smem);
+        if (e != cudaSuccess) return e;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t grid = std::min<int64_t>(std::max(1, per_sm) * (int64_t)sms, nitems);
+    kern<<<(unsigned)std::max<int64_t>(grid, 1), N * N * CPB, smem, s>>>(d_probs, nprob, nitems, counter, tab);
+    return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t grouped_n(int alt, int stage, const Tables1D &tb, const BatchProb *d_probs, int nprob,
+                             int64_t nitems, unsigned long long *counter, int kind_max, cudaStream_t s)
+{
+    constexpr int D = cpb_default<N>(), A = cpb_alt<N>();
+    if (alt) return stage ? grouped<N, A, true>(tb, d_probs, nprob, nitems, counter, kind_max, s)
+                          : grouped<N, A, false>(tb, d_probs, nprob, nitems, counter, kind_max, s);
+    return stage ? grouped<N, D, true>(tb, d_probs, nprob, nitems, counter, kind_max, s)
+                 : grouped<N, D, false>(tb, d_probs, nprob, nitems, counter, kind_max, s);
+}
+
+cudaError_t batch_degree_launch_df(int n, int cpb_alt, int stage, const Tables1D &tb, const BatchProb *d_probs,
+                                   int nprob, int64_t nitems, unsigned long long *counter, int kind_max,
+                                   cudaStream_t s)
+{
+    switch (n) {
+    case 2: return grouped_n<2>(cpb_alt, stage, tb, d_probs, nprob, nitems, counter, kind_max, s);
+    case 3: return grouped_n<3>(cpb_alt, stage, tb, d_probs, nprob, nitems, counter, kind_max, s);
+    case 4: return grouped_n<4>(cpb_alt, stage, tb, d_probs, nprob, nitems, counter, kind_max, s);
+    case 5: return grouped_n<5>(cpb_alt, stage, tb, d_probs, nprob, nitems, counter, kind_max, s);
+    case 6: return grouped_n<6>(cpb_alt, stage, tb, d_probs, nprob, nitems, counter, kind_max, s);
+    case 7: return grouped_n<7>(cpb_alt, stage, tb, d_probs, nprob, nitems, counter, kind_max, s);
+    case 8: return grouped_n<8>(cpb_alt, stage, tb, d_probs, nprob, nitems, counter, kind_max, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace cw
