@@ -23,10 +23,27 @@
 
 namespace cw {
 
+// Even-odd form of an N x N matrix M with reflection symmetry M[N-1-a][N-1-b] = s M[a][b]
+// (s = +1 for B and B^T, -1 for D and D^T; the Gauss and Gauss-Lobatto points are symmetric about
+// 1/2). With e_b = x_b + x_{N-1-b}, o_b = x_b - x_{N-1-b} (b < N/2) and, for odd N, the middle
+// entry x_h:  y_a = sum_b E[a][b] e_b + sum_b O[a][b] o_b + Mid[a] x_h  and
+// y_{N-1-a} = s (sum_b E[a][b] e_b - sum_b O[a][b] o_b + Mid[a] x_h), for a < (N+1)/2, where
+// E[a][b] = (M[a][b] + M[a][N-1-b])/2, O[a][b] = (M[a][b] - M[a][N-1-b])/2, Mid[a] = M[a][h].
+// This halves the multiply-adds of a line contraction (Kronbichler and Kormann's even-odd
+// decomposition for sum factorisation).
+template <int N, class C>
+struct EOMat {
+    static constexpr int H = N / 2, NA = (N + 1) / 2;
+    C E[NA][H > 0 ? H : 1];
+    C O[NA][H > 0 ? H : 1];
+    C Mid[NA];
+};
+
 template <int N, class C>
 struct TabMetric {
     C B[N][N];  // B[q][m] = l_m(xi_q): Gauss-Lobatto basis at the Gauss points
     C D[N][N];  // D[q][r] = derivative at xi_q of the Lagrange basis on the Gauss points
+    EOMat<N, C> Bf, Bt, Df, Dt;  // even-odd forms of B, B^T (s = +1), D, D^T (s = -1)
 };
 
 template <int N, class C>
@@ -56,6 +73,65 @@ __device__ __forceinline__ void contract(const typename Ar::C (&M)[N][N], const 
 #pragma unroll
         for (int b = 1; b < N; ++b) Ar::mad(s, in[b], TR ? M[b][a] : M[a][b]);
         out[a] = Ar::norm(s);
+    }
+}
+
+// out = M in with M in even-odd form (see EOMat), S = +1 or -1 the reflection sign
+template <int N, int S, class Ar>
+__device__ __forceinline__ void contract_eo(const EOMat<N, typename Ar::C> &M, const typename Ar::T (&in)[N],
+                                            typename Ar::T (&out)[N])
+{
+    using T = typename Ar::T;
+    constexpr int H = N / 2;
+    T e[H], o[H];
+#pragma unroll
+    for (int b = 0; b < H; ++b) {
+        e[b] = Ar::add(in[b], in[N - 1 - b]);
+        o[b] = Ar::sub(in[b], in[N - 1 - b]);
+    }
+#pragma unroll
+    for (int a = 0; a < H; ++a) {
+        T ye = Ar::mul(e[0], M.E[a][0]);
+#pragma unroll
+        for (int b = 1; b < H; ++b) Ar::mad(ye, e[b], M.E[a][b]);
+        if constexpr (N % 2 == 1) Ar::mad(ye, in[H], M.Mid[a]);
+        T yo = Ar::mul(o[0], M.O[a][0]);
+#pragma unroll
+        for (int b = 1; b < H; ++b) Ar::mad(yo, o[b], M.O[a][b]);
+        out[a] = Ar::norm(Ar::add(ye, yo));
+        const T d = Ar::sub(ye, yo);
+        out[N - 1 - a] = Ar::norm(S > 0 ? d : Ar::neg(d));
+    }
+    if constexpr (N % 2 == 1) {  // middle output: only the even (S = +1) or odd (S = -1) part
+        if constexpr (S > 0) {
+            T ye = Ar::mul(in[H], M.Mid[H]);
+#pragma unroll
+            for (int b = 0; b < H; ++b) Ar::mad(ye, e[b], M.E[H][b]);
+            out[H] = Ar::norm(ye);
+        } else {
+            T yo = Ar::mul(o[0], M.O[H][0]);
+#pragma unroll
+            for (int b = 1; b < H; ++b) Ar::mad(yo, o[b], M.O[H][b]);
+            out[H] = Ar::norm(yo);
+        }
+    }
+}
+
+// line contraction with B, B^T, D or D^T: even-odd form from N = 4 up, full form below
+template <int N, class Ar, int WHICH>  // WHICH: 0 B, 1 B^T, 2 D, 3 D^T
+__device__ __forceinline__ void sweep(const TabMetric<N, typename Ar::C> &tab, const typename Ar::T (&in)[N],
+                                      typename Ar::T (&out)[N])
+{
+    if constexpr (N >= 4) {
+        if constexpr (WHICH == 0) contract_eo<N, 1, Ar>(tab.Bf, in, out);
+        else if constexpr (WHICH == 1) contract_eo<N, 1, Ar>(tab.Bt, in, out);
+        else if constexpr (WHICH == 2) contract_eo<N, -1, Ar>(tab.Df, in, out);
+        else contract_eo<N, -1, Ar>(tab.Dt, in, out);
+    } else {
+        if constexpr (WHICH == 0) contract<N, false, Ar>(tab.B, in, out);
+        else if constexpr (WHICH == 1) contract<N, true, Ar>(tab.B, in, out);
+        else if constexpr (WHICH == 2) contract<N, false, Ar>(tab.D, in, out);
+        else contract<N, true, Ar>(tab.D, in, out);
     }
 }
 
@@ -166,35 +242,35 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
 #pragma unroll
                 for (int m = 0; m < N; ++m) v[m] = act ? Ar::from(ldg_nc(xc + m)) : Ar::zero();
             }
-            contract<N, false, Ar>(tab.B, v, w);
+            sweep<N, Ar, 0>(tab, v, w);
             CW_STX(s0, w);
         }
         __syncthreads();
         // (2) y-line (i,k): contract with B along y, in place
         {
             CW_LDY(s0, v);
-            contract<N, false, Ar>(tab.B, v, w);
+            sweep<N, Ar, 0>(tab, v, w);
             CW_STY(s0, w);
         }
         __syncthreads();
         // (3) z-pencil (i,j): contract with B along z -> u at the Gauss points (registers)
         {
             CW_LDZ(s0, v);
-            contract<N, false, Ar>(tab.B, v, u);
+            sweep<N, Ar, 0>(tab, v, u);
         }
         if (HAS_K) {
             {
-                contract<N, false, Ar>(tab.D, u, gz);
+                sweep<N, Ar, 2>(tab, u, gz);
                 CW_STZ(s0, u);
             }
             __syncthreads();
             // x- and y-derivatives by collocation, as line owners
             {
                 CW_LDX(s0, v);
-                contract<N, false, Ar>(tab.D, v, w);
+                sweep<N, Ar, 2>(tab, v, w);
                 CW_STX(s1, w);
                 CW_LDY(s0, v);
-                contract<N, false, Ar>(tab.D, v, w);
+                sweep<N, Ar, 2>(tab, v, w);
                 CW_STY(s2, w);
             }
             __syncthreads();
@@ -236,7 +312,7 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
         if (HAS_K) {
             // z-part of the transposed derivative in registers, x/y parts as line owners
             {
-                contract<N, true, Ar>(tab.D, gz, v);
+                sweep<N, Ar, 3>(tab, gz, v);
 #pragma unroll
                 for (int k = 0; k < N; ++k) acc[k] = HAS_M ? Ar::add(acc[k], v[k]) : v[k];
                 CW_STZ(s1, gx);  // own pencil only: no other thread reads s1/s2 pencils now
@@ -245,10 +321,10 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
             __syncthreads();
             {
                 CW_LDX(s1, v);
-                contract<N, true, Ar>(tab.D, v, w);
+                sweep<N, Ar, 3>(tab, v, w);
                 CW_STX(s1, w);
                 CW_LDY(s2, v);
-                contract<N, true, Ar>(tab.D, v, w);
+                sweep<N, Ar, 3>(tab, v, w);
                 CW_STY(s2, w);
             }
             __syncthreads();
@@ -261,19 +337,19 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
         }
         // (5) integrate back: B^T along z (registers), y and x as line owners
         {
-            contract<N, true, Ar>(tab.B, acc, w);
+            sweep<N, Ar, 1>(tab, acc, w);
             CW_STZ(s0, w);
         }
         __syncthreads();
         {
             CW_LDY(s0, v);
-            contract<N, true, Ar>(tab.B, v, w);
+            sweep<N, Ar, 1>(tab, v, w);
             CW_STY(s0, w);
         }
         __syncthreads();
         {
             CW_LDX(s0, v);
-            contract<N, true, Ar>(tab.B, v, w);
+            sweep<N, Ar, 1>(tab, v, w);
             if (act) {
                 VS *yc = yr + cell * N3 + N * r;
 #pragma unroll

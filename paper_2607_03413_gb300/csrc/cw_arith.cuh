@@ -138,6 +138,8 @@ struct ArDF {  // double-float arithmetic
     static __device__ __forceinline__ T mul(T a, C b) { return df_mul(a, b); }
     static __device__ __forceinline__ void mad(T &acc, T a, C b) { df_mad(acc, a, b); }
     static __device__ __forceinline__ T add(T a, T b) { return df_add(a, b); }
+    static __device__ __forceinline__ T sub(T a, T b) { return df_add(a, T{-b.hi, -b.lo}); }
+    static __device__ __forceinline__ T neg(T a) { return T{-a.hi, -a.lo}; }
     static __device__ __forceinline__ T norm(T a) { return df_norm(a); }
     static __device__ __forceinline__ T from(double v) { return split_f64(v); }
     static __device__ __forceinline__ T from(float v) { return T{v, 0.0f}; }
@@ -152,6 +154,8 @@ struct ArF64 {  // native FP64
     static __device__ __forceinline__ T mul(T a, C b) { return a * b; }
     static __device__ __forceinline__ void mad(T &acc, T a, C b) { acc = fma(a, b, acc); }
     static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
+    static __device__ __forceinline__ T neg(T a) { return -a; }
     static __device__ __forceinline__ T norm(T a) { return a; }
     static __device__ __forceinline__ T from(double v) { return v; }
     static __device__ __forceinline__ void to(double &d, T a) { d = a; }
@@ -165,6 +169,8 @@ struct ArF32 {  // FP32
     static __device__ __forceinline__ T mul(T a, C b) { return a * b; }
     static __device__ __forceinline__ void mad(T &acc, T a, C b) { acc = fmaf(a, b, acc); }
     static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
+    static __device__ __forceinline__ T neg(T a) { return -a; }
     static __device__ __forceinline__ T norm(T a) { return a; }
     static __device__ __forceinline__ T from(float v) { return v; }
     static __device__ __forceinline__ T from(__nv_bfloat16 v) { return __bfloat162float(v); }

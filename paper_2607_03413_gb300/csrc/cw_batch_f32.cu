@@ -16,15 +16,10 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_kernel_f32(const Batch
 
 static float mk(double v) { return static_cast<float>(v); }
 
-template <int N>
-static void fill(TabMetric<N, float> &t, const Tables1D *tb)
+template <int N, class C>
+static void fill(TabMetric<N, C> &t, const Tables1D *tb)
 {
-    if (!tb) return;
-    for (int a = 0; a < N; ++a)
-        for (int b = 0; b < N; ++b) {
-            t.B[a][b] = mk(tb->B[a][b]);
-            t.D[a][b] = mk(tb->D[a][b]);
-        }
+    if (tb) fill_metric_tab<N>(t, *tb, mk);
 }
 
 cudaError_t batch_upload_tables_f32(const Tables1D *const tabs[9])
@@ -61,11 +56,7 @@ static cudaError_t grouped(const Tables1D &tb, const BatchProb *d_probs, int npr
                            unsigned long long *counter, int kind_max, cudaStream_t s)
 {
     TabMetric<N, float> tab;
-    for (int a = 0; a < N; ++a)
-        for (int b = 0; b < N; ++b) {
-            tab.B[a][b] = mk(tb.B[a][b]);
-            tab.D[a][b] = mk(tb.D[a][b]);
-        }
+    fill_metric_tab<N>(tab, tb, mk);
     // shared memory for the largest metric of the group (kind_max components)
     const size_t smem = metric_smem_bytes<N, CPB, typename ArF32::T, float>(metric_ncomp(kind_max), STAGE);
     auto kern = batch_degree_kernel<N, CPB, ArF32, float, float, STAGE>;

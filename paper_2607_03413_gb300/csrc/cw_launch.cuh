@@ -27,6 +27,36 @@ struct MakeC<ArF32> {
     static float from(double v) { return static_cast<float>(v); }
 };
 
+// fills the full and even-odd forms of B and D from the double tables
+template <int N, class C, class MK>
+void fill_metric_tab(TabMetric<N, C> &t, const Tables1D &tb, MK mk)
+{
+    double B[N][N], Bt[N][N], D[N][N], Dt[N][N];
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+            B[a][b] = tb.B[a][b];
+            Bt[a][b] = tb.B[b][a];
+            D[a][b] = tb.D[a][b];
+            Dt[a][b] = tb.D[b][a];
+            t.B[a][b] = mk(tb.B[a][b]);
+            t.D[a][b] = mk(tb.D[a][b]);
+        }
+    auto eo = [&](EOMat<N, C> &E, const double (&M)[N][N]) {
+        constexpr int H = N / 2, NA = (N + 1) / 2;
+        for (int a = 0; a < NA; ++a) {
+            for (int b = 0; b < (H > 0 ? H : 1); ++b) {
+                E.E[a][b] = mk(b < H ? 0.5 * (M[a][b] + M[a][N - 1 - b]) : 0.0);
+                E.O[a][b] = mk(b < H ? 0.5 * (M[a][b] - M[a][N - 1 - b]) : 0.0);
+            }
+            E.Mid[a] = mk((N % 2 == 1) ? M[a][H] : 0.0);
+        }
+    };
+    eo(t.Bf, B);
+    eo(t.Bt, Bt);
+    eo(t.Df, D);
+    eo(t.Dt, Dt);
+}
+
 // cells per CTA: the default (about 128-200 threads) and the alternative the tuner can pick
 template <int N>
 constexpr int cpb_default()
@@ -51,11 +81,7 @@ template <int N, int CPB, class Ar, class VS, class GS, bool STAGE>
 cudaError_t launch_metric(const Op &op, const void *x, void *y, cudaStream_t s)
 {
     TabMetric<N, typename Ar::C> tab;
-    for (int a = 0; a < N; ++a)
-        for (int b = 0; b < N; ++b) {
-            tab.B[a][b] = MakeC<Ar>::from(op.tab.B[a][b]);
-            tab.D[a][b] = MakeC<Ar>::from(op.tab.D[a][b]);
-        }
+    fill_metric_tab<N>(tab, op.tab, [](double v) { return MakeC<Ar>::from(v); });
     const size_t smem = metric_smem_bytes<N, CPB, typename Ar::T, GS>(metric_ncomp(op.kind), STAGE);
     auto kern = apply_metric_kernel<N, CPB, Ar, VS, GS, STAGE>;
     static size_t opted = 0;  // largest size opted in so far for this instantiation
