@@ -132,9 +132,10 @@ int64_t cw_op_device_bytes(cw_op op);
 
 /*
  * Apply-kernel variant (the tuning knobs): cells per CTA -- 0 for the degree's default or one of
- * the two choices cw_op_get_variant reports -- and stage = 1 to move each CTA's input and metric
- * tiles into shared memory with bulk asynchronous copies (TMA) at kernel entry, 0 for direct
- * loads. Results do not depend on the variant beyond rounding order. CW_PREC_F64_NATIVE has only
+ * the two choices cw_op_get_variant reports -- and stage: 0 direct loads; 1 each CTA's input and
+ * metric tiles moved into shared memory with bulk asynchronous copies (TMA) at kernel entry; 2 the
+ * input tile by TMA and the metric tile prefetched into L2 by a bulk prefetch (less shared memory,
+ * more CTAs per SM). Results do not depend on the variant beyond rounding order. CW_PREC_F64_NATIVE has only
  * the default variant (CW_ERR_UNSUPPORTED otherwise).
  */
 cw_status cw_op_set_variant(cw_op op, int cells_per_cta, int stage);
@@ -201,7 +202,7 @@ cw_status cw_cg_solve(cw_op op, const double *b, double *u, double rtol, int max
  * Work items are (problem, chunk of tiles, right-hand side), right-hand side fastest, taken from a
  * device counter by persistent CTAs (no waiting: an item number past the end ends a CTA).
  * Mode CW_BATCH_GROUPED (default): one persistent kernel per degree present, shaped like the
- * per-operator kernel (variant = cells-per-CTA choice + 2 * TMA staging, 0..3). Mode
+ * per-operator kernel (variant = cells-per-CTA choice + 2 * staging mode of cw_op_set_variant, 0..5). Mode
  * CW_BATCH_SINGLE: all degrees in ONE persistent kernel of 128-thread CTAs (variant = 0 full tile,
  * 1 half tile); its 1D tables live in the library's constant memory, uploaded at create, so only
  * one single-mode batch per precision may be launched at a time.

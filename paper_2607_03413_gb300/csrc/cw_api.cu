@@ -217,28 +217,52 @@ struct AddOp<__nv_bfloat16> {
     }
 };
 
-template <class VS>
-__global__ void dss_axis_kernel(VS *__restrict__ v, int nx, int ny, int nz, int p, int ax)
-{
-    const int n = p + 1, n2 = n * n, n3 = n2 * n;
-    const int dims[3] = {nx, ny, nz};
-    const int64_t nitf = (int64_t)(dims[ax] - 1) * dims[(ax + 1) % 3] * dims[(ax + 2) % 3];
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nitf * n2) return;
-    const int64_t itf = t / n2;
-    const int f = (int)(t - itf * n2), fa = f % n, fb = f / n;
-    // interface -> left cell coordinates, x fastest; the axis coordinate runs over dims[ax]-1
-    int64_t c[3];
-    int64_t rem = itf;
-    for (int a = 0; a < 3; ++a) {
-        const int64_t ext = (a == ax) ? dims[a] - 1 : dims[a];
-        c[a] = rem % ext;
-        rem /= ext;
+// 32-bit division by a runtime constant: q = umulhi(x, floor((2^32-1)/d)), corrected once
+struct FastDiv {
+    uint32_t d, m;
+    static FastDiv make(uint32_t d) { return FastDiv{d, 0xFFFFFFFFu / d}; }
+    __device__ __forceinline__ uint32_t div(uint32_t x) const
+    {
+        uint32_t q = __umulhi(x, m);
+        if ((q + 1) * d <= x) ++q;
+        return q;
     }
-    const int64_t KL = c[0] + (int64_t)nx * (c[1] + (int64_t)ny * c[2]);
+};
+
+// grid: x covers (face node, first in-face cell coordinate, interface coordinate along ax),
+// y the remaining cell coordinate. All index arithmetic is 32-bit.
+template <class VS>
+__global__ void dss_axis_kernel(VS *__restrict__ v, int nx, int ny, int nz, int p, int ax, uint32_t nx_thr,
+                                FastDiv fd_n2, FastDiv fd_e0)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nx_thr) return;
+    const int n = p + 1, n2 = n * n, n3 = n2 * n;
+    // x index: f + n2 * (c_a + e0 * c_ax) with (c_a, c_ax) the in-face coordinate and the
+    // interface coordinate, e0 the extent of c_a
+    const uint32_t q = fd_n2.div(t);
+    const uint32_t f = t - q * static_cast<uint32_t>(n2);
+    const uint32_t c_ax = fd_e0.div(q);
+    const uint32_t c_a = q - c_ax * fd_e0.d;
+    const uint32_t c_b = blockIdx.y;
+    const uint32_t fa = f % n, fb = f / n;  // n <= 8: cheap
+    uint32_t cx, cy, cz;
+    if (ax == 0) {
+        cx = c_ax;
+        cy = c_a;
+        cz = c_b;
+    } else if (ax == 1) {
+        cx = c_a;
+        cy = c_ax;
+        cz = c_b;
+    } else {
+        cx = c_a;
+        cy = c_b;
+        cz = c_ax;
+    }
+    const int64_t KL = cx + (int64_t)nx * (cy + (int64_t)ny * cz);
     const int64_t stride = (ax == 0) ? 1 : (ax == 1 ? nx : (int64_t)nx * ny);
     const int64_t KR = KL + stride;
-    // face node (fa, fb) in the two in-face directions (lower axis first)
     int il, ir;
     if (ax == 0) {
         il = p + n * fa + n2 * fb;
@@ -254,6 +278,7 @@ __global__ void dss_axis_kernel(VS *__restrict__ v, int nx, int ny, int nz, int 
     const VS s = AddOp<VS>::add(*pl, *pr);
     *pl = s;
     *pr = s;
+    (void)nz;
 }
 
 template <class VS>
@@ -300,9 +325,14 @@ static cudaError_t dss_typed(const Op &op, VS *v, int flags, cudaStream_t s)
     const int n2 = op.n * op.n;
     for (int ax = 0; ax < 3; ++ax) {
         if (dims[ax] < 2) continue;
-        const int64_t nthr = (int64_t)(dims[ax] - 1) * dims[(ax + 1) % 3] * dims[(ax + 2) % 3] * n2;
+        // in-face coordinates: a = lower of the two other axes (x-index part), b = the other (grid y)
+        const int a = (ax == 0) ? 1 : 0, b = (ax == 2) ? 1 : 2;
+        const uint32_t e0 = dims[a];
+        const uint32_t nthr = (uint32_t)n2 * e0 * (uint32_t)(dims[ax] - 1);
         const int bs = 256;
-        dss_axis_kernel<VS><<<(unsigned)((nthr + bs - 1) / bs), bs, 0, s>>>(v, m.nx, m.ny, m.nz, op.p, ax);
+        dim3 grid((nthr + bs - 1) / bs, dims[b]);
+        dss_axis_kernel<VS><<<grid, bs, 0, s>>>(v, m.nx, m.ny, m.nz, op.p, ax, nthr, FastDiv::make(n2),
+                                                FastDiv::make(e0));
     }
     if (flags == CW_DSS_AVERAGE) {
         const int bs = 256;
@@ -655,7 +685,7 @@ cw_status cw_op_set_variant(cw_op oh, int cells_per_cta, int stage)
     cpb_choices(op->p, ch);
     if (cells_per_cta != 0 && cells_per_cta != ch[0] && cells_per_cta != ch[1])
         return fail(CW_ERR_ARG, "cw_op_set_variant: cells_per_cta must be 0 or one of cw_op_get_variant's choices");
-    if (stage != 0 && stage != 1) return fail(CW_ERR_ARG, "cw_op_set_variant: stage must be 0 or 1");
+    if (stage < 0 || stage > 2) return fail(CW_ERR_ARG, "cw_op_set_variant: stage must be 0, 1 or 2");
     if (op->prec == CW_PREC_F64_NATIVE && (cells_per_cta != 0 || stage != 0))
         return fail(CW_ERR_UNSUPPORTED, "cw_op_set_variant: CW_PREC_F64_NATIVE has only the default variant");
     op->cpb = cells_per_cta == ch[0] ? 0 : cells_per_cta;
@@ -697,7 +727,7 @@ cw_status cw_op_autotune(cw_op oh, const void *x, void *y, int reps, void *strea
     CW_CUDA_TRY(cudaEventCreate(&e1));
     float best = 1e30f;
     int bc = 0, bs = op->stage;
-    const int nstage = op->geom == CW_GEOM_METRIC ? 2 : 1;
+    const int nstage = op->geom == CW_GEOM_METRIC ? 3 : 1;
     for (int ci = 0; ci < 2; ++ci)
         for (int st = 0; st < nstage; ++st) {
             op->cpb = ci == 0 ? 0 : ch[1];

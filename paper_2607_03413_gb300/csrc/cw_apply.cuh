@@ -164,17 +164,22 @@ __host__ __device__ constexpr int metric_ncomp(int kind) { return kind == 1 ? 6 
 // interpolation and gradient sweeps. Tiles that cannot use a bulk copy (ragged last tile,
 // misaligned span) and copies that do not complete within the wait bound are read with ordinary
 // global loads instead.
+// STAGE 0: direct loads; 1: x and metric tiles staged in shared memory by TMA; 2: x tile staged by
+// TMA, metric tile prefetched into L2 by a bulk prefetch (a third of the shared memory of mode 1,
+// so more CTAs per SM), then read with direct loads.
 template <int N, int CPB, class T, class GS>
-__host__ __device__ constexpr size_t metric_smem_bytes(int nc, bool stage)
+__host__ __device__ constexpr size_t metric_smem_bytes(int nc, int stage)
 {
-    return stage ? ((3 * CPB * Lines<N>::CS * sizeof(T) + 15) / 16 * 16 + (CPB * nc * N * N * N * sizeof(GS) + 15) / 16 * 16 + 16)
-                 : 3 * CPB * Lines<N>::CS * sizeof(T);
+    return stage == 1 ? ((3 * CPB * Lines<N>::CS * sizeof(T) + 15) / 16 * 16 +
+                         (CPB * nc * N * N * N * sizeof(GS) + 15) / 16 * 16 + 16)
+           : stage == 2 ? (3 * CPB * Lines<N>::CS * sizeof(T) + 15) / 16 * 16 + 16
+                        : 3 * CPB * Lines<N>::CS * sizeof(T);
 }
 
 // One tile of `cpt` consecutive cells starting at cell tile*cpt, worked by CPB cell slots of N*N
 // threads (cpt <= CPB; slots c >= cpt compute on zeros and store nothing, so a CTA may have more
-// threads than the tile needs). STAGE (cpt == CPB only): TMA staging of the x and metric tiles.
-template <int N, int CPB, class Ar, class VS, class GS, bool STAGE>
+// threads than the tile needs). STAGE (see metric_smem_bytes; staging needs cpt == CPB).
+template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
 __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__restrict__ y, const GS *__restrict__ geo,
                                             int64_t ncells, int kind, const TabMetric<N, typename Ar::C> &tab,
                                             int64_t tile, int cpt, unsigned char *smem_raw)
@@ -199,7 +204,7 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
     const VS *xs = nullptr;
     const GS *gs = nullptr;
     uint64_t *bar = nullptr;
-    if constexpr (STAGE) {
+    if constexpr (STAGE == 1) {
         const size_t offg = (3 * CPB * CS * sizeof(T) + 15) / 16 * 16;
         GS *sG = reinterpret_cast<GS *>(smem_raw + offg);
         bar = reinterpret_cast<uint64_t *>(smem_raw + offg + (CPB * NC * N3 * sizeof(GS) + 15) / 16 * 16);
@@ -225,6 +230,25 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
             xs = sX + c * N3;
             gs = sG + c * NC * N3;
             g_smem = true;  // decided at the physics step
+        }
+    } else if constexpr (STAGE == 2) {
+        bar = reinterpret_cast<uint64_t *>(smem_raw + (3 * CPB * CS * sizeof(T) + 15) / 16 * 16);
+        VS *sX = reinterpret_cast<VS *>(S0 + CPB * CS);
+        const VS *xsrc = x + cell0 * N3;
+        const GS *gsrc = geo + cell0 * NC * N3;
+        const uint32_t xb = CPB * N3 * sizeof(VS), gb = CPB * NC * N3 * sizeof(GS);
+        const bool full = cell0 + CPB <= ncells;
+        const bool ok = full && aligned16(xsrc) && aligned16(sX) && (xb % 16 == 0);
+        if (t == 0 && full && aligned16(gsrc) && (gb % 16 == 0)) bulk_prefetch_l2(gsrc, gb);
+        if (ok) {  // block-uniform
+            if (t == 0) mbar_init(bar, 1);
+            __syncthreads();
+            if (t == 0) {
+                mbar_expect_tx(bar, xb);
+                bulk_g2s(sX, xsrc, xb, bar);
+            }
+            x_smem = mbar_wait_bounded(bar, 0);
+            xs = sX + c * N3;
         }
     }
 
@@ -280,7 +304,7 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
             }
         }
         // (4) quadrature-point physics on the owned pencil, qp = (ra, rb, k)
-        if constexpr (STAGE) {
+        if constexpr (STAGE == 1) {
             if (g_smem) g_smem = mbar_wait_bounded(bar + 1, 0);
         }
         {
@@ -357,7 +381,7 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
             }
         }
     }
-    if constexpr (STAGE) {
+    if constexpr (STAGE == 1) {
         // a copy that missed its wait bound must not land in shared memory after exit
         if (xs != nullptr && (!x_smem || !g_smem)) {
             mbar_wait_bounded(bar, 0);
@@ -366,7 +390,7 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
     }
 }
 
-template <int N, int CPB, class Ar, class VS, class GS, bool STAGE>
+template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
 __global__ void __launch_bounds__(N *N *CPB) apply_metric_kernel(const VS *__restrict__ x, VS *__restrict__ y,
                                                                   const GS *__restrict__ geo, int64_t ncells,
                                                                   int kind, TabMetric<N, typename Ar::C> tab)

@@ -206,7 +206,7 @@ cw_status cw_batch_set_mode(cw_batch bh, int mode)
     return batch_rebuild(*b);
 }
 
-static int variant_count(const Batch &b) { return b.mode == CW_BATCH_SINGLE ? 2 : 4; }
+static int variant_count(const Batch &b) { return b.mode == CW_BATCH_SINGLE ? 2 : 6; }
 
 cw_status cw_batch_set_variant(cw_batch bh, int degree, int variant)
 {

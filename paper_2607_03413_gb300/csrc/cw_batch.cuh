@@ -75,8 +75,7 @@ __device__ __noinline__ void batch_item(const BatchProb &P, const BatchTables<ty
     const int64_t t0 = chunk * P.tpi, t1 = min(P.ntiles, t0 + P.tpi);
     for (int64_t tile = t0; tile < t1; ++tile) {
         if (tile > t0) __syncthreads();  // the previous tile has finished with shared memory
-        metric_tile<N, batch_slots(N), Ar, VS, GS, false>(x, y, g, P.ncells, P.kind, batch_tab<N>(T), tile, P.cpt,
-                                                          smem);
+        metric_tile<N, batch_slots(N), Ar, VS, GS, 0>(x, y, g, P.ncells, P.kind, batch_tab<N>(T), tile, P.cpt, smem);
     }
 }
 
@@ -122,7 +121,7 @@ __device__ __forceinline__ void batch_body(const BatchProb *__restrict__ probs, 
 // ---- grouped mode: one persistent kernel per degree, shaped like the per-operator kernel
 // (N*N*CPB threads, its own register allocation, optional TMA staging). Work items are
 // (problem, chunk of tiles, right-hand side) over the problems of that degree only.
-template <int N, int CPB, class Ar, class VS, class GS, bool STAGE>
+template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
 __global__ void __launch_bounds__(N *N *CPB) batch_degree_kernel(const BatchProb *__restrict__ probs, int nprob,
                                                                   int64_t nitems, unsigned long long *__restrict__ counter,
                                                                   TabMetric<N, typename Ar::C> tab)
@@ -161,7 +160,7 @@ __global__ void __launch_bounds__(N *N *CPB) batch_degree_kernel(const BatchProb
     }
 }
 
-// per-unit launchers of the grouped mode (variant: cells per CTA choice 0/1, staging 0/1)
+// per-unit launchers of the grouped mode (variant: cells per CTA choice 0/1, staging mode 0/1/2)
 cudaError_t batch_degree_launch_df(int n, int cpb_alt, int stage, const Tables1D &tb, const BatchProb *d_probs,
                                    int nprob, int64_t nitems, unsigned long long *counter, int kind_max,
                                    cudaStream_t s);

@@ -51,7 +51,7 @@ cudaError_t batch_launch_f32(const BatchProb *d_probs, int nprob, int64_t nitems
     return cudaGetLastError();
 }
 
-template <int N, int CPB, bool STAGE>
+template <int N, int CPB, int STAGE>
 static cudaError_t grouped(const Tables1D &tb, const BatchProb *d_probs, int nprob, int64_t nitems,
                            unsigned long long *counter, int kind_max, cudaStream_t s)
 {
@@ -82,10 +82,12 @@ static cudaError_t grouped_n(int alt, int stage, const Tables1D &tb, const Batch
                              int64_t nitems, unsigned long long *counter, int kind_max, cudaStream_t s)
 {
     constexpr int D = cpb_default<N>(), A = cpb_alt<N>();
-    if (alt) return stage ? grouped<N, A, true>(tb, d_probs, nprob, nitems, counter, kind_max, s)
-                          : grouped<N, A, false>(tb, d_probs, nprob, nitems, counter, kind_max, s);
-    return stage ? grouped<N, D, true>(tb, d_probs, nprob, nitems, counter, kind_max, s)
-                 : grouped<N, D, false>(tb, d_probs, nprob, nitems, counter, kind_max, s);
+    if (alt) return stage == 1 ? grouped<N, A, 1>(tb, d_probs, nprob, nitems, counter, kind_max, s)
+                   : stage == 2 ? grouped<N, A, 2>(tb, d_probs, nprob, nitems, counter, kind_max, s)
+                                : grouped<N, A, 0>(tb, d_probs, nprob, nitems, counter, kind_max, s);
+    return stage == 1 ? grouped<N, D, 1>(tb, d_probs, nprob, nitems, counter, kind_max, s)
+           : stage == 2 ? grouped<N, D, 2>(tb, d_probs, nprob, nitems, counter, kind_max, s)
+                        : grouped<N, D, 0>(tb, d_probs, nprob, nitems, counter, kind_max, s);
 }
 
 cudaError_t batch_degree_launch_f32(int n, int cpb_alt, int stage, const Tables1D &tb, const BatchProb *d_probs,

@@ -22,6 +22,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 
@@ -37,7 +38,10 @@ constexpr int kBatch = 16;
 // device scalar slots
 enum : int { S_RHO = 0, S_PQ, S_ALPHA, S_BETA, S_RES0, S_RES, S_RHO_NEW, S_TOL2, S_ENERGY, S_NSCAL = 16 };
 // device flag slots
-enum : int { F_DONE = 0, F_ITER, F_STATUS, F_MAXIT, F_NFLAG = 8 };
+// F_ACTIVE: the current iteration started before convergence (set at its <p,Ap> stage); its
+// direction update p = z + beta p runs even if the iteration converges, so that a later segment
+// can continue from a consistent (r, p) pair
+enum : int { F_DONE = 0, F_ITER, F_STATUS, F_MAXIT, F_ACTIVE, F_NFLAG = 8 };
 enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_MAXIT = 3 };
 
 struct CgLevel {  // vectors of one precision level
@@ -144,7 +148,7 @@ template <class V, class U>
 __global__ void k_update(U *__restrict__ u, const V *__restrict__ p, V *__restrict__ r, const V *__restrict__ q,
                          int64_t n, const double *__restrict__ scal, const int *__restrict__ flags)
 {
-    if (flags[F_DONE]) return;
+    if (!flags[F_ACTIVE]) return;
     const double alpha = scal[S_ALPHA];
     const V a = static_cast<V>(alpha);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -158,7 +162,7 @@ template <class V>
 __global__ void k_pupdate(V *__restrict__ p, const V *__restrict__ z, int64_t n, const double *__restrict__ scal,
                           const int *__restrict__ flags)
 {
-    if (flags[F_DONE]) return;
+    if (!flags[F_ACTIVE] || flags[F_STATUS] == ST_BREAKDOWN) return;
     const V beta = static_cast<V>(scal[S_BETA]);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = z[i] + beta * p[i];
@@ -236,7 +240,11 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const double *__restri
                                                           double *__restrict__ scal, int *__restrict__ flags,
                                                           int stage)
 {
-    if (stage != STAGE_INIT && stage != STAGE_RES && stage != STAGE_ENERGY && flags[F_DONE]) return;
+    if (stage == STAGE_PQ && flags[F_DONE]) {  // an iteration after convergence: a no-op
+        if (threadIdx.x == 0) flags[F_ACTIVE] = 0;
+        return;
+    }
+    if (stage == STAGE_RHO && !flags[F_ACTIVE]) return;
     const double s0 = sum_partials(part, nb);
     const double s1 = (stage == STAGE_INIT || stage == STAGE_RHO || stage == STAGE_RES) ? sum_partials(part + nb, nb) : 0.0;
     if (threadIdx.x != 0) return;
@@ -255,8 +263,10 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const double *__restri
         if (!(s0 > 0.0) || !isfinite(s0)) {
             flags[F_STATUS] = ST_BREAKDOWN;
             flags[F_DONE] = 1;
+            flags[F_ACTIVE] = 0;
             return;
         }
+        flags[F_ACTIVE] = 1;
         scal[S_PQ] = s0;
         scal[S_ALPHA] = scal[S_RHO] / s0;
     } else if (stage == STAGE_RHO) {
@@ -286,6 +296,16 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const double *__restri
 
 // --------------------------------------------------------------------------- host side ----
 static unsigned vec_grid() { return kRedBlocks; }
+
+// CWFEM_DEBUG=1 in the environment prints the outer refinement loop of cw_cg_solve to stderr
+static bool debug_trace()
+{
+    static const bool on = [] {
+        const char *e = std::getenv("CWFEM_DEBUG");
+        return e && e[0] && e[0] != '0';
+    }();
+    return on;
+}
 
 // which operator evaluation an inner level uses
 enum ApplyKind : int { AK_DF = 0, AK_NATIVE = 1, AK_OP = 2 };
@@ -363,8 +383,12 @@ static cudaError_t cg_iteration(const Op &aop, int ak, CgLevel &lv, U *u, CgScra
 }
 
 // CG on A u = rhs for level lv (rhs already in lv.r), u zeroed here. Returns the final status.
+// keep_p: continue with the search direction of the previous run (residual replacement / reliable
+// update: the new rhs is the accurate residual of the same problem, so the Krylov direction stays
+// useful); otherwise p starts as the preconditioned residual.
 template <class V, class U>
-static cw_status cg_run(const Op &aop, int ak, CgLevel &lv, U *u, CgScratch &c, double rtol, int maxit, int *iters)
+static cw_status cg_run(const Op &aop, int ak, CgLevel &lv, U *u, CgScratch &c, double rtol, int maxit, int *iters,
+                        bool keep_p = false, double *rec_reduction = nullptr)
 {
     cudaStream_t s = c.stream;
     const int64_t L = aop.L;
@@ -382,7 +406,7 @@ static cw_status cg_run(const Op &aop, int ak, CgLevel &lv, U *u, CgScratch &c, 
     CW_CUDA_TRY(dss_launch(aop, z, CW_DSS_SUM, s));
     k_precond<V><<<vec_grid(), kRedThreads, 0, s>>>(r, z, dinv, L, c.kappa, c.partials, c.flags);
     k_finalize<<<1, kRedThreads, 0, s>>>(c.partials, kRedBlocks, c.scal, c.flags, STAGE_INIT);
-    k_copy<V, V><<<vec_grid(), 256, 0, s>>>(p, z, L);
+    if (!keep_p) k_copy<V, V><<<vec_grid(), 256, 0, s>>>(p, z, L);
     CW_CUDA_TRY(cudaGetLastError());
     // one eager iteration (first-use initialisation of the kernels), then graph batches
     CW_CUDA_TRY((cg_iteration<V, U>(aop, ak, lv, u, c, s)));
@@ -412,6 +436,11 @@ static cw_status cg_run(const Op &aop, int ak, CgLevel &lv, U *u, CgScratch &c, 
         CW_CUDA_TRY(cudaGraphLaunch(lv.graph, s));
     }
     *iters = c.h_flags[F_ITER];
+    if (rec_reduction) {  // recursive residual reduction of this run: sqrt(res / res0)
+        CW_CUDA_TRY(cudaMemcpyAsync(c.h_scal, c.scal, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CW_CUDA_TRY(cudaStreamSynchronize(s));
+        *rec_reduction = c.h_scal[S_RES0] > 0.0 ? std::sqrt(c.h_scal[S_RES] / c.h_scal[S_RES0]) : 0.0;
+    }
     switch (c.h_flags[F_STATUS]) {
     case ST_CONVERGED: return CW_OK;
     case ST_BREAKDOWN: return fail(CW_ERR_BREAKDOWN, "cw_cg_solve: breakdown (<p,Ap> <= 0 or non-finite)");
@@ -537,11 +566,14 @@ static cw_status averaged_rhs(const Op &op, const double *r, double *work, void 
 using namespace cw;
 
 // Every mode runs the same outer loop: r = b - A u with the native-FP64 operator (the accurate
-// residual), stop when ||m G^T r|| <= rtol ||m G^T b||, else solve A d = S_bar r approximately with
-// an inner Jacobi-PCG and set u += d. The inner solver is FP64 with the double-float operator
+// residual), stop when ||m G^T r|| <= rtol ||m G^T b||, else continue the inner Jacobi-PCG on
+// A d = S_bar r and set u += d. The inner solver is FP64 with the double-float operator
 // (CW_CG_F64), FP64 with the native operator (CW_CG_F64_NATIVE), or FP32 with the FP32 / BF16-metric
-// operator (CW_CG_IR_*). The inner tolerance is the reduction still needed (FP64 inner levels) or
-// that reduction clamped to at least 1e-4 (FP32 inner levels, whose attainable accuracy is lower).
+// operator (CW_CG_IR_*). The inner CG is not restarted between segments: each segment replaces the
+// recursive residual by the accurate one and keeps the search direction (reliable updates, as in
+// mixed-precision Krylov solvers). A segment ends when its recursive residual has dropped by the
+// reduction still needed (FP64 inner levels) or by a factor 10 (FP32 inner levels, whose recursive
+// residual drifts from the true one as the iteration proceeds).
 extern "C" cw_status cw_cg_solve(cw_op oh, const double *b, double *u, double rtol, int maxit, int mode,
                                  cw_cg_stats *stats, void *stream)
 {
@@ -564,7 +596,7 @@ extern "C" cw_status cw_cg_solve(cw_op oh, const double *b, double *u, double rt
     CW_CUDA_TRY(cudaEventRecord(c.ev0, s));
     const bool fp64_inner = (mode == CW_CG_F64 || mode == CW_CG_F64_NATIVE);
     const int ak = mode == CW_CG_F64 ? AK_DF : (mode == CW_CG_F64_NATIVE ? AK_NATIVE : AK_OP);
-    const double floor_tol = fp64_inner ? 1e-15 : 1e-4;
+    const double floor_tol = fp64_inner ? 1e-15 : 0.1;
     double *r = c.rout, *w = c.q64b;
     int iters = 0, outer = 0;
     double res0 = 0.0, res = 0.0;
@@ -574,7 +606,8 @@ extern "C" cw_status cw_cg_solve(cw_op oh, const double *b, double *u, double rt
     if (!std::isfinite(res0)) return fail(CW_ERR_BREAKDOWN, "cw_cg_solve: non-finite right-hand side");
     res = res0;
     st = res0 > 0.0 ? CW_ERR_NOT_CONVERGED : CW_OK;
-    while (res0 > 0.0 && iters < maxit && outer < 50) {
+    bool consistent = false;  // the last segment's true reduction followed its recursive one
+    while (res0 > 0.0 && iters < maxit && outer < 200) {
         if (res <= rtol * rtol * res0) {
             st = CW_OK;
             break;
@@ -582,24 +615,37 @@ extern "C" cw_status cw_cg_solve(cw_op oh, const double *b, double *u, double rt
         const double need = rtol * std::sqrt(res0 / res);
         const double itol = std::min(0.5, std::max(floor_tol, 0.5 * need));
         int it = 0;
+        double rec = 1.0;
         cw_status ist;
-        if (fp64_inner) {
-            if ((ist = averaged_rhs(*op, r, w, c.lv64.r, false, s)) != CW_OK) return ist;
-            ist = cg_run<double, double>(*op, ak, c.lv64, c.d64, c, itol, maxit - iters, &it);
-            k_add_correction_f64<<<vec_grid(), 256, 0, s>>>(u, c.d64, L);
-        } else {
-            if ((ist = averaged_rhs(*op, r, w, c.lv32.r, true, s)) != CW_OK) return ist;
-            ist = cg_run<float, float>(*op->inner, AK_OP, c.lv32, c.d32, c, itol, maxit - iters, &it);
-            k_add_correction<<<vec_grid(), 256, 0, s>>>(u, c.d32, L);
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            // continue the Krylov process only after a consistent segment; restart otherwise or
+            // when a continued segment breaks down
+            const bool keep = consistent && attempt == 0;
+            if (fp64_inner) {
+                if ((ist = averaged_rhs(*op, r, w, c.lv64.r, false, s)) != CW_OK) return ist;
+                ist = cg_run<double, double>(*op, ak, c.lv64, c.d64, c, itol, maxit - iters, &it, keep, &rec);
+            } else {
+                if ((ist = averaged_rhs(*op, r, w, c.lv32.r, true, s)) != CW_OK) return ist;
+                ist = cg_run<float, float>(*op->inner, AK_OP, c.lv32, c.d32, c, itol, maxit - iters, &it, keep, &rec);
+            }
+            if (debug_trace())
+                std::fprintf(stderr, "[cwfem cg] outer %d: inner status %d, %d iterations (tol %.2e, %s)\n", outer,
+                             (int)ist, it, itol, keep ? "continued" : "restarted");
+            iters += it;
+            if (ist != CW_ERR_BREAKDOWN || !keep) break;
         }
         if (ist == CW_ERR_BREAKDOWN) return ist;
-        iters += it;
+        if (fp64_inner) k_add_correction_f64<<<vec_grid(), 256, 0, s>>>(u, c.d64, L);
+        else k_add_correction<<<vec_grid(), 256, 0, s>>>(u, c.d32, L);
         ++outer;
         // accurate residual with the native FP64 operator
+        const double res_prev = res;
         CW_CUDA_TRY(apply_launch_f64n(*op, u, w, s));
         k_sub<<<vec_grid(), 256, 0, s>>>(r, b, w, L);
         if ((st = residual_norm2(*op, r, w, c, &res)) != CW_OK) return st;
+        if (debug_trace()) std::fprintf(stderr, "[cwfem cg] outer %d: true rel residual %.3e\n", outer, std::sqrt(res / res0));
         if (!std::isfinite(res)) return fail(CW_ERR_BREAKDOWN, "cw_cg_solve: non-finite residual");
+        consistent = std::sqrt(res / res_prev) <= 1.25 * rec;
         st = CW_ERR_NOT_CONVERGED;
     }
     if (res <= rtol * rtol * res0) st = CW_OK;

@@ -77,7 +77,7 @@ static cudaError_t opt_in_smem(K kernel, size_t smem)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <int N, int CPB, class Ar, class VS, class GS, bool STAGE>
+template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
 cudaError_t launch_metric(const Op &op, const void *x, void *y, cudaStream_t s)
 {
     TabMetric<N, typename Ar::C> tab;
@@ -131,12 +131,14 @@ cudaError_t launch_variant(const Op &op, const void *x, void *y, cudaStream_t s)
     }
     if constexpr (ALL_VARIANTS) {
         const bool alt = (op.cpb == A);
-        if (op.stage) return alt ? launch_metric<N, A, Ar, VS, GS, true>(op, x, y, s)
-                                 : launch_metric<N, D, Ar, VS, GS, true>(op, x, y, s);
-        return alt ? launch_metric<N, A, Ar, VS, GS, false>(op, x, y, s)
-                   : launch_metric<N, D, Ar, VS, GS, false>(op, x, y, s);
+        if (op.stage == 1) return alt ? launch_metric<N, A, Ar, VS, GS, 1>(op, x, y, s)
+                                      : launch_metric<N, D, Ar, VS, GS, 1>(op, x, y, s);
+        if (op.stage == 2) return alt ? launch_metric<N, A, Ar, VS, GS, 2>(op, x, y, s)
+                                      : launch_metric<N, D, Ar, VS, GS, 2>(op, x, y, s);
+        return alt ? launch_metric<N, A, Ar, VS, GS, 0>(op, x, y, s)
+                   : launch_metric<N, D, Ar, VS, GS, 0>(op, x, y, s);
     }
-    return launch_metric<N, D, Ar, VS, GS, false>(op, x, y, s);
+    return launch_metric<N, D, Ar, VS, GS, 0>(op, x, y, s);
 }
 
 template <class Ar, class VS, class GS, bool ALL_VARIANTS = true>

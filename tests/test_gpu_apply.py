@@ -136,7 +136,8 @@ def test_load_vector(cw, orc, p, which):
 @pytest.mark.parametrize("prec", [0, 2, 4], ids=["df64", "f32", "bf16"])
 @pytest.mark.parametrize("p", [1, 3, 4, 7])
 def test_apply_all_variants(cw, orc, p, prec):
-    """Every kernel variant (two tile sizes x TMA-staged or direct loads) gives the oracle's result;
+    """Every kernel variant (two tile sizes x direct loads, TMA staging, or TMA + L2 prefetch) gives
+    the oracle's result;
     the mesh has a ragged last tile for both tile sizes."""
     import torch
     mesh = synth.box_mesh(3, 3, 5, perturb=0.2) if p < 7 else synth.box_mesh(3, 1, 3, perturb=0.2)
@@ -148,7 +149,7 @@ def test_apply_all_variants(cw, orc, p, prec):
     xd = torch.from_numpy(x).cuda().to(op.vec_dtype)
     tol = {0: TOL64, 2: 2e-6, 4: 3e-2}[prec]
     for cpb in choices:
-        for stage in (0, 1):
+        for stage in (0, 1, 2):
             op.set_variant(cpb, stage)
             y = op.apply(xd)
             torch.cuda.synchronize()
@@ -165,7 +166,7 @@ def test_autotune_keeps_a_valid_variant(cw, orc):
     y = op.empty()
     ms = op.autotune(x, y, reps=2)
     cpb, stage, choices = op.variant()
-    assert ms > 0 and cpb in choices and stage in (0, 1)
+    assert ms > 0 and cpb in choices and stage in (0, 1, 2)
     y2 = op.apply(x)
     ref = orc.apply_local(mesh, p, 3, to_np(x))
     assert rel_err(to_np(y2), ref) <= TOL64

@@ -52,7 +52,7 @@ def test_batch_equals_per_operator_apply(cw, prec, graph, mode):
     B = cw.Batch(ops, nrhs, xs, ys)
     B.set_mode(mode)
     assert B.values == sum(o.L * r for o, r in zip(ops, nrhs))
-    for variant in range(4 if mode == 0 else 2):
+    for variant in range(6 if mode == 0 else 2):
         for (_, p, _, _) in SPECS:
             B.set_variant(p, variant)
         for y in ys:
