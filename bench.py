@@ -60,6 +60,12 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# DRAM bytes per cell of the double-float K+M p=4 apply kernel, variant (8 cells/CTA, TMA staging):
+# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of a 40^3-cell case
+# (512.2 MB + 55.5 MB for 64,000 cells), to be scaled by the cell count of a launch.
+DF64_KM_P4_TRAFFIC_PER_CELL = (512.221696e6 + 55.474688e6) / 64000
+PROFILED_VARIANT = (8, 1)
+
 # FP32 issue-rate roofline for double-float arithmetic: 152 SMs x 128 FP32 lanes x 2.07 GHz,
 # 12 FP32 instructions per emulated FP64 multiply-add (2 flops).
 DF64_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 12 * 2 / 1e12
@@ -239,8 +245,13 @@ def gpu_arm(args, rank, local, world):
     fl = flops_per_value(n, KIND) * op.L
     achieved_tflops = fl / (kern_ms * 1e-3) / 1e12
     by = bytes_per_value(0, KIND) * op.L
+    traffic = None
+    if args.prec == 0 and (variant[0], variant[1]) == PROFILED_VARIANT:
+        traffic = round(DF64_KM_P4_TRAFFIC_PER_CELL * args.cells ** 3)
     roof = {"bound": "alu", "achieved": round(achieved_tflops, 3), "peak": round(DF64_PEAK_TFLOPS, 3),
-            "unit": "TFLOP/s", "frac": round(achieved_tflops / DF64_PEAK_TFLOPS, 4), "traffic": None,
+            "unit": "TFLOP/s", "frac": round(achieved_tflops / DF64_PEAK_TFLOPS, 4), "traffic": traffic,
+            "traffic_note": "bytes per launch, ncu on a 40^3 case scaled by cells (null unless the timed variant "
+                            "is the profiled one)",
             "kernel": f"apply_metric_kernel<N=5, cells/CTA={variant[0]}, staged={variant[1]}, double-float>",
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 12 instructions per double-float MAD",
             "hbm": {"achieved": round(by / (kern_ms * 1e-3) / 1e9, 1), "peak": hbm, "unit": "GB/s",
