@@ -317,13 +317,68 @@ __global__ void scale_by_valence_kernel(VS *__restrict__ v, int nx, int ny, int 
     if (val > 1) v[t] = MulOp<VS>::mul(v[t], 1.0 / val);
 }
 
+// dst = src with the x pass of Algorithm struct_dss applied: an entry on an interior x-face adds its
+// partner copy in the neighbouring cell, every other entry is copied (out of place, so the read of
+// a partner never sees an updated value). Replaces a copy and an in-place x pass with one pass.
 template <class VS>
-static cudaError_t dss_typed(const Op &op, VS *v, int flags, cudaStream_t s)
+__global__ void dss_x_from_kernel(const VS *__restrict__ src, VS *__restrict__ dst, int nx, int p, uint32_t L,
+                                  FastDiv fd_n3, FastDiv fd_nx)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L) return;
+    const uint32_t n = p + 1, n3 = fd_n3.d;
+    const uint32_t c = fd_n3.div(t);
+    const uint32_t loc = t - c * n3;
+    const uint32_t i = loc % n;
+    const uint32_t cx = c - fd_nx.div(c) * static_cast<uint32_t>(nx);
+    VS v = src[t];
+    if (i == static_cast<uint32_t>(p) && cx + 1 < static_cast<uint32_t>(nx)) v = AddOp<VS>::add(v, src[t + n3 - p]);
+    else if (i == 0 && cx > 0) v = AddOp<VS>::add(src[t - n3 + p], v);
+    dst[t] = v;
+}
+
+template <class VS>
+static cudaError_t dss_typed(const Op &op, VS *v, int flags, cudaStream_t s, int first_axis = 0);
+
+// dst = S src (or S_bar src), src unchanged; src and dst must not overlap
+template <class VS>
+static cudaError_t dss_from_typed(const Op &op, const VS *src, VS *dst, int flags, cudaStream_t s)
+{
+    const Mesh &m = *op.mesh;
+    if (op.L >= (int64_t)1 << 31) {  // 32-bit index path not applicable: copy, then all passes
+        cudaError_t e = cudaMemcpyAsync(dst, src, op.L * sizeof(VS), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+        return dss_typed(op, dst, flags, s, 0);
+    }
+    const int n3 = op.n * op.n * op.n;
+    const uint32_t L = (uint32_t)op.L;
+    dss_x_from_kernel<VS><<<(L + 255) / 256, 256, 0, s>>>(src, dst, m.nx, op.p, L, FastDiv::make(n3),
+                                                            FastDiv::make(m.nx));
+    return dss_typed(op, dst, flags, s, 1);
+}
+
+cudaError_t dss_from(const Op &op, const void *src, void *dst, int flags, cudaStream_t s)
+{
+    switch (vec_elem_size(op.prec)) {
+    case 8: return dss_from_typed(op, static_cast<const double *>(src), static_cast<double *>(dst), flags, s);
+    case 4: return dss_from_typed(op, static_cast<const float *>(src), static_cast<float *>(dst), flags, s);
+    default:
+        return dss_from_typed(op, static_cast<const __nv_bfloat16 *>(src), static_cast<__nv_bfloat16 *>(dst), flags, s);
+    }
+}
+
+cudaError_t dss_from_f64(const Op &op, const double *src, double *dst, int flags, cudaStream_t s)
+{
+    return dss_from_typed(op, src, dst, flags, s);
+}
+
+template <class VS>
+static cudaError_t dss_typed(const Op &op, VS *v, int flags, cudaStream_t s, int first_axis)
 {
     const Mesh &m = *op.mesh;
     const int dims[3] = {m.nx, m.ny, m.nz};
     const int n2 = op.n * op.n;
-    for (int ax = 0; ax < 3; ++ax) {
+    for (int ax = first_axis; ax < 3; ++ax) {
         if (dims[ax] < 2) continue;
         // in-face coordinates: a = lower of the two other axes (x-index part), b = the other (grid y)
         const int a = (ax == 0) ? 1 : 0, b = (ax == 2) ? 1 : 2;

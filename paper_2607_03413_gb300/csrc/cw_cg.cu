@@ -92,13 +92,42 @@ __device__ __forceinline__ void block_sum_store(double v, double *out)
     __syncthreads();
 }
 
+// 16-byte chunks of a vector (float4 / double2 loads and stores); every vector here is the start
+// of a cudaMalloc allocation, so chunk k at element k*W is 16-byte aligned; the last n % W
+// elements are handled one by one
+template <class V>
+struct __align__(16) Chunk {
+    static constexpr int W = 16 / sizeof(V);
+    V v[W];
+};
+template <class V>
+__device__ __forceinline__ Chunk<V> ldc(const V *p, int64_t k)
+{
+    return reinterpret_cast<const Chunk<V> *>(p)[k];
+}
+template <class V>
+__device__ __forceinline__ void stc(V *p, int64_t k, const Chunk<V> &c)
+{
+    reinterpret_cast<Chunk<V> *>(p)[k] = c;
+}
+
+#define CW_GRID_LOOP(i, n)                                                                          \
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
 // partial <a, b> with double-float accumulation (products exact in the FP32-pair format)
 template <class V>
 __global__ void __launch_bounds__(kRedThreads) k_dot(const V *__restrict__ a, const V *__restrict__ b, int64_t n,
                                                      double *__restrict__ part)
 {
+    constexpr int W = Chunk<V>::W;
     df64 acc{0.0f, 0.0f};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    CW_GRID_LOOP(k, n / W)
+    {
+        const Chunk<V> ca = ldc(a, k), cb = ldc(b, k);
+#pragma unroll
+        for (int l = 0; l < W; ++l) df_mad(acc, as_df(ca.v[l]), as_df(cb.v[l]));
+    }
+    for (int64_t i = n / W * W + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         df_mad(acc, as_df(a[i]), as_df(b[i]));
     block_sum_store(df_to_double(acc), part);
 }
@@ -117,11 +146,22 @@ __device__ __host__ __forceinline__ int entry_valence(int64_t t, int nx, int ny,
     return v;
 }
 
-
 // Given w = S r: z = dinv * w (in place on w), r <- w / kappa (the averaged dual S_bar r, which has
 // the same assembly G^T r, so every later use of r is unchanged, but each copy now carries 1/kappa
 // of the assembled value instead of a partial integral with cancellation), and partials
 // <r, z> and <m w, r> (m = dinv != 0) = ||m G^T r||^2.
+template <class V>
+__device__ __forceinline__ void precond_one(V &r, V &w, V d, uint8_t kap, df64 &a1, df64 &a2)
+{
+    const V wi = w;
+    const V zi = d * wi;
+    const V ri = wi / V(kap);
+    w = zi;
+    r = ri;
+    df_mad(a1, as_df(ri), as_df(zi));
+    if (d != V(0)) df_mad(a2, as_df(wi), as_df(ri));
+}
+
 template <class V>
 __global__ void __launch_bounds__(kRedThreads) k_precond(V *__restrict__ r, V *__restrict__ w,
                                                          const V *__restrict__ dinv, int64_t n,
@@ -129,16 +169,19 @@ __global__ void __launch_bounds__(kRedThreads) k_precond(V *__restrict__ r, V *_
                                                          double *__restrict__ part, const int *__restrict__ flags)
 {
     if (flags[F_DONE]) return;
+    constexpr int W = Chunk<V>::W;
     df64 a1{0.0f, 0.0f}, a2{0.0f, 0.0f};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const V d = dinv[i], wi = w[i];
-        const V zi = d * wi;
-        const V ri = wi / V(kappa[i]);
-        w[i] = zi;
-        r[i] = ri;
-        df_mad(a1, as_df(ri), as_df(zi));
-        if (d != V(0)) df_mad(a2, as_df(wi), as_df(ri));
+    CW_GRID_LOOP(k, n / W)
+    {
+        Chunk<V> cr = ldc(r, k), cw = ldc(w, k);
+        const Chunk<V> cd = ldc(dinv, k);
+#pragma unroll
+        for (int l = 0; l < W; ++l) precond_one(cr.v[l], cw.v[l], cd.v[l], kappa[k * W + l], a1, a2);
+        stc(r, k, cr);
+        stc(w, k, cw);
     }
+    for (int64_t i = n / W * W + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        precond_one(r[i], w[i], dinv[i], kappa[i], a1, a2);
     block_sum_store(df_to_double(a1), part);
     block_sum_store(df_to_double(a2), part + gridDim.x);
 }
@@ -148,11 +191,24 @@ template <class V, class U>
 __global__ void k_update(U *__restrict__ u, const V *__restrict__ p, V *__restrict__ r, const V *__restrict__ q,
                          int64_t n, const double *__restrict__ scal, const int *__restrict__ flags)
 {
+    static_assert(sizeof(U) == sizeof(V), "iterate and vectors share one type");
     if (!flags[F_ACTIVE]) return;
-    const double alpha = scal[S_ALPHA];
-    const V a = static_cast<V>(alpha);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        u[i] = u[i] + static_cast<U>(a) * static_cast<U>(p[i]);
+    const V a = static_cast<V>(scal[S_ALPHA]);
+    constexpr int W = Chunk<V>::W;
+    CW_GRID_LOOP(k, n / W)
+    {
+        Chunk<V> cu = ldc(reinterpret_cast<const V *>(u), k), cr = ldc(r, k);
+        const Chunk<V> cp = ldc(p, k), cq = ldc(q, k);
+#pragma unroll
+        for (int l = 0; l < W; ++l) {
+            cu.v[l] = cu.v[l] + a * cp.v[l];
+            cr.v[l] = cr.v[l] - a * cq.v[l];
+        }
+        stc(reinterpret_cast<V *>(u), k, cu);
+        stc(r, k, cr);
+    }
+    for (int64_t i = n / W * W + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        u[i] = u[i] + a * p[i];
         r[i] = r[i] - a * q[i];
     }
 }
@@ -164,7 +220,16 @@ __global__ void k_pupdate(V *__restrict__ p, const V *__restrict__ z, int64_t n,
 {
     if (!flags[F_ACTIVE] || flags[F_STATUS] == ST_BREAKDOWN) return;
     const V beta = static_cast<V>(scal[S_BETA]);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    constexpr int W = Chunk<V>::W;
+    CW_GRID_LOOP(k, n / W)
+    {
+        Chunk<V> cp = ldc(p, k);
+        const Chunk<V> cz = ldc(z, k);
+#pragma unroll
+        for (int l = 0; l < W; ++l) cp.v[l] = cz.v[l] + beta * cp.v[l];
+        stc(p, k, cp);
+    }
+    for (int64_t i = n / W * W + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = z[i] + beta * p[i];
 }
 
@@ -374,8 +439,7 @@ static cudaError_t cg_iteration(const Op &aop, int ak, CgLevel &lv, U *u, CgScra
     k_dot<V><<<vec_grid(), kRedThreads, 0, s>>>(p, q, L, c.partials);
     k_finalize<<<1, kRedThreads, 0, s>>>(c.partials, kRedBlocks, c.scal, c.flags, STAGE_PQ);
     k_update<V, U><<<vec_grid(), 256, 0, s>>>(u, p, r, q, L, c.scal, c.flags);
-    k_copy<V, V><<<vec_grid(), 256, 0, s>>>(z, r, L);
-    if ((e = dss_launch(aop, z, CW_DSS_SUM, s)) != cudaSuccess) return e;
+    if ((e = dss_from(aop, r, z, CW_DSS_SUM, s)) != cudaSuccess) return e;  // z = S r
     k_precond<V><<<vec_grid(), kRedThreads, 0, s>>>(r, z, dinv, L, c.kappa, c.partials, c.flags);
     k_finalize<<<1, kRedThreads, 0, s>>>(c.partials, kRedBlocks, c.scal, c.flags, STAGE_RHO);
     k_pupdate<V><<<vec_grid(), 256, 0, s>>>(p, z, L, c.scal, c.flags);
@@ -402,11 +466,10 @@ static cw_status cg_run(const Op &aop, int ak, CgLevel &lv, U *u, CgScratch &c, 
     CW_CUDA_TRY(cudaMemcpyAsync(c.flags + F_DONE, &c.h_flags[0], sizeof(int), cudaMemcpyHostToDevice, s));
     CW_CUDA_TRY(cudaMemcpyAsync(c.flags + F_MAXIT, &c.h_flags[1], sizeof(int), cudaMemcpyHostToDevice, s));
     // z = D^-1 S r, r <- S_bar r, rho = <r, z>, res0 = <m S r, r>, p = z
-    k_copy<V, V><<<vec_grid(), 256, 0, s>>>(z, r, L);
-    CW_CUDA_TRY(dss_launch(aop, z, CW_DSS_SUM, s));
+    CW_CUDA_TRY(dss_from(aop, r, z, CW_DSS_SUM, s));
     k_precond<V><<<vec_grid(), kRedThreads, 0, s>>>(r, z, dinv, L, c.kappa, c.partials, c.flags);
     k_finalize<<<1, kRedThreads, 0, s>>>(c.partials, kRedBlocks, c.scal, c.flags, STAGE_INIT);
-    if (!keep_p) k_copy<V, V><<<vec_grid(), 256, 0, s>>>(p, z, L);
+    if (!keep_p) CW_CUDA_TRY(cudaMemcpyAsync(p, z, L * sizeof(V), cudaMemcpyDeviceToDevice, s));
     CW_CUDA_TRY(cudaGetLastError());
     // one eager iteration (first-use initialisation of the kernels), then graph batches
     CW_CUDA_TRY((cg_iteration<V, U>(aop, ak, lv, u, c, s)));
@@ -524,9 +587,8 @@ static cw_status residual_norm2(const Op &op, const double *r, double *w, CgScra
     cudaStream_t s = c.stream;
     const int64_t L = op.L;
     double *rr = static_cast<double *>(c.lv64.r);  // scratch copy: k_precond averages it in place
-    k_copy<double, double><<<vec_grid(), 256, 0, s>>>(w, r, L);
-    k_copy<double, double><<<vec_grid(), 256, 0, s>>>(rr, r, L);
-    CW_CUDA_TRY(dss_launch(op, w, CW_DSS_SUM, s));
+    CW_CUDA_TRY(dss_from(op, r, w, CW_DSS_SUM, s));
+    CW_CUDA_TRY(cudaMemcpyAsync(rr, r, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CW_CUDA_TRY(cudaMemsetAsync(c.flags + F_DONE, 0, sizeof(int), s));
     k_precond<double><<<vec_grid(), kRedThreads, 0, s>>>(rr, w, static_cast<double *>(c.lv64.dinv), L, c.kappa,
                                                          c.partials, c.flags);
@@ -551,8 +613,7 @@ static cw_status energy(const Op &op, const double *r, const double *u, CgScratc
 // S_bar r (averaging DSS, Eq. (averaging_dss)) of the FP64 residual into the inner level's rhs
 static cw_status averaged_rhs(const Op &op, const double *r, double *work, void *dst, bool to_f32, cudaStream_t s)
 {
-    k_copy<double, double><<<vec_grid(), 256, 0, s>>>(work, r, op.L);
-    CW_CUDA_TRY(dss_launch(op, work, CW_DSS_AVERAGE, s));
+    CW_CUDA_TRY(dss_from(op, r, work, CW_DSS_AVERAGE, s));
     if (to_f32)
         k_copy<float, double><<<vec_grid(), 256, 0, s>>>(static_cast<float *>(dst), work, op.L);
     else

@@ -61,6 +61,9 @@ cudaError_t apply_launch_f32(const Op &op, const void *x, void *y, cudaStream_t 
 // dispatch to the right unit
 cudaError_t apply_local(const Op &op, const void *x, void *y, cudaStream_t s);
 cudaError_t dss_launch(const Op &op, void *v, int flags, cudaStream_t s);
+// out of place: dst = S src (flags CW_DSS_SUM) or S_bar src (CW_DSS_AVERAGE); the x pass is fused
+// with the copy
+cudaError_t dss_from(const Op &op, const void *src, void *dst, int flags, cudaStream_t s);
 
 // solver scratch release (cw_cg.cu)
 void cg_release(Op *op);
