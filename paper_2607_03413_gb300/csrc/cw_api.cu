@@ -321,20 +321,26 @@ __global__ void scale_by_valence_kernel(VS *__restrict__ v, int nx, int ny, int 
 // partner copy in the neighbouring cell, every other entry is copied (out of place, so the read of
 // a partner never sees an updated value). Replaces a copy and an in-place x pass with one pass.
 template <class VS>
-__global__ void dss_x_from_kernel(const VS *__restrict__ src, VS *__restrict__ dst, int nx, int p, uint32_t L,
-                                  FastDiv fd_n3, FastDiv fd_nx)
+__global__ void dss_x_from_kernel(const VS *__restrict__ src, VS *__restrict__ dst, int nx, int p, uint32_t nlines,
+                                  FastDiv fd_n2, FastDiv fd_nx)
 {
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= L) return;
-    const uint32_t n = p + 1, n3 = fd_n3.d;
-    const uint32_t c = fd_n3.div(t);
-    const uint32_t loc = t - c * n3;
-    const uint32_t i = loc % n;
+    // one thread per x-line (n consecutive entries of a cell); only its two end entries have partners
+    const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nlines) return;
+    const int n = p + 1;
+    const uint32_t n3 = fd_n2.d * n;
+    const uint32_t c = fd_n2.div(l);
     const uint32_t cx = c - fd_nx.div(c) * static_cast<uint32_t>(nx);
-    VS v = src[t];
-    if (i == static_cast<uint32_t>(p) && cx + 1 < static_cast<uint32_t>(nx)) v = AddOp<VS>::add(v, src[t + n3 - p]);
-    else if (i == 0 && cx > 0) v = AddOp<VS>::add(src[t - n3 + p], v);
-    dst[t] = v;
+    const int64_t b = static_cast<int64_t>(l) * n;
+    VS v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        if (i < n) v[i] = src[b + i];
+    if (cx > 0) v[0] = AddOp<VS>::add(src[b - n3 + p], v[0]);
+    if (cx + 1 < static_cast<uint32_t>(nx)) v[p] = AddOp<VS>::add(v[p], src[b + n3]);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        if (i < n) dst[b + i] = v[i];
 }
 
 template <class VS>
@@ -350,10 +356,9 @@ static cudaError_t dss_from_typed(const Op &op, const VS *src, VS *dst, int flag
         if (e != cudaSuccess) return e;
         return dss_typed(op, dst, flags, s, 0);
     }
-    const int n3 = op.n * op.n * op.n;
-    const uint32_t L = (uint32_t)op.L;
-    dss_x_from_kernel<VS><<<(L + 255) / 256, 256, 0, s>>>(src, dst, m.nx, op.p, L, FastDiv::make(n3),
-                                                            FastDiv::make(m.nx));
+    const uint32_t nlines = (uint32_t)(op.L / op.n);
+    dss_x_from_kernel<VS><<<(nlines + 255) / 256, 256, 0, s>>>(src, dst, m.nx, op.p, nlines, FastDiv::make(op.n * op.n),
+                                                                 FastDiv::make(m.nx));
     return dss_typed(op, dst, flags, s, 1);
 }
 

@@ -41,7 +41,8 @@ enum : int { S_RHO = 0, S_PQ, S_ALPHA, S_BETA, S_RES0, S_RES, S_RHO_NEW, S_TOL2,
 // F_ACTIVE: the current iteration started before convergence (set at its <p,Ap> stage); its
 // direction update p = z + beta p runs even if the iteration converges, so that a later segment
 // can continue from a consistent (r, p) pair
-enum : int { F_DONE = 0, F_ITER, F_STATUS, F_MAXIT, F_ACTIVE, F_NFLAG = 8 };
+// F_BLOCKS: arrival counter of the fused reductions (last block finalises, then resets it)
+enum : int { F_DONE = 0, F_ITER, F_STATUS, F_MAXIT, F_ACTIVE, F_BLOCKS = 7, F_NFLAG = 8 };
 enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_MAXIT = 3 };
 
 struct CgLevel {  // vectors of one precision level
@@ -301,9 +302,8 @@ __device__ __forceinline__ double sum_partials(const double *part, int nb)
 enum : int { STAGE_INIT = 0, STAGE_PQ = 1, STAGE_RHO = 2, STAGE_RES = 3, STAGE_ENERGY = 4 };
 
 // turns block partials into scalars and runs the CG scalar logic for one stage (one block)
-__global__ void __launch_bounds__(kRedThreads) k_finalize(const double *__restrict__ part, int nb,
-                                                          double *__restrict__ scal, int *__restrict__ flags,
-                                                          int stage)
+__device__ __forceinline__ void finalize_body(const double *__restrict__ part, int nb, double *__restrict__ scal,
+                                              int *__restrict__ flags, int stage)
 {
     if (stage == STAGE_PQ && flags[F_DONE]) {  // an iteration after convergence: a no-op
         if (threadIdx.x == 0) flags[F_ACTIVE] = 0;
@@ -357,6 +357,74 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const double *__restri
     } else {
         scal[S_ENERGY] = s0;
     }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_finalize(const double *__restrict__ part, int nb,
+                                                          double *__restrict__ scal, int *__restrict__ flags,
+                                                          int stage)
+{
+    finalize_body(part, nb, scal, flags, stage);
+}
+
+// called by every block after block_sum_store: the last block to arrive (threadfence reduction)
+// sums all partials and runs the stage logic, so no separate finalize launch is needed
+__device__ __forceinline__ void last_block_finalize(const double *__restrict__ part, double *__restrict__ scal,
+                                                    int *__restrict__ flags, int stage)
+{
+    __shared__ int s_last;
+    __threadfence();
+    if (threadIdx.x == 0)
+        s_last = (atomicAdd(reinterpret_cast<unsigned *>(flags + F_BLOCKS), 1u) == gridDim.x - 1) ? 1 : 0;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    finalize_body(part, gridDim.x, scal, flags, stage);
+    if (threadIdx.x == 0) flags[F_BLOCKS] = 0;
+}
+
+template <class V>
+__global__ void __launch_bounds__(kRedThreads) k_dot_fin(const V *__restrict__ a, const V *__restrict__ b, int64_t n,
+                                                         double *__restrict__ part, double *__restrict__ scal,
+                                                         int *__restrict__ flags, int stage)
+{
+    constexpr int W = Chunk<V>::W;
+    df64 acc{0.0f, 0.0f};
+    CW_GRID_LOOP(k, n / W)
+    {
+        const Chunk<V> ca = ldc(a, k), cb = ldc(b, k);
+#pragma unroll
+        for (int l = 0; l < W; ++l) df_mad(acc, as_df(ca.v[l]), as_df(cb.v[l]));
+    }
+    for (int64_t i = n / W * W + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        df_mad(acc, as_df(a[i]), as_df(b[i]));
+    block_sum_store(df_to_double(acc), part);
+    last_block_finalize(part, scal, flags, stage);
+}
+
+template <class V>
+__global__ void __launch_bounds__(kRedThreads) k_precond_fin(V *__restrict__ r, V *__restrict__ w,
+                                                             const V *__restrict__ dinv, int64_t n,
+                                                             const uint8_t *__restrict__ kappa,
+                                                             double *__restrict__ part, double *__restrict__ scal,
+                                                             int *__restrict__ flags, int stage)
+{
+    if (stage == STAGE_RHO && flags[F_DONE]) return;  // an iteration after convergence
+    constexpr int W = Chunk<V>::W;
+    df64 a1{0.0f, 0.0f}, a2{0.0f, 0.0f};
+    CW_GRID_LOOP(k, n / W)
+    {
+        Chunk<V> cr = ldc(r, k), cw = ldc(w, k);
+        const Chunk<V> cd = ldc(dinv, k);
+#pragma unroll
+        for (int l = 0; l < W; ++l) precond_one(cr.v[l], cw.v[l], cd.v[l], kappa[k * W + l], a1, a2);
+        stc(r, k, cr);
+        stc(w, k, cw);
+    }
+    for (int64_t i = n / W * W + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        precond_one(r[i], w[i], dinv[i], kappa[i], a1, a2);
+    block_sum_store(df_to_double(a1), part);
+    block_sum_store(df_to_double(a2), part + gridDim.x);
+    last_block_finalize(part, scal, flags, stage);
 }
 
 // --------------------------------------------------------------------------- host side ----
@@ -436,12 +504,11 @@ static cudaError_t cg_iteration(const Op &aop, int ak, CgLevel &lv, U *u, CgScra
       *z = static_cast<V *>(lv.z), *dinv = static_cast<V *>(lv.dinv);
     cudaError_t e = apply_by_kind(aop, ak, p, q, s);
     if (e != cudaSuccess) return e;
-    k_dot<V><<<vec_grid(), kRedThreads, 0, s>>>(p, q, L, c.partials);
-    k_finalize<<<1, kRedThreads, 0, s>>>(c.partials, kRedBlocks, c.scal, c.flags, STAGE_PQ);
+    k_dot_fin<V><<<vec_grid(), kRedThreads, 0, s>>>(p, q, L, c.partials, c.scal, c.flags, STAGE_PQ);
     k_update<V, U><<<vec_grid(), 256, 0, s>>>(u, p, r, q, L, c.scal, c.flags);
     if ((e = dss_from(aop, r, z, CW_DSS_SUM, s)) != cudaSuccess) return e;  // z = S r
-    k_precond<V><<<vec_grid(), kRedThreads, 0, s>>>(r, z, dinv, L, c.kappa, c.partials, c.flags);
-    k_finalize<<<1, kRedThreads, 0, s>>>(c.partials, kRedBlocks, c.scal, c.flags, STAGE_RHO);
+    k_precond_fin<V><<<vec_grid(), kRedThreads, 0, s>>>(r, z, dinv, L, c.kappa, c.partials, c.scal, c.flags,
+                                                        STAGE_RHO);
     k_pupdate<V><<<vec_grid(), 256, 0, s>>>(p, z, L, c.scal, c.flags);
     return cudaGetLastError();
 }
@@ -467,8 +534,8 @@ static cw_status cg_run(const Op &aop, int ak, CgLevel &lv, U *u, CgScratch &c, 
     CW_CUDA_TRY(cudaMemcpyAsync(c.flags + F_MAXIT, &c.h_flags[1], sizeof(int), cudaMemcpyHostToDevice, s));
     // z = D^-1 S r, r <- S_bar r, rho = <r, z>, res0 = <m S r, r>, p = z
     CW_CUDA_TRY(dss_from(aop, r, z, CW_DSS_SUM, s));
-    k_precond<V><<<vec_grid(), kRedThreads, 0, s>>>(r, z, dinv, L, c.kappa, c.partials, c.flags);
-    k_finalize<<<1, kRedThreads, 0, s>>>(c.partials, kRedBlocks, c.scal, c.flags, STAGE_INIT);
+    k_precond_fin<V><<<vec_grid(), kRedThreads, 0, s>>>(r, z, dinv, L, c.kappa, c.partials, c.scal, c.flags,
+                                                        STAGE_INIT);
     if (!keep_p) CW_CUDA_TRY(cudaMemcpyAsync(p, z, L * sizeof(V), cudaMemcpyDeviceToDevice, s));
     CW_CUDA_TRY(cudaGetLastError());
     // one eager iteration (first-use initialisation of the kernels), then graph batches
