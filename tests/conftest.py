@@ -10,7 +10,7 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the compiled library")
-    config.addinivalue_line("markers", "slow: long-running test")
+    config.addinivalue_line("markers", "slow: long-running test (full workload sizes)")
 
 
 @pytest.fixture(scope="session")
