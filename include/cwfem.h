@@ -158,6 +158,17 @@ cw_status cw_gather(cw_op op, const double *u_global, void *x, void *stream);
 cw_status cw_apply(cw_op op, const void *x, void *y, int flags, void *stream);
 
 /*
+ * y = A x or S A x with x and y in HOST memory (layout and type as for cw_apply; page-locked memory
+ * gives full copy bandwidth). The cells are processed in slabs of whole z-layers (at most 16): the
+ * host-to-device copy of one slab overlaps the work on the previous one, and each slab is copied back
+ * as soon as it is final (for CW_APPLY_ASSEMBLE, after the DSS across its interface with the next
+ * slab). Asynchronous on `stream`: x and y must stay valid, and y must not be read, until `stream`
+ * reaches the end of the call. The first call allocates two device vectors, three streams and events
+ * owned by the op.
+ */
+cw_status cw_apply_host(cw_op op, const void *x_host, void *y_host, int flags, void *stream);
+
+/*
  * In-place DSS on a cell-wise device array of the op's vector type: v <- S v (CW_DSS_SUM,
  * Algorithm struct_dss: three sequential axis passes over all interior faces) or
  * v <- S_bar v (CW_DSS_AVERAGE: the sum divided by the DoF valence).

@@ -34,7 +34,7 @@ EXPORTED = [
     "cw_apply", "cw_dss", "cw_diagonal", "cw_load_vector", "cw_cg_solve", "cw_op_set_variant",
     "cw_op_get_variant", "cw_op_autotune", "cw_cg_solve_noalloc", "cw_batch_create", "cw_batch_destroy",
     "cw_batch_values", "cw_batch_launch", "cw_batch_graph_launch", "cw_batch_set_variant",
-    "cw_batch_get_variant", "cw_batch_autotune", "cw_batch_set_mode",
+    "cw_batch_get_variant", "cw_batch_autotune", "cw_batch_set_mode", "cw_apply_host",
 ]
 
 
@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH):
         "cw_batch_get_variant": ([vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "cw_batch_autotune": ([vp, i32, vp, ctypes.POINTER(ctypes.c_float)], i32),
         "cw_batch_set_mode": ([vp, i32], i32),
+        "cw_apply_host": ([vp, vp, vp, i32, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -170,6 +171,20 @@ def cw_gather(op, u_global, x, stream=None):
 
 def cw_apply(op, x, y, flags=CW_APPLY_LOCAL, stream=None):
     _check(load().cw_apply(op, _ptr(x), _ptr(y), flags, _stream(stream)), "cw_apply")
+
+
+def _host_ptr(t):
+    if hasattr(t, "data_ptr"):
+        if getattr(t, "is_cuda", False):
+            raise ValueError("expected a host (CPU) tensor")
+        if not t.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def cw_apply_host(op, x_host, y_host, flags=CW_APPLY_LOCAL, stream=None):
+    _check(load().cw_apply_host(op, _host_ptr(x_host), _host_ptr(y_host), flags, _stream(stream)), "cw_apply_host")
 
 
 def cw_dss(op, v, flags=CW_DSS_SUM, stream=None):

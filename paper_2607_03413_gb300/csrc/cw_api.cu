@@ -4,10 +4,12 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "cw_apply.cuh"
 #include "cw_internal.h"
@@ -344,7 +346,7 @@ __global__ void dss_x_from_kernel(const VS *__restrict__ src, VS *__restrict__ d
 }
 
 template <class VS>
-static cudaError_t dss_typed(const Op &op, VS *v, int flags, cudaStream_t s, int first_axis = 0);
+static cudaError_t dss_typed(const Op &op, VS *v, int flags, cudaStream_t s, int first_axis = 0, int end_axis = 3);
 
 // dst = S src (or S_bar src), src unchanged; src and dst must not overlap
 template <class VS>
@@ -378,12 +380,12 @@ cudaError_t dss_from_f64(const Op &op, const double *src, double *dst, int flags
 }
 
 template <class VS>
-static cudaError_t dss_typed(const Op &op, VS *v, int flags, cudaStream_t s, int first_axis)
+static cudaError_t dss_typed(const Op &op, VS *v, int flags, cudaStream_t s, int first_axis, int end_axis)
 {
     const Mesh &m = *op.mesh;
     const int dims[3] = {m.nx, m.ny, m.nz};
     const int n2 = op.n * op.n;
-    for (int ax = first_axis; ax < 3; ++ax) {
+    for (int ax = first_axis; ax < end_axis; ++ax) {
         if (dims[ax] < 2) continue;
         // in-face coordinates: a = lower of the two other axes (x-index part), b = the other (grid y)
         const int a = (ax == 0) ? 1 : 0, b = (ax == 2) ? 1 : 2;
@@ -407,6 +409,16 @@ cudaError_t dss_launch(const Op &op, void *v, int flags, cudaStream_t s)
     case 8: return dss_typed(op, static_cast<double *>(v), flags, s);
     case 4: return dss_typed(op, static_cast<float *>(v), flags, s);
     default: return dss_typed(op, static_cast<__nv_bfloat16 *>(v), flags, s);
+    }
+}
+
+// sum passes of the axes [ax0, ax1) only (no averaging); used on slab views of the mesh
+static cudaError_t dss_axes(const Op &op, void *v, int ax0, int ax1, cudaStream_t s)
+{
+    switch (vec_elem_size(op.prec)) {
+    case 8: return dss_typed(op, static_cast<double *>(v), CW_DSS_SUM, s, ax0, ax1);
+    case 4: return dss_typed(op, static_cast<float *>(v), CW_DSS_SUM, s, ax0, ax1);
+    default: return dss_typed(op, static_cast<__nv_bfloat16 *>(v), CW_DSS_SUM, s, ax0, ax1);
     }
 }
 
@@ -644,6 +656,14 @@ cw_status cw_op_destroy(cw_op oh)
     if (!op) return fail(CW_ERR_ARG, "cw_op_destroy: NULL");
     cg_release(op);
     if (op->inner) cw_op_destroy(reinterpret_cast<cw_op>(op->inner));
+    cudaFree(op->h_dx);
+    cudaFree(op->h_dy);
+    for (int i = 0; i < 3; ++i)
+        if (op->h_st[i]) cudaStreamDestroy(op->h_st[i]);
+    for (int a = 0; a < 2; ++a)
+        for (int k = 0; k < 16; ++k)
+            if (op->h_ev[a][k]) cudaEventDestroy(op->h_ev[a][k]);
+    if (op->h_done) cudaEventDestroy(op->h_done);
     cudaFree(op->d_geo);
     cudaFree(op->d_dinv);
     delete op;
@@ -819,6 +839,106 @@ cw_status cw_op_autotune(cw_op oh, const void *x, void *y, int reps, void *strea
     op->cpb = bc;
     op->stage = bs;
     if (best_ms) *best_ms = best;
+    return CW_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+// Apply with host input and output. The cells are split into slabs of whole z-layers: the
+// host-to-device copy of slab k overlaps the work of slab k-1. For CW_APPLY_LOCAL slab k is copied
+// back as soon as its apply is done. For CW_APPLY_ASSEMBLE each slab runs its apply, its x and y DSS
+// passes and the z pass of its interior interfaces, then the z pass of the interface with slab k-1;
+// the DSS cascade couples slabs only through that interface, so slab k-1 is then final and its
+// copy back overlaps the work on slab k.
+cw_status cw_apply_host(cw_op oh, const void *x_host, void *y_host, int flags, void *stream)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    if (!op || !x_host || !y_host) return fail(CW_ERR_ARG, "cw_apply_host: NULL argument");
+    if (flags != CW_APPLY_LOCAL && flags != CW_APPLY_ASSEMBLE) return fail(CW_ERR_ARG, "cw_apply_host: bad flags");
+    if (x_host == y_host) return fail(CW_ERR_ARG, "cw_apply_host: x and y must not alias");
+    const size_t es = vec_elem_size(op->prec);
+    const int64_t n3 = (int64_t)op->n * op->n * op->n;
+    if (!op->h_dx) {
+        CW_CUDA_TRY(cudaMalloc(&op->h_dx, op->L * es));
+        CW_CUDA_TRY(cudaMalloc(&op->h_dy, op->L * es));
+        for (int i = 0; i < 3; ++i) CW_CUDA_TRY(cudaStreamCreateWithFlags(&op->h_st[i], cudaStreamNonBlocking));
+        for (int a = 0; a < 2; ++a)
+            for (int k = 0; k < 16; ++k) CW_CUDA_TRY(cudaEventCreateWithFlags(&op->h_ev[a][k], cudaEventDisableTiming));
+        CW_CUDA_TRY(cudaEventCreateWithFlags(&op->h_done, cudaEventDisableTiming));
+        op->owned_bytes += 2 * op->L * (int64_t)es;
+    }
+    cudaStream_t us = static_cast<cudaStream_t>(stream);
+    cudaStream_t sin = op->h_st[0], scomp = op->h_st[1], sout = op->h_st[2];
+    CW_CUDA_TRY(cudaEventRecord(op->h_done, us));  // order after the caller's stream
+    for (int i = 0; i < 3; ++i) CW_CUDA_TRY(cudaStreamWaitEvent(op->h_st[i], op->h_done, 0));
+    const Mesh &m = *op->mesh;
+    const int64_t plane = (int64_t)m.nx * m.ny;  // cells per z-layer
+    const int planes = std::max(1, (m.nz + 7) / 8);
+    const int nslab = (m.nz + planes - 1) / planes;
+    const size_t gbytes_per_cell = op->geo_bytes / op->E;
+    unsigned char *dx = static_cast<unsigned char *>(op->h_dx), *dy = static_cast<unsigned char *>(op->h_dy);
+    const unsigned char *hx = static_cast<const unsigned char *>(x_host);
+    unsigned char *hy = static_cast<unsigned char *>(y_host);
+    // a view of the operator on z-layers [z0, z0 + nzv)
+    std::vector<Mesh> views(nslab + 1);
+    auto view = [&](int vi, int z0, int nzv, Op &o) {
+        views[vi] = m;
+        views[vi].nz = nzv;
+        views[vi].h_verts.clear();
+        o = *op;
+        o.mesh = &views[vi];
+        o.E = plane * nzv;
+        o.L = o.E * n3;
+        o.d_geo = static_cast<unsigned char *>(op->d_geo) + z0 * plane * gbytes_per_cell;
+    };
+    auto slab_bytes = [&](int k, size_t &off, size_t &bytes) {
+        const int64_t z0 = (int64_t)k * planes, nz = std::min<int64_t>(planes, m.nz - z0);
+        off = (size_t)(z0 * plane * n3) * es;
+        bytes = (size_t)(nz * plane * n3) * es;
+    };
+    Mesh bview = m;  // two-layer view across a slab interface
+    bview.nz = 2;
+    bview.h_verts.clear();
+    for (int k = 0; k < nslab; ++k) {
+        size_t off, bytes;
+        slab_bytes(k, off, bytes);
+        const int z0 = k * planes, nzk = std::min(planes, m.nz - z0);
+        CW_CUDA_TRY(cudaMemcpyAsync(dx + off, hx + off, bytes, cudaMemcpyHostToDevice, sin));
+        CW_CUDA_TRY(cudaEventRecord(op->h_ev[0][k], sin));
+        CW_CUDA_TRY(cudaStreamWaitEvent(scomp, op->h_ev[0][k], 0));
+        Op part;
+        view(k, z0, nzk, part);
+        CW_CUDA_TRY(apply_local(part, dx + off, dy + off, scomp));
+        if (flags == CW_APPLY_ASSEMBLE) {
+            CW_CUDA_TRY(dss_axes(part, dy + off, 0, 3, scomp));  // x, y and interior z interfaces
+            if (k > 0) {
+                Op bop = *op;
+                bop.mesh = &bview;
+                bop.E = plane * 2;
+                bop.L = bop.E * n3;
+                const size_t boff = (size_t)((int64_t)(z0 - 1) * plane * n3) * es;
+                CW_CUDA_TRY(dss_axes(bop, dy + boff, 2, 3, scomp));  // the interface with slab k-1
+            }
+        }
+        CW_CUDA_TRY(cudaEventRecord(op->h_ev[1][k], scomp));
+        const int ready = (flags == CW_APPLY_ASSEMBLE) ? k - 1 : k;  // slab that is final now
+        if (ready >= 0) {
+            size_t roff, rbytes;
+            slab_bytes(ready, roff, rbytes);
+            CW_CUDA_TRY(cudaStreamWaitEvent(sout, op->h_ev[1][k], 0));
+            CW_CUDA_TRY(cudaMemcpyAsync(hy + roff, dy + roff, rbytes, cudaMemcpyDeviceToHost, sout));
+        }
+    }
+    if (flags == CW_APPLY_ASSEMBLE) {  // the last slab
+        size_t roff, rbytes;
+        slab_bytes(nslab - 1, roff, rbytes);
+        CW_CUDA_TRY(cudaStreamWaitEvent(sout, op->h_ev[1][nslab - 1], 0));
+        CW_CUDA_TRY(cudaMemcpyAsync(hy + roff, dy + roff, rbytes, cudaMemcpyDeviceToHost, sout));
+    }
+    CW_CUDA_TRY(cudaEventRecord(op->h_done, sout));
+    CW_CUDA_TRY(cudaStreamWaitEvent(us, op->h_done, 0));
     return CW_OK;
 }
 

@@ -45,6 +45,11 @@ struct Op {
     double *d_dinv = nullptr;  // cell-wise masked inverse diagonal (solver), lazily
     CgScratch *cg = nullptr;
     Op *inner = nullptr;  // reduced-precision twin used by iterative refinement
+    // host-buffer apply (cw_apply_host): device staging vectors, streams and events, lazily
+    void *h_dx = nullptr, *h_dy = nullptr;
+    cudaStream_t h_st[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t h_ev[2][16] = {};
+    cudaEvent_t h_done = nullptr;
     int cpb = 0;          // apply kernel variant: cells per CTA (0 = default for the degree)
     int stage = 1;        // apply kernel variant: TMA staging of the input and metric tiles
     int64_t owned_bytes = 0;
