@@ -179,10 +179,12 @@ __host__ __device__ constexpr size_t metric_smem_bytes(int nc, int stage)
 // One tile of `cpt` consecutive cells starting at cell tile*cpt, worked by CPB cell slots of N*N
 // threads (cpt <= CPB; slots c >= cpt compute on zeros and store nothing, so a CTA may have more
 // threads than the tile needs). STAGE (see metric_smem_bytes; staging needs cpt == CPB).
-template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
+// DOT: also accumulate this thread's share of <x, y> over its final x-line into *dot (double-float
+// products of the values as stored in y; the x line is re-read from global memory, L1/L2-resident).
+template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool DOT = false>
 __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__restrict__ y, const GS *__restrict__ geo,
                                             int64_t ncells, int kind, const TabMetric<N, typename Ar::C> &tab,
-                                            int64_t tile, int cpt, unsigned char *smem_raw)
+                                            int64_t tile, int cpt, unsigned char *smem_raw, df64 *dot = nullptr)
 {
     using T = typename Ar::T;
     using L = Lines<N>;
@@ -378,6 +380,15 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
                 VS *yc = yr + cell * N3 + N * r;
 #pragma unroll
                 for (int m = 0; m < N; ++m) Ar::to(yc[m], w[m]);
+                if constexpr (DOT) {
+                    const VS *xc = xr + cell * N3 + N * r;
+#pragma unroll
+                    for (int m = 0; m < N; ++m) {
+                        VS ys;
+                        Ar::to(ys, w[m]);
+                        df_mad(*dot, Ar::to_df(Ar::from(ldg_nc(xc + m))), Ar::to_df(Ar::from(ys)));
+                    }
+                }
             }
         }
     }
@@ -397,6 +408,35 @@ __global__ void __launch_bounds__(N *N *CPB) apply_metric_kernel(const VS *__res
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     metric_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw);
+}
+
+// y = A x and the CTA's partial of <x, y> in part[blockIdx.x] (deterministic: fixed order in a CTA)
+template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
+__global__ void __launch_bounds__(N *N *CPB) apply_metric_dot_kernel(const VS *__restrict__ x, VS *__restrict__ y,
+                                                                      const GS *__restrict__ geo, int64_t ncells,
+                                                                      int kind, TabMetric<N, typename Ar::C> tab,
+                                                                      double *__restrict__ part)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double s_red[(N * N * CPB + 31) / 32];
+    df64 acc{0.0f, 0.0f};
+    metric_tile<N, CPB, Ar, VS, GS, STAGE, true>(x, y, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw, &acc);
+    double v = df_to_double(acc);
+    // N^2 * CPB is not always a multiple of 32: the last warp may hold only nw lanes
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = min(32, N * N * CPB - wid * 32);
+    const unsigned mask = nw == 32 ? 0xffffffffu : ((1u << nw) - 1u);
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(mask, v, o);
+        if (lane + o < nw) v += ov;
+    }
+    if (lane == 0) s_red[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (N * N * CPB + 31) / 32; ++i) t += s_red[i];
+        part[blockIdx.x] = t;
+    }
 }
 
 // ---------------------------------------------------------------------- Cartesian kernel ----

@@ -145,6 +145,7 @@ struct ArDF {  // double-float arithmetic
     static __device__ __forceinline__ T from(float v) { return T{v, 0.0f}; }
     static __device__ __forceinline__ void to(double &d, T a) { d = df_to_double(a); }
     static __device__ __forceinline__ double to_f64(T a) { return df_to_double(a); }
+    static __device__ __forceinline__ df64 to_df(T a) { return a; }
 };
 
 struct ArF64 {  // native FP64
@@ -177,6 +178,7 @@ struct ArF32 {  // FP32
     static __device__ __forceinline__ void to(float &d, T a) { d = a; }
     static __device__ __forceinline__ void to(__nv_bfloat16 &d, T a) { d = __float2bfloat16_rn(a); }
     static __device__ __forceinline__ double to_f64(T a) { return static_cast<double>(a); }
+    static __device__ __forceinline__ df64 to_df(T a) { return df64{a, 0.0f}; }
 };
 
 }  // namespace cw

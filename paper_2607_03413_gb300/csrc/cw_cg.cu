@@ -60,6 +60,7 @@ struct CgScratch {
     double *d64 = nullptr;   // FP64 inner correction
     float *d32 = nullptr;    // FP32 inner correction
     double *partials = nullptr;
+    double *dotpart = nullptr;  // one <p, Ap> partial per apply CTA (at most one per cell)
     double *scal = nullptr;
     int *flags = nullptr;
     uint8_t *kappa = nullptr;  // valence of every cell-wise entry (1, 2, 4 or 8)
@@ -286,9 +287,19 @@ __global__ void k_make_dinv(const double *__restrict__ d, V *__restrict__ dinv, 
 __device__ __forceinline__ double sum_partials(const double *part, int nb)
 {
     __shared__ double sh[kRedThreads];
-    double v = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) v += part[i];
-    sh[threadIdx.x] = v;
+    // four independent accumulators keep four loads in flight per thread (nb reaches ~1e4 for the
+    // per-CTA partials of the operator epilogue)
+    const int bd = blockDim.x;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    int i = threadIdx.x;
+    for (; i + 3 * bd < nb; i += 4 * bd) {
+        v0 += part[i];
+        v1 += part[i + bd];
+        v2 += part[i + 2 * bd];
+        v3 += part[i + 3 * bd];
+    }
+    for (; i < nb; i += bd) v0 += part[i];
+    sh[threadIdx.x] = (v0 + v1) + (v2 + v3);
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
@@ -382,6 +393,18 @@ __device__ __forceinline__ void last_block_finalize(const double *__restrict__ p
     if (threadIdx.x == 0) flags[F_BLOCKS] = 0;
 }
 
+// sums nb partials (one per operator CTA) into this grid's block partials, then the last block
+// runs the stage logic
+__global__ void __launch_bounds__(kRedThreads) k_sum_fin(const double *__restrict__ in, int64_t nb,
+                                                         double *__restrict__ part, double *__restrict__ scal,
+                                                         int *__restrict__ flags, int stage)
+{
+    double v = 0.0;
+    CW_GRID_LOOP(i, nb) v += in[i];
+    block_sum_store(v, part);
+    last_block_finalize(part, scal, flags, stage);
+}
+
 template <class V>
 __global__ void __launch_bounds__(kRedThreads) k_dot_fin(const V *__restrict__ a, const V *__restrict__ b, int64_t n,
                                                          double *__restrict__ part, double *__restrict__ scal,
@@ -449,6 +472,25 @@ static cudaError_t apply_by_kind(const Op &op, int ak, const void *x, void *y, c
     return apply_local(op, x, y, s);
 }
 
+// whether q = A p can carry the <p, q> partials in its epilogue (curved cells, default tile and
+// TMA staging, double-float or FP32 arithmetic)
+static bool apply_dot_ok(const Op &op, int ak)
+{
+    if (ak == AK_NATIVE || op.geom != CW_GEOM_METRIC || op.stage != 1) return false;
+    static const int dflt[9] = {0, 0, 32, 16, 8, 8, 4, 4, 2};  // default cells per CTA by n
+    if (op.cpb != 0 && op.cpb != dflt[op.n]) return false;
+    return op.prec == CW_PREC_F64 || op.prec == CW_PREC_F32 || op.prec == CW_PREC_F32_BF16G;
+}
+
+static cudaError_t apply_dot_by_kind(const Op &op, const void *x, void *y, double *part, int64_t *nb, cudaStream_t s)
+{
+    switch (op.prec) {
+    case CW_PREC_F64: return apply_dot_launch_df(op, x, y, part, nb, s);
+    case CW_PREC_F32: return apply_dot_launch_f32(op, x, y, part, nb, s);
+    default: return apply_dot_launch_f32g16(op, x, y, part, nb, s);
+    }
+}
+
 template <class V>
 static cudaError_t alloc_level(CgLevel &lv, int64_t L, int64_t &bytes)
 {
@@ -483,6 +525,7 @@ void cg_release(Op *op)
     cudaFree(c->d64);
     cudaFree(c->d32);
     cudaFree(c->partials);
+    cudaFree(c->dotpart);
     cudaFree(c->scal);
     cudaFree(c->flags);
     cudaFree(c->kappa);
@@ -502,9 +545,16 @@ static cudaError_t cg_iteration(const Op &aop, int ak, CgLevel &lv, U *u, CgScra
     const int64_t L = aop.L;
     V *r = static_cast<V *>(lv.r), *p = static_cast<V *>(lv.p), *q = static_cast<V *>(lv.q),
       *z = static_cast<V *>(lv.z), *dinv = static_cast<V *>(lv.dinv);
-    cudaError_t e = apply_by_kind(aop, ak, p, q, s);
-    if (e != cudaSuccess) return e;
-    k_dot_fin<V><<<vec_grid(), kRedThreads, 0, s>>>(p, q, L, c.partials, c.scal, c.flags, STAGE_PQ);
+    cudaError_t e;
+    if (c.dotpart && apply_dot_ok(aop, ak)) {  // <p, q> from the apply epilogue
+        int64_t nb = 0;
+        if ((e = apply_dot_by_kind(aop, p, q, c.dotpart, &nb, s)) != cudaSuccess) return e;
+        const unsigned g = (unsigned)std::min<int64_t>(kRedBlocks, (nb + kRedThreads - 1) / kRedThreads);
+        k_sum_fin<<<g, kRedThreads, 0, s>>>(c.dotpart, nb, c.partials, c.scal, c.flags, STAGE_PQ);
+    } else {
+        if ((e = apply_by_kind(aop, ak, p, q, s)) != cudaSuccess) return e;
+        k_dot_fin<V><<<vec_grid(), kRedThreads, 0, s>>>(p, q, L, c.partials, c.scal, c.flags, STAGE_PQ);
+    }
     k_update<V, U><<<vec_grid(), 256, 0, s>>>(u, p, r, q, L, c.scal, c.flags);
     if ((e = dss_from(aop, r, z, CW_DSS_SUM, s)) != cudaSuccess) return e;  // z = S r
     k_precond_fin<V><<<vec_grid(), kRedThreads, 0, s>>>(r, z, dinv, L, c.kappa, c.partials, c.scal, c.flags,
@@ -589,6 +639,7 @@ static cw_status ensure_scratch(Op *op, int mode)
         CW_CUDA_TRY(cudaEventCreate(&c->ev0));
         CW_CUDA_TRY(cudaEventCreate(&c->ev1));
         CW_CUDA_TRY(cudaMalloc(&c->partials, 2 * kRedBlocks * sizeof(double)));
+        CW_CUDA_TRY(cudaMalloc(&c->dotpart, op->E * sizeof(double)));
         CW_CUDA_TRY(cudaMalloc(&c->scal, S_NSCAL * sizeof(double)));
         CW_CUDA_TRY(cudaMalloc(&c->flags, F_NFLAG * sizeof(int)));
         CW_CUDA_TRY(cudaMemset(c->scal, 0, S_NSCAL * sizeof(double)));
@@ -599,7 +650,7 @@ static cw_status ensure_scratch(Op *op, int mode)
         CW_CUDA_TRY(cudaMalloc(&c->rout, L * sizeof(double)));
         CW_CUDA_TRY(cudaMalloc(&c->q64b, L * sizeof(double)));
         CW_CUDA_TRY(cudaMalloc(&c->kappa, L));
-        c->bytes += 2 * L * sizeof(double) + L + 2 * kRedBlocks * sizeof(double);
+        c->bytes += 2 * L * sizeof(double) + L + 2 * kRedBlocks * sizeof(double) + op->E * sizeof(double);
         k_make_kappa<<<vec_grid(), 256, 0, c->stream>>>(c->kappa, op->mesh->nx, op->mesh->ny, op->mesh->nz, op->p, L);
         // FP64 masked inverse diagonal
         double *d = static_cast<double *>(c->lv64.q);  // borrow q as the diagonal buffer

@@ -11,4 +11,8 @@ cudaError_t apply_launch_f32(const Op &op, const void *x, void *y, cudaStream_t 
     default: return apply_launch_bf16(op, x, y, s);
     }
 }
+cudaError_t apply_dot_launch_f32(const Op &op, const void *x, void *y, double *part, int64_t *nb, cudaStream_t s)
+{
+    return launch_dot_degree<ArF32, float, float>(op, x, y, part, nb, s);
+}
 }  // namespace cw

@@ -7,4 +7,8 @@ cudaError_t apply_launch_f32g16(const Op &op, const void *x, void *y, cudaStream
 {
     return launch_degree<ArF32, float, __nv_bfloat16>(op, x, y, s);
 }
+cudaError_t apply_dot_launch_f32g16(const Op &op, const void *x, void *y, double *part, int64_t *nb, cudaStream_t s)
+{
+    return launch_dot_degree<ArF32, float, __nv_bfloat16>(op, x, y, part, nb, s);
+}
 }  // namespace cw

@@ -63,6 +63,12 @@ cudaError_t apply_launch_df(const Op &op, const void *x, void *y, cudaStream_t s
 cudaError_t apply_launch_f64n(const Op &op, const void *x, void *y, cudaStream_t s);
 cudaError_t apply_launch_f32(const Op &op, const void *x, void *y, cudaStream_t s);
 
+// y = A x plus the per-CTA partials of <x, y> (curved cells, default tile and staging; for
+// CW_PREC_F64, CW_PREC_F32 and CW_PREC_F32_BF16G); *nb = number of partials
+cudaError_t apply_dot_launch_df(const Op &op, const void *x, void *y, double *part, int64_t *nb, cudaStream_t s);
+cudaError_t apply_dot_launch_f32(const Op &op, const void *x, void *y, double *part, int64_t *nb, cudaStream_t s);
+cudaError_t apply_dot_launch_f32g16(const Op &op, const void *x, void *y, double *part, int64_t *nb, cudaStream_t s);
+
 // dispatch to the right unit
 cudaError_t apply_local(const Op &op, const void *x, void *y, cudaStream_t s);
 cudaError_t dss_launch(const Op &op, void *v, int flags, cudaStream_t s);

@@ -96,6 +96,44 @@ cudaError_t launch_metric(const Op &op, const void *x, void *y, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// y = A x with the CTA partials of <x, y> written to part (default tile size, TMA staging);
+// *nblocks receives the number of partials
+template <int N, class Ar, class VS, class GS>
+cudaError_t launch_metric_dot(const Op &op, const void *x, void *y, double *part, int64_t *nblocks, cudaStream_t s)
+{
+    constexpr int CPB = cpb_default<N>();
+    TabMetric<N, typename Ar::C> tab;
+    fill_metric_tab<N>(tab, op.tab, [](double v) { return MakeC<Ar>::from(v); });
+    const size_t smem = metric_smem_bytes<N, CPB, typename Ar::T, GS>(metric_ncomp(op.kind), 1);
+    auto kern = apply_metric_dot_kernel<N, CPB, Ar, VS, GS, 1>;
+    static size_t opted = 0;
+    if (smem > opted) {
+        cudaError_t e = opt_in_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        opted = smem;
+    }
+    const unsigned grid = (unsigned)((op.E + CPB - 1) / CPB);
+    *nblocks = grid;
+    kern<<<grid, N * N * CPB, smem, s>>>(static_cast<const VS *>(x), static_cast<VS *>(y),
+                                         static_cast<const GS *>(op.d_geo), op.E, op.kind, tab, part);
+    return cudaGetLastError();
+}
+
+template <class Ar, class VS, class GS>
+cudaError_t launch_dot_degree(const Op &op, const void *x, void *y, double *part, int64_t *nb, cudaStream_t s)
+{
+    switch (op.n) {
+    case 2: return launch_metric_dot<2, Ar, VS, GS>(op, x, y, part, nb, s);
+    case 3: return launch_metric_dot<3, Ar, VS, GS>(op, x, y, part, nb, s);
+    case 4: return launch_metric_dot<4, Ar, VS, GS>(op, x, y, part, nb, s);
+    case 5: return launch_metric_dot<5, Ar, VS, GS>(op, x, y, part, nb, s);
+    case 6: return launch_metric_dot<6, Ar, VS, GS>(op, x, y, part, nb, s);
+    case 7: return launch_metric_dot<7, Ar, VS, GS>(op, x, y, part, nb, s);
+    case 8: return launch_metric_dot<8, Ar, VS, GS>(op, x, y, part, nb, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <int N, int CPB, class Ar, class VS>
 cudaError_t launch_affine(const Op &op, const void *x, void *y, cudaStream_t s)
 {
