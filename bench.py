@@ -33,7 +33,7 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 P, NCELL, KIND = 4, 64, 3
-WORKLOAD = "laplace+mass apply+DSS, Q4 (125 DoFs/cell), 5 Gauss pts/dir, 64^3 curved cells, metric 7xFP64/qp"
+WORKLOAD = "laplace+mass apply+DSS, Q4 (125 DoFs/cell), 5 Gauss pts/dir, 64^3 curved cells, metric 7 x 8 B/qp (FP64 values held as rounded float pairs)"
 METRIC = "cell-wise DoF/s of apply at p=2..7 (FP64 vs mixed); CG time-to-1e-10 on 1 GB300"
 SWEEP_N = {1: 256, 2: 171, 3: 128, 4: 102, 5: 85, 6: 73, 7: 64}
 

@@ -142,6 +142,13 @@ template <>
 __device__ __forceinline__ void store_g<float>(float *p, double v) { *p = static_cast<float>(v); }
 template <>
 __device__ __forceinline__ void store_g<__nv_bfloat16>(__nv_bfloat16 *p, double v) { *p = __double2bfloat16(v); }
+// FP64 metric: rounded float pair hi + lo (hi = fl32(v), lo = fl32(v - hi); ~48 significant bits)
+template <>
+__device__ __forceinline__ void store_g<df64s>(df64s *p, double v)
+{
+    const float hi = __double2float_rn(v);
+    *p = df64s{hi, __double2float_rn(v - static_cast<double>(hi))};
+}
 
 // one thread per (cell, quadrature point); comps selected by kind
 template <class GS>
@@ -612,8 +619,8 @@ cw_status cw_op_create(cw_mesh mh, int degree, int kind, int geom, int prec, int
             const int64_t nthr = op->E * n3;
             const unsigned blocks = (unsigned)((nthr + 255) / 256);
             if (metric_is_f64(prec))
-                metric_kernel<double><<<blocks, 256>>>(m->d_verts, m->nx, m->ny, op->E, op->n, kind, rule,
-                                                       static_cast<double *>(op->d_geo), d_bad);
+                metric_kernel<df64s><<<blocks, 256>>>(m->d_verts, m->nx, m->ny, op->E, op->n, kind, rule,
+                                                      static_cast<df64s *>(op->d_geo), d_bad);
             else if (prec == CW_PREC_F32)
                 metric_kernel<float><<<blocks, 256>>>(m->d_verts, m->nx, m->ny, op->E, op->n, kind, rule,
                                                       static_cast<float *>(op->d_geo), d_bad);

@@ -17,6 +17,12 @@ struct df64 {
     float hi, lo;
 };
 
+// storage form of a double-float value (the FP64 metric tensor is kept pre-split, so the operator
+// reads each metric entry with one 8-byte load and no conversion work)
+struct __align__(8) df64s {
+    float hi, lo;
+};
+
 // ---------------------------------------------------------------- conversions ----
 
 // Split a double into hi + lo floats using integer operations only. |x| < 2^-126 maps to 0 and
@@ -143,6 +149,7 @@ struct ArDF {  // double-float arithmetic
     static __device__ __forceinline__ T norm(T a) { return df_norm(a); }
     static __device__ __forceinline__ T from(double v) { return split_f64(v); }
     static __device__ __forceinline__ T from(float v) { return T{v, 0.0f}; }
+    static __device__ __forceinline__ T from(df64s v) { return T{v.hi, v.lo}; }
     static __device__ __forceinline__ void to(double &d, T a) { d = df_to_double(a); }
     static __device__ __forceinline__ double to_f64(T a) { return df_to_double(a); }
     static __device__ __forceinline__ df64 to_df(T a) { return a; }
@@ -159,6 +166,7 @@ struct ArF64 {  // native FP64
     static __device__ __forceinline__ T neg(T a) { return -a; }
     static __device__ __forceinline__ T norm(T a) { return a; }
     static __device__ __forceinline__ T from(double v) { return v; }
+    static __device__ __forceinline__ T from(df64s v) { return widen_f32(v.hi) + widen_f32(v.lo); }
     static __device__ __forceinline__ void to(double &d, T a) { d = a; }
     static __device__ __forceinline__ double to_f64(T a) { return a; }
 };

@@ -1,4 +1,4 @@
-// Persistent batched apply, double-float arithmetic on FP64 vectors and metric.
+// Persistent batched apply, double-float arithmetic on FP64 vectors and the pre-split (hi, lo) metric.
 #include "cw_batch.cuh"
 #include "cw_launch.cuh"
 
@@ -11,7 +11,7 @@ __constant__ BatchTables<df64> c_batch_tabs_df;
 __global__ void __launch_bounds__(kBatchThreads, 4) batch_kernel_df(const BatchProb *__restrict__ probs, int nprob,
                                                                    int64_t nitems, unsigned long long *__restrict__ counter)
 {
-    batch_body<ArDF, double, double>(probs, nprob, nitems, counter, c_batch_tabs_df);
+    batch_body<ArDF, double, df64s>(probs, nprob, nitems, counter, c_batch_tabs_df);
 }
 
 static df64 mk(double v) { return df64{static_cast<float>(v), static_cast<float>(v - static_cast<double>(static_cast<float>(v)))}; }
@@ -58,8 +58,8 @@ static cudaError_t grouped(const Tables1D &tb, const BatchProb *d_probs, int npr
     TabMetric<N, df64> tab;
     fill_metric_tab<N>(tab, tb, mk);
     // shared memory for the largest metric of the group (kind_max components)
-    const size_t smem = metric_smem_bytes<N, CPB, typename ArDF::T, double>(metric_ncomp(kind_max), STAGE);
-    auto kern = batch_degree_kernel<N, CPB, ArDF, double, double, STAGE>;
+    const size_t smem = metric_smem_bytes<N, CPB, typename ArDF::T, df64s>(metric_ncomp(kind_max), STAGE);
+    auto kern = batch_degree_kernel<N, CPB, ArDF, double, df64s, STAGE>;
     static size_t opted = 0;
     static int per_sm = 0;
     if (smem > opted) {

@@ -40,7 +40,7 @@ struct Op {
     int p = 0, n = 0, kind = 0, geom = 0, prec = 0, bc = 0;
     int64_t E = 0, L = 0, NG = 0;
     Tables1D tab;
-    void *d_geo = nullptr;  // metric [E][ncomp][n^3] in the metric type, or affine [E][4] doubles
+    void *d_geo = nullptr;  // metric [E][ncomp][n^3] in the metric type (FP64 precisions: df64s pairs), or affine [E][4] doubles
     int64_t geo_bytes = 0;
     double *d_dinv = nullptr;  // cell-wise masked inverse diagonal (solver), lazily
     CgScratch *cg = nullptr;
