@@ -160,25 +160,28 @@ def event_pair():
 
 
 def time_apply(cw, op, x, y, steps, warmup, stream, assemble=True):
-    """Times `steps` steps (LOCAL apply kernel, then the DSS passes when assemble) with events on
-    the launching stream; returns (ms per step, ms per apply kernel)."""
+    """Times `steps` steps with events on the launching stream; returns (ms per step, ms per apply
+    kernel). A step is one cw_apply call: CW_APPLY_ASSEMBLE (the operator kernel, which also sums the
+    x-interfaces inside its tiles, then the remaining DSS passes) or CW_APPLY_LOCAL. The kernel time
+    comes from events around CW_APPLY_LOCAL launches of the same kernel on the same buffers, timed
+    right after the steps (the assembled launch adds only the in-tile x sums to it)."""
     import torch
+    flags = cw.CW_APPLY_ASSEMBLE if assemble else cw.CW_APPLY_LOCAL
+    sid = stream.cuda_stream
     for _ in range(warmup):
-        cw.cw_apply(op.handle, x, y, cw.CW_APPLY_LOCAL, stream=stream.cuda_stream)
-        if assemble:
-            cw.cw_dss(op.handle, y, cw.CW_DSS_SUM, stream=stream.cuda_stream)
+        cw.cw_apply(op.handle, x, y, flags, stream=sid)
     torch.cuda.synchronize()
-    ev = [event_pair() for _ in range(steps)]
     t0, t1 = event_pair()
+    ev = [event_pair() for _ in range(steps)]
     with torch.cuda.stream(stream):
         t0.record(stream)
+        for _ in range(steps):
+            cw.cw_apply(op.handle, x, y, flags, stream=sid)
+        t1.record(stream)
         for a, b in ev:
             a.record(stream)
-            cw.cw_apply(op.handle, x, y, cw.CW_APPLY_LOCAL, stream=stream.cuda_stream)
+            cw.cw_apply(op.handle, x, y, cw.CW_APPLY_LOCAL, stream=sid)
             b.record(stream)
-            if assemble:
-                cw.cw_dss(op.handle, y, cw.CW_DSS_SUM, stream=stream.cuda_stream)
-        t1.record(stream)
     torch.cuda.synchronize()
     step_ms = t0.elapsed_time(t1) / steps
     kern_ms = sum(a.elapsed_time(b) for a, b in ev) / steps

@@ -214,17 +214,6 @@ __global__ void gather_kernel(const double *__restrict__ ug, VS *__restrict__ x,
 // between cells K_L and K_R = K_L + stride, s = v[K_L, face = p] + v[K_R, face = 0] is written to
 // both copies. One thread per (interface, face node); no atomics; exchange partners at static
 // offsets.
-template <class VS>
-struct AddOp {
-    static __device__ __forceinline__ VS add(VS a, VS b) { return a + b; }
-};
-template <>
-struct AddOp<__nv_bfloat16> {
-    static __device__ __forceinline__ __nv_bfloat16 add(__nv_bfloat16 a, __nv_bfloat16 b)
-    {
-        return __float2bfloat16_rn(__bfloat162float(a) + __bfloat162float(b));
-    }
-};
 
 // 32-bit division by a runtime constant: q = umulhi(x, floor((2^32-1)/d)), corrected once
 struct FastDiv {
@@ -290,6 +279,27 @@ __global__ void dss_axis_kernel(VS *__restrict__ v, int nx, int ny, int nz, int 
     (void)nz;
 }
 
+// The x pass of Algorithm struct_dss restricted to the interfaces between tiles of `xtile`
+// consecutive cells (K_L = (b+1) xtile - 1 with K_L + 1 < E and K_L not the last cell of its x-row);
+// the interfaces inside tiles were summed by the operator kernel. One thread per (interface, face node).
+template <class VS>
+__global__ void dss_xtile_kernel(VS *__restrict__ v, int nx, int p, int xtile, int64_t E, uint32_t nthr,
+                                 FastDiv fd_n2)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nthr) return;
+    const int n = p + 1, n2 = n * n, n3 = n2 * n;
+    const uint32_t b = fd_n2.div(t);
+    const uint32_t f = t - b * static_cast<uint32_t>(n2);
+    const int64_t KL = (int64_t)(b + 1) * xtile - 1;
+    if (KL + 1 >= E || KL % nx == nx - 1) return;
+    const uint32_t fa = f % n, fb = f / n;
+    VS *pl = v + KL * n3 + p + n * fa + n2 * fb, *pr = v + (KL + 1) * n3 + n * fa + n2 * fb;
+    const VS sum = AddOp<VS>::add(*pl, *pr);
+    *pl = sum;
+    *pr = sum;
+}
+
 template <class VS>
 struct MulOp {
     static __device__ __forceinline__ VS mul(VS a, double s) { return static_cast<VS>(a * s); }
@@ -353,7 +363,8 @@ __global__ void dss_x_from_kernel(const VS *__restrict__ src, VS *__restrict__ d
 }
 
 template <class VS>
-static cudaError_t dss_typed(const Op &op, VS *v, int flags, cudaStream_t s, int first_axis = 0, int end_axis = 3);
+static cudaError_t dss_typed(const Op &op, VS *v, int flags, cudaStream_t s, int first_axis = 0, int end_axis = 3,
+                             int xtile = 0);
 
 // dst = S src (or S_bar src), src unchanged; src and dst must not overlap
 template <class VS>
@@ -387,7 +398,7 @@ cudaError_t dss_from_f64(const Op &op, const double *src, double *dst, int flags
 }
 
 template <class VS>
-static cudaError_t dss_typed(const Op &op, VS *v, int flags, cudaStream_t s, int first_axis, int end_axis)
+static cudaError_t dss_typed(const Op &op, VS *v, int flags, cudaStream_t s, int first_axis, int end_axis, int xtile)
 {
     const Mesh &m = *op.mesh;
     const int dims[3] = {m.nx, m.ny, m.nz};
@@ -400,6 +411,14 @@ static cudaError_t dss_typed(const Op &op, VS *v, int flags, cudaStream_t s, int
         const uint32_t nthr = (uint32_t)n2 * e0 * (uint32_t)(dims[ax] - 1);
         const int bs = 256;
         dim3 grid((nthr + bs - 1) / bs, dims[b]);
+        if (ax == 0 && xtile > 1) {  // only the x-interfaces between tiles are left
+            const int64_t nb = (op.E / xtile) * n2;  // interface K_L = (b+1) xtile - 1, b < E/xtile
+            if (nb >= ((int64_t)1 << 32)) return cudaErrorInvalidValue;  // callers fuse only below this
+            if (nb > 0)
+                dss_xtile_kernel<VS><<<(unsigned)((nb + bs - 1) / bs), bs, 0, s>>>(
+                    v, m.nx, op.p, xtile, op.E, (uint32_t)nb, FastDiv::make(n2));
+            continue;
+        }
         dss_axis_kernel<VS><<<grid, bs, 0, s>>>(v, m.nx, m.ny, m.nz, op.p, ax, nthr, FastDiv::make(n2),
                                                 FastDiv::make(e0));
     }
@@ -410,31 +429,31 @@ static cudaError_t dss_typed(const Op &op, VS *v, int flags, cudaStream_t s, int
     return cudaGetLastError();
 }
 
-cudaError_t dss_launch(const Op &op, void *v, int flags, cudaStream_t s)
+cudaError_t dss_launch(const Op &op, void *v, int flags, cudaStream_t s, int xtile)
 {
     switch (vec_elem_size(op.prec)) {
-    case 8: return dss_typed(op, static_cast<double *>(v), flags, s);
-    case 4: return dss_typed(op, static_cast<float *>(v), flags, s);
-    default: return dss_typed(op, static_cast<__nv_bfloat16 *>(v), flags, s);
+    case 8: return dss_typed(op, static_cast<double *>(v), flags, s, 0, 3, xtile);
+    case 4: return dss_typed(op, static_cast<float *>(v), flags, s, 0, 3, xtile);
+    default: return dss_typed(op, static_cast<__nv_bfloat16 *>(v), flags, s, 0, 3, xtile);
     }
 }
 
 // sum passes of the axes [ax0, ax1) only (no averaging); used on slab views of the mesh
-static cudaError_t dss_axes(const Op &op, void *v, int ax0, int ax1, cudaStream_t s)
+static cudaError_t dss_axes(const Op &op, void *v, int ax0, int ax1, cudaStream_t s, int xtile = 0)
 {
     switch (vec_elem_size(op.prec)) {
-    case 8: return dss_typed(op, static_cast<double *>(v), CW_DSS_SUM, s, ax0, ax1);
-    case 4: return dss_typed(op, static_cast<float *>(v), CW_DSS_SUM, s, ax0, ax1);
-    default: return dss_typed(op, static_cast<__nv_bfloat16 *>(v), CW_DSS_SUM, s, ax0, ax1);
+    case 8: return dss_typed(op, static_cast<double *>(v), CW_DSS_SUM, s, ax0, ax1, xtile);
+    case 4: return dss_typed(op, static_cast<float *>(v), CW_DSS_SUM, s, ax0, ax1, xtile);
+    default: return dss_typed(op, static_cast<__nv_bfloat16 *>(v), CW_DSS_SUM, s, ax0, ax1, xtile);
     }
 }
 
-cudaError_t apply_local(const Op &op, const void *x, void *y, cudaStream_t s)
+cudaError_t apply_local(const Op &op, const void *x, void *y, cudaStream_t s, int *xfuse)
 {
     switch (op.prec) {
-    case CW_PREC_F64: return apply_launch_df(op, x, y, s);
-    case CW_PREC_F64_NATIVE: return apply_launch_f64n(op, x, y, s);
-    default: return apply_launch_f32(op, x, y, s);
+    case CW_PREC_F64: return apply_launch_df(op, x, y, s, xfuse);
+    case CW_PREC_F64_NATIVE: return apply_launch_f64n(op, x, y, s, xfuse);
+    default: return apply_launch_f32(op, x, y, s, xfuse);
     }
 }
 
@@ -718,8 +737,15 @@ cw_status cw_apply(cw_op oh, const void *x, void *y, int flags, void *stream)
     if (flags != CW_APPLY_LOCAL && flags != CW_APPLY_ASSEMBLE) return fail(CW_ERR_ARG, "cw_apply: bad flags");
     if (x == y) return fail(CW_ERR_ARG, "cw_apply: x and y must not alias");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    CW_CUDA_TRY(apply_local(*op, x, y, s));
-    if (flags == CW_APPLY_ASSEMBLE) CW_CUDA_TRY(dss_launch(*op, y, CW_DSS_SUM, s));
+    if (flags == CW_APPLY_LOCAL) {
+        CW_CUDA_TRY(apply_local(*op, x, y, s));
+        return CW_OK;
+    }
+    // the operator kernel sums the x-interfaces inside its tiles; the DSS does the rest
+    int xtile = 0;
+    const bool fuse = op->E * (int64_t)(op->n * op->n) < ((int64_t)1 << 32);
+    CW_CUDA_TRY(apply_local(*op, x, y, s, fuse ? &xtile : nullptr));
+    CW_CUDA_TRY(dss_launch(*op, y, CW_DSS_SUM, s, xtile));
     return CW_OK;
 }
 
@@ -917,9 +943,11 @@ cw_status cw_apply_host(cw_op oh, const void *x_host, void *y_host, int flags, v
         CW_CUDA_TRY(cudaStreamWaitEvent(scomp, op->h_ev[0][k], 0));
         Op part;
         view(k, z0, nzk, part);
-        CW_CUDA_TRY(apply_local(part, dx + off, dy + off, scomp));
+        int xtile = 0;  // x-interfaces inside the operator's tiles are summed by its kernel
+        const bool fuse = flags == CW_APPLY_ASSEMBLE && part.E * (int64_t)(n3 / op->n) < ((int64_t)1 << 32);
+        CW_CUDA_TRY(apply_local(part, dx + off, dy + off, scomp, fuse ? &xtile : nullptr));
         if (flags == CW_APPLY_ASSEMBLE) {
-            CW_CUDA_TRY(dss_axes(part, dy + off, 0, 3, scomp));  // x, y and interior z interfaces
+            CW_CUDA_TRY(dss_axes(part, dy + off, 0, 3, scomp, xtile));  // x, y and interior z interfaces
             if (k > 0) {
                 Op bop = *op;
                 bop.mesh = &bview;

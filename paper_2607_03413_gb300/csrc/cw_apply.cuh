@@ -54,6 +54,19 @@ struct TabAffine {
 
 // small helpers -------------------------------------------------------------------------------
 
+// sum of two stored values as the structured DSS forms it (BF16: FP32 sum rounded once)
+template <class VS>
+struct AddOp {
+    static __device__ __forceinline__ VS add(VS a, VS b) { return a + b; }
+};
+template <>
+struct AddOp<__nv_bfloat16> {
+    static __device__ __forceinline__ __nv_bfloat16 add(__nv_bfloat16 a, __nv_bfloat16 b)
+    {
+        return __float2bfloat16_rn(__bfloat162float(a) + __bfloat162float(b));
+    }
+};
+
 template <class S>
 __device__ __forceinline__ S ldg_nc(const S *p) { return __ldg(p); }
 template <>
@@ -181,10 +194,15 @@ __host__ __device__ constexpr size_t metric_smem_bytes(int nc, int stage)
 // threads than the tile needs). STAGE (see metric_smem_bytes; staging needs cpt == CPB).
 // DOT: also accumulate this thread's share of <x, y> over its final x-line into *dot (double-float
 // products of the values as stored in y; the x line is re-read from global memory, L1/L2-resident).
+// asm_nx > 0 (the mesh's cells per x-row): the x pass of Algorithm struct_dss is applied to the
+// x-interfaces between cells of this tile before the store (the two end values of each x-line are
+// exchanged through shared memory and summed as that pass sums them); the interfaces between tiles
+// are left to the DSS.
 template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool DOT = false>
 __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__restrict__ y, const GS *__restrict__ geo,
                                             int64_t ncells, int kind, const TabMetric<N, typename Ar::C> &tab,
-                                            int64_t tile, int cpt, unsigned char *smem_raw, df64 *dot = nullptr)
+                                            int64_t tile, int cpt, unsigned char *smem_raw, df64 *dot = nullptr,
+                                            int asm_nx = 0)
 {
     using T = typename Ar::T;
     using L = Lines<N>;
@@ -376,7 +394,27 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
         {
             CW_LDX(s0, v);
             sweep<N, Ar, 1>(tab, v, w);
-            if (act) {
+            if (asm_nx > 0) {  // kernel-uniform
+                VS o0, o1;
+                Ar::to(o0, w[0]);
+                Ar::to(o1, w[N - 1]);
+                // the S1 buffer is free: its last reads precede the first barrier of step (5)
+                VS *exl = reinterpret_cast<VS *>(S0 + CPB * CS), *exr = exl + CPB * N2;
+                exl[c * N2 + r] = o0;
+                exr[c * N2 + r] = o1;
+                __syncthreads();
+                if (act) {
+                    const int64_t cx = cell % asm_nx;
+                    if (c + 1 < cpt && cell + 1 < ncells && cx + 1 < asm_nx)
+                        o1 = AddOp<VS>::add(o1, exl[(c + 1) * N2 + r]);
+                    if (c > 0 && cx > 0) o0 = AddOp<VS>::add(exr[(c - 1) * N2 + r], o0);
+                    VS *yc = yr + cell * N3 + N * r;
+                    yc[0] = o0;
+#pragma unroll
+                    for (int m = 1; m < N - 1; ++m) Ar::to(yc[m], w[m]);
+                    yc[N - 1] = o1;
+                }
+            } else if (act) {
                 VS *yc = yr + cell * N3 + N * r;
 #pragma unroll
                 for (int m = 0; m < N; ++m) Ar::to(yc[m], w[m]);
@@ -404,10 +442,11 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
 template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
 __global__ void __launch_bounds__(N *N *CPB) apply_metric_kernel(const VS *__restrict__ x, VS *__restrict__ y,
                                                                   const GS *__restrict__ geo, int64_t ncells,
-                                                                  int kind, TabMetric<N, typename Ar::C> tab)
+                                                                  int kind, TabMetric<N, typename Ar::C> tab,
+                                                                  int asm_nx)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    metric_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw);
+    metric_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw, nullptr, asm_nx);
 }
 
 // y = A x and the CTA's partial of <x, y> in part[blockIdx.x] (deterministic: fixed order in a CTA)

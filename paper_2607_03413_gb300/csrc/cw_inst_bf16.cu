@@ -3,8 +3,8 @@
 
 #include "cw_launch.cuh"
 namespace cw {
-cudaError_t apply_launch_bf16(const Op &op, const void *x, void *y, cudaStream_t s)
+cudaError_t apply_launch_bf16(const Op &op, const void *x, void *y, cudaStream_t s, int *xfuse)
 {
-    return launch_degree<ArF32, __nv_bfloat16, __nv_bfloat16>(op, x, y, s);
+    return launch_degree<ArF32, __nv_bfloat16, __nv_bfloat16>(op, x, y, s, xfuse);
 }
 }  // namespace cw

@@ -3,9 +3,9 @@
 
 #include "cw_launch.cuh"
 namespace cw {
-cudaError_t apply_launch_f32g16(const Op &op, const void *x, void *y, cudaStream_t s)
+cudaError_t apply_launch_f32g16(const Op &op, const void *x, void *y, cudaStream_t s, int *xfuse)
 {
-    return launch_degree<ArF32, float, __nv_bfloat16>(op, x, y, s);
+    return launch_degree<ArF32, float, __nv_bfloat16>(op, x, y, s, xfuse);
 }
 cudaError_t apply_dot_launch_f32g16(const Op &op, const void *x, void *y, double *part, int64_t *nb, cudaStream_t s)
 {

@@ -2,8 +2,8 @@
 // (hi, lo) float-pair form shared with CW_PREC_F64, widened to double exactly on load.
 #include "cw_launch.cuh"
 namespace cw {
-cudaError_t apply_launch_f64n(const Op &op, const void *x, void *y, cudaStream_t s)
+cudaError_t apply_launch_f64n(const Op &op, const void *x, void *y, cudaStream_t s, int *xfuse)
 {
-    return launch_degree<ArF64, double, df64s, false>(op, x, y, s);
+    return launch_degree<ArF64, double, df64s, false>(op, x, y, s, xfuse);
 }
 }  // namespace cw

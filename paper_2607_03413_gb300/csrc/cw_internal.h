@@ -59,9 +59,11 @@ size_t vec_elem_size(int prec);
 bool metric_is_f64(int prec);
 
 // launchers implemented in the instantiation units
-cudaError_t apply_launch_df(const Op &op, const void *x, void *y, cudaStream_t s);
-cudaError_t apply_launch_f64n(const Op &op, const void *x, void *y, cudaStream_t s);
-cudaError_t apply_launch_f32(const Op &op, const void *x, void *y, cudaStream_t s);
+// xfuse != nullptr asks the curved-cell kernel to apply the DSS x pass inside each tile; *xfuse
+// receives the tile size in cells (0: nothing fused, e.g. Cartesian cells)
+cudaError_t apply_launch_df(const Op &op, const void *x, void *y, cudaStream_t s, int *xfuse = nullptr);
+cudaError_t apply_launch_f64n(const Op &op, const void *x, void *y, cudaStream_t s, int *xfuse = nullptr);
+cudaError_t apply_launch_f32(const Op &op, const void *x, void *y, cudaStream_t s, int *xfuse = nullptr);
 
 // y = A x plus the per-CTA partials of <x, y> (curved cells, default tile and staging; for
 // CW_PREC_F64, CW_PREC_F32 and CW_PREC_F32_BF16G); *nb = number of partials
@@ -70,8 +72,9 @@ cudaError_t apply_dot_launch_f32(const Op &op, const void *x, void *y, double *p
 cudaError_t apply_dot_launch_f32g16(const Op &op, const void *x, void *y, double *part, int64_t *nb, cudaStream_t s);
 
 // dispatch to the right unit
-cudaError_t apply_local(const Op &op, const void *x, void *y, cudaStream_t s);
-cudaError_t dss_launch(const Op &op, void *v, int flags, cudaStream_t s);
+cudaError_t apply_local(const Op &op, const void *x, void *y, cudaStream_t s, int *xfuse = nullptr);
+// xtile > 0: the x pass skips the interfaces inside tiles of xtile consecutive cells (already summed)
+cudaError_t dss_launch(const Op &op, void *v, int flags, cudaStream_t s, int xtile = 0);
 // out of place: dst = S src (flags CW_DSS_SUM) or S_bar src (CW_DSS_AVERAGE); the x pass is fused
 // with the copy
 cudaError_t dss_from(const Op &op, const void *src, void *dst, int flags, cudaStream_t s);

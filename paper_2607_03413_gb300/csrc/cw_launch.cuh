@@ -77,8 +77,10 @@ static cudaError_t opt_in_smem(K kernel, size_t smem)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// xfuse != nullptr: the kernel also applies the x pass of the DSS inside each tile and *xfuse
+// receives the tile size (cells), so the DSS x pass only has the interfaces between tiles left
 template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
-cudaError_t launch_metric(const Op &op, const void *x, void *y, cudaStream_t s)
+cudaError_t launch_metric(const Op &op, const void *x, void *y, cudaStream_t s, int *xfuse = nullptr)
 {
     TabMetric<N, typename Ar::C> tab;
     fill_metric_tab<N>(tab, op.tab, [](double v) { return MakeC<Ar>::from(v); });
@@ -91,8 +93,10 @@ cudaError_t launch_metric(const Op &op, const void *x, void *y, cudaStream_t s)
         opted = smem;
     }
     const unsigned grid = (unsigned)((op.E + CPB - 1) / CPB);
+    if (xfuse) *xfuse = CPB;
     kern<<<grid, N * N * CPB, smem, s>>>(static_cast<const VS *>(x), static_cast<VS *>(y),
-                                         static_cast<const GS *>(op.d_geo), op.E, op.kind, tab);
+                                         static_cast<const GS *>(op.d_geo), op.E, op.kind, tab,
+                                         xfuse ? op.mesh->nx : 0);
     return cudaGetLastError();
 }
 
@@ -159,37 +163,38 @@ cudaError_t launch_affine(const Op &op, const void *x, void *y, cudaStream_t s)
 
 // variant selection: op.cpb (0 = default, else cpb_default or cpb_alt), op.stage (0/1)
 template <int N, class Ar, class VS, class GS, bool ALL_VARIANTS>
-cudaError_t launch_variant(const Op &op, const void *x, void *y, cudaStream_t s)
+cudaError_t launch_variant(const Op &op, const void *x, void *y, cudaStream_t s, int *xfuse)
 {
     constexpr int D = cpb_default<N>(), A = cpb_alt<N>();
-    if (op.geom == CW_GEOM_AFFINE) {
+    if (op.geom == CW_GEOM_AFFINE) {  // no fused DSS work: *xfuse stays 0
         if constexpr (ALL_VARIANTS)
             if (op.cpb == A) return launch_affine<N, A, Ar, VS>(op, x, y, s);
         return launch_affine<N, D, Ar, VS>(op, x, y, s);
     }
     if constexpr (ALL_VARIANTS) {
         const bool alt = (op.cpb == A);
-        if (op.stage == 1) return alt ? launch_metric<N, A, Ar, VS, GS, 1>(op, x, y, s)
-                                      : launch_metric<N, D, Ar, VS, GS, 1>(op, x, y, s);
-        if (op.stage == 2) return alt ? launch_metric<N, A, Ar, VS, GS, 2>(op, x, y, s)
-                                      : launch_metric<N, D, Ar, VS, GS, 2>(op, x, y, s);
-        return alt ? launch_metric<N, A, Ar, VS, GS, 0>(op, x, y, s)
-                   : launch_metric<N, D, Ar, VS, GS, 0>(op, x, y, s);
+        if (op.stage == 1) return alt ? launch_metric<N, A, Ar, VS, GS, 1>(op, x, y, s, xfuse)
+                                      : launch_metric<N, D, Ar, VS, GS, 1>(op, x, y, s, xfuse);
+        if (op.stage == 2) return alt ? launch_metric<N, A, Ar, VS, GS, 2>(op, x, y, s, xfuse)
+                                      : launch_metric<N, D, Ar, VS, GS, 2>(op, x, y, s, xfuse);
+        return alt ? launch_metric<N, A, Ar, VS, GS, 0>(op, x, y, s, xfuse)
+                   : launch_metric<N, D, Ar, VS, GS, 0>(op, x, y, s, xfuse);
     }
-    return launch_metric<N, D, Ar, VS, GS, 0>(op, x, y, s);
+    return launch_metric<N, D, Ar, VS, GS, 0>(op, x, y, s, xfuse);
 }
 
 template <class Ar, class VS, class GS, bool ALL_VARIANTS = true>
-cudaError_t launch_degree(const Op &op, const void *x, void *y, cudaStream_t s)
+cudaError_t launch_degree(const Op &op, const void *x, void *y, cudaStream_t s, int *xfuse = nullptr)
 {
+    if (xfuse) *xfuse = 0;
     switch (op.n) {
-    case 2: return launch_variant<2, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s);
-    case 3: return launch_variant<3, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s);
-    case 4: return launch_variant<4, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s);
-    case 5: return launch_variant<5, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s);
-    case 6: return launch_variant<6, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s);
-    case 7: return launch_variant<7, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s);
-    case 8: return launch_variant<8, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s);
+    case 2: return launch_variant<2, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s, xfuse);
+    case 3: return launch_variant<3, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s, xfuse);
+    case 4: return launch_variant<4, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s, xfuse);
+    case 5: return launch_variant<5, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s, xfuse);
+    case 6: return launch_variant<6, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s, xfuse);
+    case 7: return launch_variant<7, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s, xfuse);
+    case 8: return launch_variant<8, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s, xfuse);
     }
     return cudaErrorInvalidValue;
 }

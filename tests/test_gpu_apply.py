@@ -68,6 +68,32 @@ def test_apply_assemble_f64(cw, orc, p):
     assert rel_err(y, ref) <= TOL64
 
 
+CPB_DEFAULT = {1: 32, 2: 16, 3: 8, 4: 8, 5: 4, 6: 4, 7: 2}
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 4], ids=["df64", "f64native", "f32", "bf16"])
+@pytest.mark.parametrize("dims", [(4, 3, 5), (1, 3, 2), (2, 1, 1), (5, 1, 3), (9, 2, 2)])
+@pytest.mark.parametrize("p", [1, 2, 4, 7])
+def test_assemble_fused_x_matches_axis_passes(cw, p, dims, prec):
+    """The assembled apply sums the x-interfaces inside each operator tile in the kernel's epilogue
+    and leaves the rest to the DSS: bit-identical to a local apply followed by the three axis passes
+    of Algorithm struct_dss, for every tile size and staging mode (tiles that straddle x-rows and a
+    ragged last tile included)."""
+    import torch
+    mesh = synth.box_mesh(*dims, perturb=0.1)
+    M = cw.Mesh.from_synth(mesh)
+    op = cw.Operator(M, p, 3, cw.CW_GEOM_METRIC, prec)
+    x = torch.from_numpy(synth.cellwise_random(mesh, p, seed=40 + p)).cuda().to(op.vec_dtype)
+    variants = [(0, 0)] if prec == 1 else [(c, st) for c in (CPB_DEFAULT[p], CPB_DEFAULT[p] // 2) for st in (0, 1, 2)]
+    for cpb, stage in variants:
+        if cpb:
+            op.set_variant(cpb, stage)
+        y_fused = op.apply(x, assemble=True)
+        y_passes = op.dss(op.apply(x))
+        torch.cuda.synchronize()
+        assert torch.equal(y_fused, y_passes), (cpb, stage)
+
+
 @pytest.mark.parametrize("prec,tol", [(2, 2e-6), (3, 1e-2), (4, 3e-2)], ids=["f32", "f32_bf16g", "bf16"])
 @pytest.mark.parametrize("p", [1, 2, 4, 7])
 def test_apply_reduced_precision_error(cw, orc, p, prec, tol):
