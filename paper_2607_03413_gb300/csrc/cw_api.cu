@@ -362,6 +362,48 @@ __global__ void dss_x_from_kernel(const VS *__restrict__ src, VS *__restrict__ d
         if (i < n) dst[b + i] = v[i];
 }
 
+// r - a q with one rounding, written once so that every use (own line, partner copy) gives the same value
+template <class VS>
+__device__ __forceinline__ VS resid_update(VS r, VS q, VS a) { return fma(-a, q, r); }
+template <>
+__device__ __forceinline__ float resid_update<float>(float r, float q, float a) { return fmaf(-a, q, r); }
+
+// dst = x pass of (r - a q), a = *active ? *alpha : 0: the CG residual update r <- r - alpha A p fused
+// into the first pass of the DSS that follows it (the updated residual itself is only needed as S r).
+template <class VS>
+__global__ void dss_x_axpy_kernel(const VS *__restrict__ r, const VS *__restrict__ q,
+                                  const double *__restrict__ alpha, const int *__restrict__ active,
+                                  VS *__restrict__ dst, int nx, int p, uint32_t nlines, FastDiv fd_n2, FastDiv fd_nx)
+{
+    const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nlines) return;
+    const VS a = *active ? static_cast<VS>(*alpha) : VS(0);
+    const int n = p + 1;
+    const uint32_t n3 = fd_n2.d * n;
+    const uint32_t c = fd_n2.div(l);
+    const uint32_t cx = c - fd_nx.div(c) * static_cast<uint32_t>(nx);
+    const int64_t b = static_cast<int64_t>(l) * n;
+    VS v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        if (i < n) v[i] = resid_update(r[b + i], q[b + i], a);
+    if (cx > 0) v[0] = AddOp<VS>::add(resid_update(r[b - n3 + p], q[b - n3 + p], a), v[0]);
+    if (cx + 1 < static_cast<uint32_t>(nx)) v[p] = AddOp<VS>::add(v[p], resid_update(r[b + n3], q[b + n3], a));
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        if (i < n) dst[b + i] = v[i];
+}
+
+// r <- r - a q (a as above), the unfused form for vectors beyond 32-bit line indexing
+template <class VS>
+__global__ void resid_update_kernel(VS *__restrict__ r, const VS *__restrict__ q, const double *__restrict__ alpha,
+                                    const int *__restrict__ active, int64_t L)
+{
+    const VS a = *active ? static_cast<VS>(*alpha) : VS(0);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = resid_update(r[i], q[i], a);
+}
+
 template <class VS>
 static cudaError_t dss_typed(const Op &op, VS *v, int flags, cudaStream_t s, int first_axis = 0, int end_axis = 3,
                              int xtile = 0);
@@ -380,6 +422,34 @@ static cudaError_t dss_from_typed(const Op &op, const VS *src, VS *dst, int flag
     dss_x_from_kernel<VS><<<(nlines + 255) / 256, 256, 0, s>>>(src, dst, m.nx, op.p, nlines, FastDiv::make(op.n * op.n),
                                                                  FastDiv::make(m.nx));
     return dss_typed(op, dst, flags, s, 1);
+}
+
+template <class VS>
+static cudaError_t dss_from_axpy_typed(const Op &op, VS *r, const VS *q, const double *alpha, const int *active,
+                                       VS *dst, cudaStream_t s)
+{
+    if (op.L >= (int64_t)1 << 31) {
+        resid_update_kernel<VS><<<1216, 256, 0, s>>>(r, q, alpha, active, op.L);
+        return dss_from_typed(op, static_cast<const VS *>(r), dst, CW_DSS_SUM, s);
+    }
+    const uint32_t nlines = (uint32_t)(op.L / op.n);
+    dss_x_axpy_kernel<VS><<<(nlines + 255) / 256, 256, 0, s>>>(r, q, alpha, active, dst, op.mesh->nx, op.p, nlines,
+                                                                 FastDiv::make(op.n * op.n), FastDiv::make(op.mesh->nx));
+    return dss_typed(op, dst, CW_DSS_SUM, s, 1);
+}
+
+cudaError_t dss_from_axpy(const Op &op, void *r, const void *q, const double *alpha, const int *active, void *dst,
+                          cudaStream_t s)
+{
+    switch (vec_elem_size(op.prec)) {
+    case 8:
+        return dss_from_axpy_typed(op, static_cast<double *>(r), static_cast<const double *>(q), alpha, active,
+                                   static_cast<double *>(dst), s);
+    case 4:
+        return dss_from_axpy_typed(op, static_cast<float *>(r), static_cast<const float *>(q), alpha, active,
+                                   static_cast<float *>(dst), s);
+    default: return cudaErrorInvalidValue;  // the solver keeps FP32 or FP64 vectors
+    }
 }
 
 cudaError_t dss_from(const Op &op, const void *src, void *dst, int flags, cudaStream_t s)

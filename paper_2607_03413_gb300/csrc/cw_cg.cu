@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kRedThreads) k_precond(V *__restrict__ r, V *_
     df64 a1{0.0f, 0.0f}, a2{0.0f, 0.0f};
     CW_GRID_LOOP(k, n / W)
     {
-        Chunk<V> cr = ldc(r, k), cw = ldc(w, k);
+        Chunk<V> cr, cw = ldc(w, k);  // r is written only
         const Chunk<V> cd = ldc(dinv, k);
 #pragma unroll
         for (int l = 0; l < W; ++l) precond_one(cr.v[l], cw.v[l], cd.v[l], kappa[k * W + l], a1, a2);
@@ -188,51 +188,35 @@ __global__ void __launch_bounds__(kRedThreads) k_precond(V *__restrict__ r, V *_
     block_sum_store(df_to_double(a2), part + gridDim.x);
 }
 
-// u += alpha p ; r -= alpha q
+// u += alpha p (iteration active), then p = z + beta p (and not broken down): the iterate update
+// of the iteration joined to the direction update, one pass over p
 template <class V, class U>
-__global__ void k_update(U *__restrict__ u, const V *__restrict__ p, V *__restrict__ r, const V *__restrict__ q,
-                         int64_t n, const double *__restrict__ scal, const int *__restrict__ flags)
+__global__ void k_pupdate_u(U *__restrict__ u, V *__restrict__ p, const V *__restrict__ z, int64_t n,
+                            const double *__restrict__ scal, const int *__restrict__ flags)
 {
     static_assert(sizeof(U) == sizeof(V), "iterate and vectors share one type");
     if (!flags[F_ACTIVE]) return;
-    const V a = static_cast<V>(scal[S_ALPHA]);
+    const bool dir = flags[F_STATUS] != ST_BREAKDOWN;
+    const V a = static_cast<V>(scal[S_ALPHA]), beta = static_cast<V>(scal[S_BETA]);
     constexpr int W = Chunk<V>::W;
     CW_GRID_LOOP(k, n / W)
     {
-        Chunk<V> cu = ldc(reinterpret_cast<const V *>(u), k), cr = ldc(r, k);
-        const Chunk<V> cp = ldc(p, k), cq = ldc(q, k);
+        Chunk<V> cu = ldc(reinterpret_cast<const V *>(u), k), cp = ldc(p, k);
 #pragma unroll
-        for (int l = 0; l < W; ++l) {
-            cu.v[l] = cu.v[l] + a * cp.v[l];
-            cr.v[l] = cr.v[l] - a * cq.v[l];
-        }
+        for (int l = 0; l < W; ++l) cu.v[l] = cu.v[l] + a * cp.v[l];
         stc(reinterpret_cast<V *>(u), k, cu);
-        stc(r, k, cr);
+        if (dir) {
+            const Chunk<V> cz = ldc(z, k);
+#pragma unroll
+            for (int l = 0; l < W; ++l) cp.v[l] = cz.v[l] + beta * cp.v[l];
+            stc(p, k, cp);
+        }
     }
     for (int64_t i = n / W * W + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        u[i] = u[i] + a * p[i];
-        r[i] = r[i] - a * q[i];
+        const V pi = p[i];
+        u[i] = u[i] + a * pi;
+        if (dir) p[i] = z[i] + beta * pi;
     }
-}
-
-// p = z + beta p
-template <class V>
-__global__ void k_pupdate(V *__restrict__ p, const V *__restrict__ z, int64_t n, const double *__restrict__ scal,
-                          const int *__restrict__ flags)
-{
-    if (!flags[F_ACTIVE] || flags[F_STATUS] == ST_BREAKDOWN) return;
-    const V beta = static_cast<V>(scal[S_BETA]);
-    constexpr int W = Chunk<V>::W;
-    CW_GRID_LOOP(k, n / W)
-    {
-        Chunk<V> cp = ldc(p, k);
-        const Chunk<V> cz = ldc(z, k);
-#pragma unroll
-        for (int l = 0; l < W; ++l) cp.v[l] = cz.v[l] + beta * cp.v[l];
-        stc(p, k, cp);
-    }
-    for (int64_t i = n / W * W + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = z[i] + beta * p[i];
 }
 
 template <class D, class S>
@@ -436,7 +420,7 @@ __global__ void __launch_bounds__(kRedThreads) k_precond_fin(V *__restrict__ r, 
     df64 a1{0.0f, 0.0f}, a2{0.0f, 0.0f};
     CW_GRID_LOOP(k, n / W)
     {
-        Chunk<V> cr = ldc(r, k), cw = ldc(w, k);
+        Chunk<V> cr, cw = ldc(w, k);  // r is written only
         const Chunk<V> cd = ldc(dinv, k);
 #pragma unroll
         for (int l = 0; l < W; ++l) precond_one(cr.v[l], cw.v[l], cd.v[l], kappa[k * W + l], a1, a2);
@@ -555,11 +539,11 @@ static cudaError_t cg_iteration(const Op &aop, int ak, CgLevel &lv, U *u, CgScra
         if ((e = apply_by_kind(aop, ak, p, q, s)) != cudaSuccess) return e;
         k_dot_fin<V><<<vec_grid(), kRedThreads, 0, s>>>(p, q, L, c.partials, c.scal, c.flags, STAGE_PQ);
     }
-    k_update<V, U><<<vec_grid(), 256, 0, s>>>(u, p, r, q, L, c.scal, c.flags);
-    if ((e = dss_from(aop, r, z, CW_DSS_SUM, s)) != cudaSuccess) return e;  // z = S r
+    // z = S (r - alpha q): the residual update rides on the DSS's first pass
+    if ((e = dss_from_axpy(aop, r, q, c.scal + S_ALPHA, c.flags + F_ACTIVE, z, s)) != cudaSuccess) return e;
     k_precond_fin<V><<<vec_grid(), kRedThreads, 0, s>>>(r, z, dinv, L, c.kappa, c.partials, c.scal, c.flags,
                                                         STAGE_RHO);
-    k_pupdate<V><<<vec_grid(), 256, 0, s>>>(p, z, L, c.scal, c.flags);
+    k_pupdate_u<V, U><<<vec_grid(), 256, 0, s>>>(u, p, z, L, c.scal, c.flags);
     return cudaGetLastError();
 }
 

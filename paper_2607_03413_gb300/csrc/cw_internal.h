@@ -78,6 +78,11 @@ cudaError_t dss_launch(const Op &op, void *v, int flags, cudaStream_t s, int xti
 // out of place: dst = S src (flags CW_DSS_SUM) or S_bar src (CW_DSS_AVERAGE); the x pass is fused
 // with the copy
 cudaError_t dss_from(const Op &op, const void *src, void *dst, int flags, cudaStream_t s);
+// dst = S (r - a q) with a = *active ? *alpha : 0 (device scalars): the CG residual update fused into
+// the DSS (r is left unchanged unless the vector exceeds 32-bit line indexing, where it is updated
+// in place first). FP32 or FP64 vectors.
+cudaError_t dss_from_axpy(const Op &op, void *r, const void *q, const double *alpha, const int *active, void *dst,
+                          cudaStream_t s);
 
 // solver scratch release (cw_cg.cu)
 void cg_release(Op *op);
