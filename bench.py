@@ -12,7 +12,7 @@ time-to-1e-10 (plain FP64 Jacobi-PCG vs FP64 iterative refinement around an FP32
 the batched apply (16 RHS on Q5 64^3 + 48 uneven problems in one persistent launch).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-sweep] [--no-cg]
-                  [--no-batched] [--no-mixed] [--no-e2e] [--no-cpu] [--no-tune] [--cells N] [--prec P]
+                  [--no-batched] [--no-mixed] [--no-e2e] [--no-cpu] [--no-tune] [--variant C,S] [--cells N] [--prec P]
 
 --impl reference times the FP64 CPU oracle (explicit element matrices) on a bounded cell sample of
 the same workload on the host cores.
@@ -60,11 +60,15 @@ def peaks():
     return 6800.0, "fallback"
 
 
-# DRAM bytes per cell of the double-float K+M p=4 apply kernel, variant (8 cells/CTA, TMA staging):
-# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of a 40^3-cell case
-# (512.2 MB + 55.5 MB for 64,000 cells), to be scaled by the cell count of a launch.
-DF64_KM_P4_TRAFFIC_PER_CELL = (512.221696e6 + 55.474688e6) / 64000
-PROFILED_VARIANT = (8, 1)
+# DRAM bytes per cell of the double-float K+M p=4 apply kernel by variant (cells/CTA, staging):
+# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture per variant of a 40^3-cell case
+# (64,000 cells), to be scaled by the cell count of a launch. Variants not listed report null.
+DF64_KM_P4_TRAFFIC_PER_CELL = {
+    (8, 0): (512.082176e6 + 55.454976e6) / 64000,
+    (8, 1): (512.255488e6 + 55.196928e6) / 64000,
+    (8, 2): (512.073472e6 + 55.251712e6) / 64000,
+    (4, 2): (512.071424e6 + 55.187456e6) / 64000,
+}
 
 # FP32 issue-rate roofline for double-float arithmetic: 152 SMs x 128 FP32 lanes x 2.07 GHz,
 # 12 FP32 instructions per emulated FP64 multiply-add (2 flops).
@@ -203,7 +207,9 @@ def gpu_arm(args, rank, local, world):
     ug = torch.from_numpy(synth.global_vector(mesh, P, seed=rank)).cuda()
     x = op.gather(ug)
     y = op.empty()
-    if args.tune:
+    if args.variant:
+        op.set_variant(*[int(v) for v in args.variant.split(",")])
+    elif args.tune:
         op.autotune(x, y, reps=3)  # picks cells-per-CTA and TMA staging (before the timed region)
     variant = op.variant()
     torch.cuda.synchronize()
@@ -247,12 +253,12 @@ def gpu_arm(args, rank, local, world):
     achieved_tflops = fl / (kern_ms * 1e-3) / 1e12
     by = bytes_per_value(0, KIND) * op.L
     traffic = None
-    if args.prec == 0 and (variant[0], variant[1]) == PROFILED_VARIANT:
-        traffic = round(DF64_KM_P4_TRAFFIC_PER_CELL * args.cells ** 3)
+    if args.prec == 0 and (variant[0], variant[1]) in DF64_KM_P4_TRAFFIC_PER_CELL:
+        traffic = round(DF64_KM_P4_TRAFFIC_PER_CELL[(variant[0], variant[1])] * args.cells ** 3)
     roof = {"bound": "alu", "achieved": round(achieved_tflops, 3), "peak": round(DF64_PEAK_TFLOPS, 3),
             "unit": "TFLOP/s", "frac": round(achieved_tflops / DF64_PEAK_TFLOPS, 4), "traffic": traffic,
-            "traffic_note": "bytes per launch, ncu on a 40^3 case scaled by cells (null unless the timed variant "
-                            "is the profiled one)",
+            "traffic_note": "bytes per launch, ncu on a 40^3 case of the same variant scaled by cells (null for "
+                            "variants not profiled)",
             "kernel": f"apply_metric_kernel<N=5, cells/CTA={variant[0]}, staged={variant[1]}, double-float>",
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 12 instructions per double-float MAD",
             "hbm": {"achieved": round(by / (kern_ms * 1e-3) / 1e9, 1), "peak": hbm, "unit": "GB/s",
@@ -497,6 +503,7 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
     ap.add_argument("--no-tune", dest="tune", action="store_false", help="default kernel variant, no autotuning")
+    ap.add_argument("--variant", default="", help="cells_per_cta,stage of the main step's kernel (profiling cases)")
     ap.add_argument("--cells", type=int, default=NCELL, help="cells per direction (profiling cases)")
     ap.add_argument("--prec", type=int, default=0, help="CW_PREC_* of the main step (profiling cases)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
