@@ -978,7 +978,7 @@ cw_status cw_apply_host(cw_op oh, const void *x_host, void *y_host, int flags, v
     for (int i = 0; i < 3; ++i) CW_CUDA_TRY(cudaStreamWaitEvent(op->h_st[i], op->h_done, 0));
     const Mesh &m = *op->mesh;
     const int64_t plane = (int64_t)m.nx * m.ny;  // cells per z-layer
-    const int planes = std::max(1, (m.nz + 7) / 8);
+    const int planes = std::max(1, (m.nz + 15) / 16);  // at most 16 slabs (the event arrays)
     const int nslab = (m.nz + planes - 1) / planes;
     const size_t gbytes_per_cell = op->geo_bytes / op->E;
     unsigned char *dx = static_cast<unsigned char *>(op->h_dx), *dy = static_cast<unsigned char *>(op->h_dy);
@@ -986,10 +986,19 @@ cw_status cw_apply_host(cw_op oh, const void *x_host, void *y_host, int flags, v
     unsigned char *hy = static_cast<unsigned char *>(y_host);
     // a view of the operator on z-layers [z0, z0 + nzv)
     std::vector<Mesh> views(nslab + 1);
+    // slab views share the operator's device data; the host copy of the vertices is not carried
+    // (copying it per slab made the host, not the GPU, the bottleneck of this entry point)
+    auto shallow = [&](int nzv) {
+        Mesh v;
+        v.nx = m.nx;
+        v.ny = m.ny;
+        v.nz = nzv;
+        v.d_verts = m.d_verts;
+        v.cartesian = m.cartesian;
+        return v;
+    };
     auto view = [&](int vi, int z0, int nzv, Op &o) {
-        views[vi] = m;
-        views[vi].nz = nzv;
-        views[vi].h_verts.clear();
+        views[vi] = shallow(nzv);
         o = *op;
         o.mesh = &views[vi];
         o.E = plane * nzv;
@@ -1001,9 +1010,7 @@ cw_status cw_apply_host(cw_op oh, const void *x_host, void *y_host, int flags, v
         off = (size_t)(z0 * plane * n3) * es;
         bytes = (size_t)(nz * plane * n3) * es;
     };
-    Mesh bview = m;  // two-layer view across a slab interface
-    bview.nz = 2;
-    bview.h_verts.clear();
+    Mesh bview = shallow(2);  // two-layer view across a slab interface
     for (int k = 0; k < nslab; ++k) {
         size_t off, bytes;
         slab_bytes(k, off, bytes);
