@@ -192,6 +192,49 @@ def time_apply(cw, op, x, y, steps, warmup, stream, assemble=True):
     return step_ms, kern_ms
 
 
+def host_link(xh, yh, x, y, stream, reps=5):
+    """Host link rates with whole-vector pinned copies (CUDA events): H2D, D2H and both at once on two
+    streams; bound_ms = the bytes of one host-buffer step over the two-way rate."""
+    import torch
+    s2 = torch.cuda.Stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = event_pair()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def h2d():
+        with torch.cuda.stream(stream):
+            x.copy_(xh, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(stream):
+            yh.copy_(y, non_blocking=True)
+
+    def both():
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        s2.wait_event(ev)
+        with torch.cuda.stream(stream):
+            x.copy_(xh, non_blocking=True)
+        with torch.cuda.stream(s2):
+            yh.copy_(y, non_blocking=True)
+        ev2 = torch.cuda.Event()
+        ev2.record(s2)
+        stream.wait_event(ev2)
+
+    nb = x.numel() * x.element_size()
+    t_in, t_out, t_both = timed(h2d), timed(d2h), timed(both)
+    return {"h2d_gbs": round(nb / t_in / 1e6, 1), "d2h_gbs": round(nb / t_out / 1e6, 1),
+            "both_gbs": round(2 * nb / t_both / 1e6, 1), "bound_ms": round(t_both, 3)}
+
+
 def gpu_arm(args, rank, local, world):
     import torch
 
@@ -247,7 +290,8 @@ def gpu_arm(args, rank, local, world):
         e2e_ms = max_over_ranks(a.elapsed_time(b) / args.steps, world)
         e2e = {"value": units / (e2e_ms * 1e-3), "unit": "DoF/s", "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": op.L * x.element_size(), "d2h_bytes_per_step": op.L * x.element_size(),
-               "api": "cw_apply_host (pinned host x and y, CW_APPLY_ASSEMBLE)"}
+               "api": "cw_apply_host (pinned host x and y, CW_APPLY_ASSEMBLE)",
+               "link": host_link(xh, yh, x, y, stream)}
 
     fl = flops_per_value(n, KIND) * op.L
     achieved_tflops = fl / (kern_ms * 1e-3) / 1e12

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "cw_apply.cuh"
+#include "cw_index.cuh"
 #include "cw_internal.h"
 #include "cw_launch.cuh"
 
@@ -215,18 +216,6 @@ __global__ void gather_kernel(const double *__restrict__ ug, VS *__restrict__ x,
 // both copies. One thread per (interface, face node); no atomics; exchange partners at static
 // offsets.
 
-// 32-bit division by a runtime constant: q = umulhi(x, floor((2^32-1)/d)), corrected once
-struct FastDiv {
-    uint32_t d, m;
-    static FastDiv make(uint32_t d) { return FastDiv{d, 0xFFFFFFFFu / d}; }
-    __device__ __forceinline__ uint32_t div(uint32_t x) const
-    {
-        uint32_t q = __umulhi(x, m);
-        if ((q + 1) * d <= x) ++q;
-        return q;
-    }
-};
-
 // grid: x covers (face node, first in-face cell coordinate, interface coordinate along ax),
 // y the remaining cell coordinate. All index arithmetic is 32-bit.
 template <class VS>
@@ -426,28 +415,30 @@ static cudaError_t dss_from_typed(const Op &op, const VS *src, VS *dst, int flag
 
 template <class VS>
 static cudaError_t dss_from_axpy_typed(const Op &op, VS *r, const VS *q, const double *alpha, const int *active,
-                                       VS *dst, cudaStream_t s)
+                                       VS *dst, bool x_only, cudaStream_t s)
 {
     if (op.L >= (int64_t)1 << 31) {
+        if (x_only) return cudaErrorInvalidValue;
         resid_update_kernel<VS><<<1216, 256, 0, s>>>(r, q, alpha, active, op.L);
         return dss_from_typed(op, static_cast<const VS *>(r), dst, CW_DSS_SUM, s);
     }
     const uint32_t nlines = (uint32_t)(op.L / op.n);
     dss_x_axpy_kernel<VS><<<(nlines + 255) / 256, 256, 0, s>>>(r, q, alpha, active, dst, op.mesh->nx, op.p, nlines,
                                                                  FastDiv::make(op.n * op.n), FastDiv::make(op.mesh->nx));
+    if (x_only) return cudaGetLastError();
     return dss_typed(op, dst, CW_DSS_SUM, s, 1);
 }
 
 cudaError_t dss_from_axpy(const Op &op, void *r, const void *q, const double *alpha, const int *active, void *dst,
-                          cudaStream_t s)
+                          cudaStream_t s, bool x_only)
 {
     switch (vec_elem_size(op.prec)) {
     case 8:
         return dss_from_axpy_typed(op, static_cast<double *>(r), static_cast<const double *>(q), alpha, active,
-                                   static_cast<double *>(dst), s);
+                                   static_cast<double *>(dst), x_only, s);
     case 4:
         return dss_from_axpy_typed(op, static_cast<float *>(r), static_cast<const float *>(q), alpha, active,
-                                   static_cast<float *>(dst), s);
+                                   static_cast<float *>(dst), x_only, s);
     default: return cudaErrorInvalidValue;  // the solver keeps FP32 or FP64 vectors
     }
 }

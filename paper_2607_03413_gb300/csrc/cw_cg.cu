@@ -25,8 +25,10 @@
 #include <cstdlib>
 #include <mutex>
 #include <string>
+#include <type_traits>
 
 #include "cw_arith.cuh"
+#include "cw_index.cuh"
 #include "cw_internal.h"
 
 namespace cw {
@@ -434,6 +436,115 @@ __global__ void __launch_bounds__(kRedThreads) k_precond_fin(V *__restrict__ r, 
     last_block_finalize(part, scal, flags, stage);
 }
 
+// Line access of the fused kernel below: N consecutive values; one 16-byte access for N = 4 floats
+// (every line start there is 16-byte aligned: lines are 16 bytes apart and the partner offsets are
+// multiples of 4 floats).
+template <int N, class V>
+struct LineIO {
+    static __device__ __forceinline__ void ld(const V *p, V (&v)[N])
+    {
+#pragma unroll
+        for (int m = 0; m < N; ++m) v[m] = p[m];
+    }
+    static __device__ __forceinline__ void st(V *p, const V (&v)[N])
+    {
+#pragma unroll
+        for (int m = 0; m < N; ++m) p[m] = v[m];
+    }
+};
+template <>
+struct LineIO<4, float> {
+    static __device__ __forceinline__ void ld(const float *p, float (&v)[4])
+    {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    }
+    static __device__ __forceinline__ void st(float *p, const float (&v)[4])
+    {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+
+// The y and z passes of the DSS fused with the preconditioner: w holds S_x r' (x pass done, from
+// dss_from_axpy); every x-line gathers its y-partner, z-partner and yz-partner lines and sums them in
+// the passes' order ((own + y) + (z + zy), each copy the same tree, so all copies agree and the result
+// equals the in-place passes bit for bit); then z_out = D^-1 s, r = s / kappa and the partials of
+// <r, z> and <m s, r> as k_precond_fin. Out of place (w is only read). One thread per x-line,
+// 32-bit line indexing (nlines < 2^31).
+template <int N, class V>
+__global__ void __launch_bounds__(kRedThreads) k_precond_yz_fin(
+    const V *__restrict__ w, V *__restrict__ r, V *__restrict__ zo, const V *__restrict__ dinv,
+    const uint8_t *__restrict__ kappa, uint32_t nlines, int nx, int ny, int nz, FastDiv fd_nx, FastDiv fd_ny,
+    double *__restrict__ part, double *__restrict__ scal, int *__restrict__ flags, int stage)
+{
+    if (stage == STAGE_RHO && flags[F_DONE]) return;  // an iteration after convergence
+    constexpr int P = N - 1, N2 = N * N, N3 = N2 * N;
+    using IO = LineIO<N, V>;
+    const int sx = nx * N3, sxy = nx * ny * N3;  // < L < 2^31
+    df64 a1{0.0f, 0.0f}, a2{0.0f, 0.0f};
+    for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < nlines; l += gridDim.x * blockDim.x) {
+        const uint32_t e = l / N2;
+        const int rl = static_cast<int>(l - e * N2), j = rl % N, k = rl / N;
+        const uint32_t q = fd_nx.div(e), cz = fd_ny.div(q);
+        const int cy = static_cast<int>(q - cz * static_cast<uint32_t>(ny));
+        const int oy = (j == 0 && cy > 0) ? -(sx - P * N) : ((j == P && cy < ny - 1) ? (sx - P * N) : 0);
+        const int oz = (k == 0 && cz > 0) ? -(sxy - P * N2) : ((k == P && (int)cz < nz - 1) ? (sxy - P * N2) : 0);
+        const V *b = w + static_cast<size_t>(l) * N;
+        V sv[N], t[N];
+        IO::ld(b, sv);
+        if (oy) {
+            IO::ld(b + oy, t);
+#pragma unroll
+            for (int m = 0; m < N; ++m) sv[m] = sv[m] + t[m];
+        }
+        if (oz) {
+            V c[N];
+            IO::ld(b + oz, c);
+            if (oy) {
+                IO::ld(b + oz + oy, t);
+#pragma unroll
+                for (int m = 0; m < N; ++m) c[m] = c[m] + t[m];
+            }
+#pragma unroll
+            for (int m = 0; m < N; ++m) sv[m] = sv[m] + c[m];
+        }
+        const size_t o = static_cast<size_t>(l) * N;
+        V dv[N], rv[N];
+        IO::ld(dinv + o, dv);
+#pragma unroll
+        for (int m = 0; m < N; ++m) precond_one(rv[m], sv[m], dv[m], kappa[o + m], a1, a2);
+        IO::st(r + o, rv);
+        IO::st(zo + o, sv);
+    }
+    block_sum_store(df_to_double(a1), part);
+    block_sum_store(df_to_double(a2), part + gridDim.x);
+    last_block_finalize(part, scal, flags, stage);
+}
+
+template <class V>
+static cudaError_t launch_precond_yz(const Op &op, const V *w, V *r, V *zo, const V *dinv, const uint8_t *kappa,
+                                     double *part, double *scal, int *flags, int stage, cudaStream_t s)
+{
+    const Mesh &m = *op.mesh;
+    const uint32_t nl = static_cast<uint32_t>(op.L / op.n);
+    const FastDiv fx = FastDiv::make(m.nx), fy = FastDiv::make(m.ny);
+#define CW_PYZ(NN)                                                                                     \
+    k_precond_yz_fin<NN, V><<<kRedBlocks, kRedThreads, 0, s>>>(w, r, zo, dinv, kappa, nl, m.nx, m.ny, m.nz, fx, fy, \
+                                                              part, scal, flags, stage)
+    switch (op.n) {
+    case 2: CW_PYZ(2); break;
+    case 3: CW_PYZ(3); break;
+    case 4: CW_PYZ(4); break;
+    case 5: CW_PYZ(5); break;
+    case 6: CW_PYZ(6); break;
+    case 7: CW_PYZ(7); break;
+    case 8: CW_PYZ(8); break;
+    default: return cudaErrorInvalidValue;
+    }
+#undef CW_PYZ
+    return cudaGetLastError();
+}
+
 // --------------------------------------------------------------------------- host side ----
 static unsigned vec_grid() { return kRedBlocks; }
 
@@ -538,6 +649,19 @@ static cudaError_t cg_iteration(const Op &aop, int ak, CgLevel &lv, U *u, CgScra
     } else {
         if ((e = apply_by_kind(aop, ak, p, q, s)) != cudaSuccess) return e;
         k_dot_fin<V><<<vec_grid(), kRedThreads, 0, s>>>(p, q, L, c.partials, c.scal, c.flags, STAGE_PQ);
+    }
+    if constexpr (std::is_same<V, float>::value) {
+        if (L < ((int64_t)1 << 31)) {
+            // FP32 level: z = S_x(r - alpha q), then the y and z sums gathered inside the
+            // preconditioner pass, which writes the preconditioned residual into q (free once the x
+            // pass has read it)
+            e = dss_from_axpy(aop, r, q, c.scal + S_ALPHA, c.flags + F_ACTIVE, z, s, true);
+            if (e != cudaSuccess) return e;
+            e = launch_precond_yz<V>(aop, z, r, q, dinv, c.kappa, c.partials, c.scal, c.flags, STAGE_RHO, s);
+            if (e != cudaSuccess) return e;
+            k_pupdate_u<V, U><<<vec_grid(), 256, 0, s>>>(u, p, q, L, c.scal, c.flags);
+            return cudaGetLastError();
+        }
     }
     // z = S (r - alpha q): the residual update rides on the DSS's first pass
     if ((e = dss_from_axpy(aop, r, q, c.scal + S_ALPHA, c.flags + F_ACTIVE, z, s)) != cudaSuccess) return e;

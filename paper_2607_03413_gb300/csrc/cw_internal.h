@@ -80,9 +80,10 @@ cudaError_t dss_launch(const Op &op, void *v, int flags, cudaStream_t s, int xti
 cudaError_t dss_from(const Op &op, const void *src, void *dst, int flags, cudaStream_t s);
 // dst = S (r - a q) with a = *active ? *alpha : 0 (device scalars): the CG residual update fused into
 // the DSS (r is left unchanged unless the vector exceeds 32-bit line indexing, where it is updated
-// in place first). FP32 or FP64 vectors.
+// in place first). FP32 or FP64 vectors. x_only: only the x pass (the caller completes the y and z
+// sums; needs L < 2^31, else cudaErrorInvalidValue).
 cudaError_t dss_from_axpy(const Op &op, void *r, const void *q, const double *alpha, const int *active, void *dst,
-                          cudaStream_t s);
+                          cudaStream_t s, bool x_only = false);
 
 // solver scratch release (cw_cg.cu)
 void cg_release(Op *op);
