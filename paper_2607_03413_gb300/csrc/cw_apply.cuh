@@ -192,8 +192,9 @@ __host__ __device__ constexpr size_t metric_smem_bytes(int nc, int stage)
 // One tile of `cpt` consecutive cells starting at cell tile*cpt, worked by CPB cell slots of N*N
 // threads (cpt <= CPB; slots c >= cpt compute on zeros and store nothing, so a CTA may have more
 // threads than the tile needs). STAGE (see metric_smem_bytes; staging needs cpt == CPB).
-// DOT: also accumulate this thread's share of <x, y> over its final x-line into *dot (double-float
-// products of the values as stored in y; the x line is re-read from global memory, L1/L2-resident).
+// DOT: also accumulate this thread's share of <x, A x> into *dot, as the quadrature sum over its
+// pencil of (grad u)^T G (grad u) + c u^2 (double-float accumulation): the same quadratic form as
+// x^T A_e x cell by cell, read off the quadrature-point step with no extra memory traffic.
 // asm_nx > 0 (the mesh's cells per x-row): the x pass of Algorithm struct_dss is applied to the
 // x-interfaces between cells of this tile before the store (the two end values of each x-line are
 // exchanged through shared memory and summed as that pass sums them); the interfaces between tiles
@@ -343,6 +344,11 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
                     Ar::mad(hx, gz[k], gxz);
                     Ar::mad(hy, gz[k], gyz);
                     Ar::mad(hz, gz[k], gzz);
+                    if constexpr (DOT) {  // (grad u)^T G (grad u) at this point
+                        df_mad(*dot, Ar::to_df(gx[k]), Ar::to_df(hx));
+                        df_mad(*dot, Ar::to_df(gy[k]), Ar::to_df(hy));
+                        df_mad(*dot, Ar::to_df(gz[k]), Ar::to_df(hz));
+                    }
                     gx[k] = Ar::norm(hx);
                     gy[k] = Ar::norm(hy);
                     gz[k] = Ar::norm(hz);
@@ -350,6 +356,7 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
                 if (HAS_M) {
                     const T cm = Ar::from(g[(NC - 1) * N3]);
                     acc[k] = Ar::norm(Ar::mul(u[k], cm));
+                    if constexpr (DOT) df_mad(*dot, Ar::to_df(u[k]), Ar::to_df(acc[k]));  // c u^2
                 }
             }
         }
@@ -418,15 +425,6 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
                 VS *yc = yr + cell * N3 + N * r;
 #pragma unroll
                 for (int m = 0; m < N; ++m) Ar::to(yc[m], w[m]);
-                if constexpr (DOT) {
-                    const VS *xc = xr + cell * N3 + N * r;
-#pragma unroll
-                    for (int m = 0; m < N; ++m) {
-                        VS ys;
-                        Ar::to(ys, w[m]);
-                        df_mad(*dot, Ar::to_df(Ar::from(ldg_nc(xc + m))), Ar::to_df(Ar::from(ys)));
-                    }
-                }
             }
         }
     }
@@ -449,7 +447,7 @@ __global__ void __launch_bounds__(N *N *CPB) apply_metric_kernel(const VS *__res
     metric_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw, nullptr, asm_nx);
 }
 
-// y = A x and the CTA's partial of <x, y> in part[blockIdx.x] (deterministic: fixed order in a CTA)
+// y = A x and the CTA's partial of <x, A x> in part[blockIdx.x] (deterministic: fixed order in a CTA)
 template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
 __global__ void __launch_bounds__(N *N *CPB) apply_metric_dot_kernel(const VS *__restrict__ x, VS *__restrict__ y,
                                                                       const GS *__restrict__ geo, int64_t ncells,
