@@ -33,7 +33,25 @@ struct Batch {
     int grid = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
+    // grouped mode: the degree groups run on their own streams, forked from and joined to the
+    // caller's stream, so that one group's CTAs fill the SMs another group's tail leaves idle
+    cudaStream_t g_stream[9] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[9] = {};
 };
+
+static void batch_free(Batch *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->d_probs);
+    cudaFree(b->d_counter);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (int n = 0; n < 9; ++n) {
+        if (b->g_stream[n]) cudaStreamDestroy(b->g_stream[n]);
+        if (b->ev_join[n]) cudaEventDestroy(b->ev_join[n]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    delete b;
+}
 
 static cw_status batch_rebuild(Batch &b)
 {
@@ -96,15 +114,20 @@ static cudaError_t batch_enqueue(const Batch &b, cudaStream_t s)
     if (b.mode == CW_BATCH_SINGLE)
         return b.fp64 ? batch_launch_df(b.d_probs, (int)b.h_probs.size(), b.nitems, b.d_counter, b.smem, b.grid, s)
                       : batch_launch_f32(b.d_probs, (int)b.h_probs.size(), b.nitems, b.d_counter, b.smem, b.grid, s);
+    if ((e = cudaEventRecord(b.ev_fork, s)) != cudaSuccess) return e;
     for (int n = 2; n <= 8; ++n) {
         if (!b.g_count[n]) continue;
         const int v = b.variant[n];
         const int kmax = (b.g_kind[n] & 1) ? 3 : 2;  // metric components of the largest kind present
+        cudaStream_t gs = b.g_stream[n];
+        if ((e = cudaStreamWaitEvent(gs, b.ev_fork, 0)) != cudaSuccess) return e;
         e = b.fp64 ? batch_degree_launch_df(n, v & 1, v >> 1, *b.tabs[n], b.d_probs + b.g_first[n], (int)b.g_count[n],
-                                            b.g_items[n], b.d_counter + n, kmax, s)
+                                            b.g_items[n], b.d_counter + n, kmax, gs)
                    : batch_degree_launch_f32(n, v & 1, v >> 1, *b.tabs[n], b.d_probs + b.g_first[n], (int)b.g_count[n],
-                                             b.g_items[n], b.d_counter + n, kmax, s);
+                                             b.g_items[n], b.d_counter + n, kmax, gs);
         if (e != cudaSuccess) return e;
+        if ((e = cudaEventRecord(b.ev_join[n], gs)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, b.ev_join[n], 0)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -161,18 +184,18 @@ cw_status cw_batch_create(const cw_op *ops, const int *nrhs, const void *const *
     if (e == cudaSuccess) e = cudaMalloc(&b->d_probs, nprob * sizeof(BatchProb));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 9 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    for (int n = 2; n <= 8 && e == cudaSuccess; ++n) {
+        e = cudaStreamCreateWithFlags(&b->g_stream[n], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[n], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
-        cudaFree(b->d_probs);
-        cudaFree(b->d_counter);
-        delete b;
+        batch_free(b);
         return cuda_fail(e, "cw_batch_create");
     }
     cw_status st = batch_rebuild(*b);
     if (st != CW_OK) {
-        cudaFree(b->d_probs);
-        cudaFree(b->d_counter);
-        cudaStreamDestroy(b->cap_stream);
-        delete b;
+        batch_free(b);
         return st;
     }
     *out = reinterpret_cast<cw_batch>(b);
@@ -183,11 +206,7 @@ cw_status cw_batch_destroy(cw_batch bh)
 {
     Batch *b = reinterpret_cast<Batch *>(bh);
     if (!b) return fail(CW_ERR_ARG, "cw_batch_destroy: NULL");
-    if (b->graph) cudaGraphExecDestroy(b->graph);
-    cudaFree(b->d_probs);
-    cudaFree(b->d_counter);
-    cudaStreamDestroy(b->cap_stream);
-    delete b;
+    batch_free(b);
     return CW_OK;
 }
 

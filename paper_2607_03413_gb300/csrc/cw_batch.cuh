@@ -12,6 +12,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "cw_apply.cuh"
 #include "cw_internal.h"
 
@@ -118,13 +120,29 @@ __device__ __forceinline__ void batch_body(const BatchProb *__restrict__ probs, 
     }
 }
 
+// the constant-memory tables of one arithmetic's units (specialised where they are defined)
+template <class C>
+__device__ __forceinline__ const BatchTables<C> &batch_tables();
+
+// One tile of the grouped mode, kept out of line for double-float arithmetic: inlined into the
+// persistent item loop, its 1D tables (loop-invariant, two floats per entry) were hoisted into
+// registers, which took the kernel from ~80 to 128-166 registers; out of line every table entry
+// stays an immediate constant-bank operand, as in the per-operator kernel. (FP32 bodies stay inline:
+// the call costs them more than it saves.)
+template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
+__device__ __noinline__ void grouped_tile(const VS *x, VS *y, const GS *g, int64_t ncells, int kind, int64_t tile)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    metric_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, g, ncells, kind, batch_tab<N>(batch_tables<typename Ar::C>()), tile,
+                                           CPB, smem_raw);
+}
+
 // ---- grouped mode: one persistent kernel per degree, shaped like the per-operator kernel
-// (N*N*CPB threads, its own register allocation, optional TMA staging). Work items are
-// (problem, chunk of tiles, right-hand side) over the problems of that degree only.
+// (N*N*CPB threads, optional TMA staging). Work items are (problem, chunk of tiles, right-hand
+// side) over the problems of that degree only.
 template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
 __global__ void __launch_bounds__(N *N *CPB) batch_degree_kernel(const BatchProb *__restrict__ probs, int nprob,
-                                                                  int64_t nitems, unsigned long long *__restrict__ counter,
-                                                                  TabMetric<N, typename Ar::C> tab)
+                                                                  int64_t nitems, unsigned long long *__restrict__ counter)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ long long s_next;
@@ -155,7 +173,11 @@ __global__ void __launch_bounds__(N *N *CPB) batch_degree_kernel(const BatchProb
         const int64_t t0 = chunk * P.tpi, t1 = min(P.ntiles, t0 + P.tpi);
         for (int64_t tile = t0; tile < t1; ++tile) {
             if (tile > t0) __syncthreads();
-            metric_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, g, P.ncells, P.kind, tab, tile, CPB, smem_raw);
+            if constexpr (std::is_same<Ar, ArDF>::value)
+                grouped_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, g, P.ncells, P.kind, tile);
+            else
+                metric_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, g, P.ncells, P.kind,
+                                                       batch_tab<N>(batch_tables<typename Ar::C>()), tile, CPB, smem_raw);
         }
     }
 }

@@ -7,6 +7,11 @@
 namespace cw {
 
 __constant__ BatchTables<df64> c_batch_tabs_df;
+template <>
+__device__ __forceinline__ const BatchTables<df64> &batch_tables<df64>()
+{
+    return c_batch_tabs_df;
+}
 
 __global__ void __launch_bounds__(kBatchThreads, 4) batch_kernel_df(const BatchProb *__restrict__ probs, int nprob,
                                                                    int64_t nitems, unsigned long long *__restrict__ counter)
@@ -55,8 +60,7 @@ template <int N, int CPB, int STAGE>
 static cudaError_t grouped(const Tables1D &tb, const BatchProb *d_probs, int nprob, int64_t nitems,
                            unsigned long long *counter, int kind_max, cudaStream_t s)
 {
-    TabMetric<N, df64> tab;
-    fill_metric_tab<N>(tab, tb, mk);
+    (void)tb;  // the tables are in constant memory (uploaded at batch creation)
     // shared memory for the largest metric of the group (kind_max components)
     const size_t smem = metric_smem_bytes<N, CPB, typename ArDF::T, df64s>(metric_ncomp(kind_max), STAGE);
     auto kern = batch_degree_kernel<N, CPB, ArDF, double, df64s, STAGE>;
@@ -73,7 +77,7 @@ static cudaError_t grouped(const Tables1D &tb, const BatchProb *d_probs, int npr
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t grid = std::min<int64_t>(std::max(1, per_sm) * (int64_t)sms, nitems);
-    kern<<<(unsigned)std::max<int64_t>(grid, 1), N * N * CPB, smem, s>>>(d_probs, nprob, nitems, counter, tab);
+    kern<<<(unsigned)std::max<int64_t>(grid, 1), N * N * CPB, smem, s>>>(d_probs, nprob, nitems, counter);
     return cudaGetLastError();
 }
 
