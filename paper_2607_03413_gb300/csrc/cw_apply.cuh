@@ -18,6 +18,8 @@
 //   y = a_x (M x M x K) u + a_y (M x K x M) u + a_z (K x M x M) u + a_m (M x M x M) u
 // evaluated as two x-contractions, three y-contractions and two z-contractions.
 #pragma once
+#include <type_traits>
+
 #include "cw_arith.cuh"
 #include "cw_tma.cuh"
 
@@ -31,12 +33,26 @@ namespace cw {
 // E[a][b] = (M[a][b] + M[a][N-1-b])/2, O[a][b] = (M[a][b] - M[a][N-1-b])/2, Mid[a] = M[a][h].
 // This halves the multiply-adds of a line contraction (Kronbichler and Kormann's even-odd
 // decomposition for sum factorisation).
+// For double-float tables the same entries are also stored lane-paired, P[a][b] = (E[a][b], O[a][b])
+// and PM[a] = (Mid[a], 0), so that the even and odd sums of an output pair run as one paired
+// multiply-add chain with each coefficient pair one 64-bit constant operand.
+template <class C>
+struct EOPair {
+    struct type {};
+};
+template <>
+struct EOPair<df64> {
+    using type = df64p;
+};
+
 template <int N, class C>
 struct EOMat {
     static constexpr int H = N / 2, NA = (N + 1) / 2;
     C E[NA][H > 0 ? H : 1];
     C O[NA][H > 0 ? H : 1];
     C Mid[NA];
+    typename EOPair<C>::type P[NA][H > 0 ? H : 1];
+    typename EOPair<C>::type PM[NA];
 };
 
 template <int N, class C>
@@ -102,18 +118,41 @@ __device__ __forceinline__ void contract_eo(const EOMat<N, typename Ar::C> &M, c
         e[b] = Ar::add(in[b], in[N - 1 - b]);
         o[b] = Ar::sub(in[b], in[N - 1 - b]);
     }
+    if constexpr (std::is_same<Ar, ArDF>::value) {
+        // Double-float: the even and odd sums of an output pair run as one chain of paired FP32
+        // operations (lane x even, lane y odd; the middle term enters lane y multiplied by 0, which
+        // leaves it unchanged), each lane bit-identical to the scalar chain. (Pairing the e/o
+        // formation and the final add/subtract as well was slower: the lane shuffles cost more.)
+        df64p eo[H];
 #pragma unroll
-    for (int a = 0; a < H; ++a) {
-        T ye = Ar::mul(e[0], M.E[a][0]);
+        for (int b = 0; b < H; ++b) eo[b] = dfp_pack(e[b], o[b]);
+        df64p xm;
+        if constexpr (N % 2 == 1) xm = dfp_pack(in[H], in[H]);
 #pragma unroll
-        for (int b = 1; b < H; ++b) Ar::mad(ye, e[b], M.E[a][b]);
-        if constexpr (N % 2 == 1) Ar::mad(ye, in[H], M.Mid[a]);
-        T yo = Ar::mul(o[0], M.O[a][0]);
+        for (int a = 0; a < H; ++a) {
+            df64p y2 = dfp_mul(eo[0], M.P[a][0]);
 #pragma unroll
-        for (int b = 1; b < H; ++b) Ar::mad(yo, o[b], M.O[a][b]);
-        out[a] = Ar::norm(Ar::add(ye, yo));
-        const T d = Ar::sub(ye, yo);
-        out[N - 1 - a] = Ar::norm(S > 0 ? d : Ar::neg(d));
+            for (int b = 1; b < H; ++b) dfp_mad(y2, eo[b], M.P[a][b]);
+            if constexpr (N % 2 == 1) dfp_mad(y2, xm, M.PM[a]);
+            const T ye = dfp_x(y2), yo = dfp_y(y2);
+            out[a] = Ar::norm(Ar::add(ye, yo));
+            const T d = Ar::sub(ye, yo);
+            out[N - 1 - a] = Ar::norm(S > 0 ? d : Ar::neg(d));
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < H; ++a) {
+            T ye = Ar::mul(e[0], M.E[a][0]);
+#pragma unroll
+            for (int b = 1; b < H; ++b) Ar::mad(ye, e[b], M.E[a][b]);
+            if constexpr (N % 2 == 1) Ar::mad(ye, in[H], M.Mid[a]);
+            T yo = Ar::mul(o[0], M.O[a][0]);
+#pragma unroll
+            for (int b = 1; b < H; ++b) Ar::mad(yo, o[b], M.O[a][b]);
+            out[a] = Ar::norm(Ar::add(ye, yo));
+            const T d = Ar::sub(ye, yo);
+            out[N - 1 - a] = Ar::norm(S > 0 ? d : Ar::neg(d));
+        }
     }
     if constexpr (N % 2 == 1) {  // middle output: only the even (S = +1) or odd (S = -1) part
         if constexpr (S > 0) {

@@ -133,6 +133,54 @@ __device__ __forceinline__ df64 df_add(df64 a, df64 b)
     return r;
 }
 
+// ------------------------------------------------- paired double-float operations ----
+// Two independent double-float values in one register-pair form: hi = (a.hi, b.hi), lo = (a.lo,
+// b.lo). The operations below are the scalar ones above applied to both lanes with the paired FP32
+// instructions of sm_100+ (FADD2 / FMUL2 / FFMA2: two FP32 operations per thread instruction, same
+// rounding per lane as the scalar forms), so each lane's result is bit-identical to the scalar
+// operation and the FP32 pipe gets half the instructions to issue.
+struct __align__(16) df64p {
+    float2 hi, lo;
+};
+
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e)
+{
+    s = __fadd2_rn(a, b);
+    const float2 bb = __fadd2_rn(s, neg2(a));
+    e = __fadd2_rn(__fadd2_rn(a, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(b, neg2(bb)));
+}
+
+// lane-wise df_mul
+__device__ __forceinline__ df64p dfp_mul(df64p a, df64p b)
+{
+    df64p r;
+    r.hi = __fmul2_rn(a.hi, b.hi);
+    float2 e = __ffma2_rn(a.hi, b.hi, neg2(r.hi));
+    e = __ffma2_rn(a.hi, b.lo, e);
+    e = __ffma2_rn(a.lo, b.hi, e);
+    r.lo = e;
+    return r;
+}
+
+// lane-wise df_mad
+__device__ __forceinline__ void dfp_mad(df64p &acc, df64p a, df64p b)
+{
+    const float2 p = __fmul2_rn(a.hi, b.hi);
+    float2 e = __ffma2_rn(a.hi, b.hi, neg2(p));
+    e = __ffma2_rn(a.hi, b.lo, e);
+    e = __ffma2_rn(a.lo, b.hi, e);
+    float2 s, t;
+    two_sum2(acc.hi, p, s, t);
+    acc.hi = s;
+    acc.lo = __fadd2_rn(acc.lo, __fadd2_rn(t, e));
+}
+
+__device__ __forceinline__ df64p dfp_pack(df64 a, df64 b) { return df64p{make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
+__device__ __forceinline__ df64 dfp_x(df64p a) { return df64{a.hi.x, a.lo.x}; }
+__device__ __forceinline__ df64 dfp_y(df64p a) { return df64{a.hi.y, a.lo.y}; }
+
 // ------------------------------------------------------------ arithmetic traits ----
 // Each trait defines the register type T, the constant type C used for the 1D tables, and
 // mul / mad / add / norm plus conversions from and to each storage type.

@@ -3,6 +3,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "cw_apply.cuh"
 #include "cw_internal.h"
 
@@ -27,6 +29,17 @@ struct MakeC<ArF32> {
     static float from(double v) { return static_cast<float>(v); }
 };
 
+// lane pair (a, b) of two double-float constants (host side)
+inline df64p pair(df64 a, df64 b)
+{
+    df64p p;
+    p.hi.x = a.hi;
+    p.hi.y = b.hi;
+    p.lo.x = a.lo;
+    p.lo.y = b.lo;
+    return p;
+}
+
 // fills the full and even-odd forms of B and D from the double tables
 template <int N, class C, class MK>
 void fill_metric_tab(TabMetric<N, C> &t, const Tables1D &tb, MK mk)
@@ -49,6 +62,10 @@ void fill_metric_tab(TabMetric<N, C> &t, const Tables1D &tb, MK mk)
                 E.O[a][b] = mk(b < H ? 0.5 * (M[a][b] - M[a][N - 1 - b]) : 0.0);
             }
             E.Mid[a] = mk((N % 2 == 1) ? M[a][H] : 0.0);
+            if constexpr (std::is_same<C, df64>::value) {
+                for (int b = 0; b < (H > 0 ? H : 1); ++b) E.P[a][b] = pair(E.E[a][b], E.O[a][b]);
+                E.PM[a] = pair(E.Mid[a], df64{0.0f, 0.0f});
+            }
         }
     };
     eo(t.Bf, B);
