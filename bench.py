@@ -342,6 +342,25 @@ def gpu_arm(args, rank, local, world):
     if mixed:
         out["mixed"] = mixed
 
+    # stored vs recomputed metric on the same workload: the recomputed operator reads 21
+    # trilinear-map coefficients per cell instead of 7 metric values per quadrature point
+    recomp = {}
+    for name, prec in ([("f64", cw.CW_PREC_F64), ("f32", cw.CW_PREC_F32), ("bf16", cw.CW_PREC_BF16)]
+                       if args.mixed else []):
+        o = cw.Operator(M, P, KIND, cw.CW_GEOM_RECOMPUTE, prec)
+        xx = o.gather(ug)
+        yy = o.empty()
+        o.autotune(xx, yy, reps=3)
+        sm, km = time_apply(cw, o, xx, yy, args.steps, args.warmup, stream)
+        sv = {cw.CW_PREC_F64: 8, cw.CW_PREC_F32: 4, cw.CW_PREC_BF16: 2}[prec]
+        sg = 8 if prec == cw.CW_PREC_F64 else 4
+        gbs = (2 * sv + 21 * sg / n ** 3) * o.L / (km * 1e-3) / 1e9
+        recomp[name] = {"dofs_per_s": o.L / (sm * 1e-3), "ms_per_step": sm, "apply_kernel_ms": km,
+                        "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4), "variant": o.variant()}
+        o.close()
+    if recomp:
+        out["recomputed_metric"] = recomp
+
     if args.sweep:
         out["sweep"] = degree_sweep(cw, stream, hbm, args)
     if args.cg:

@@ -69,6 +69,8 @@ typedef enum {
 /* geometry representations */
 #define CW_GEOM_AFFINE 0 /* Cartesian cells: factored 1D stiffness/mass form, per-cell scalars */
 #define CW_GEOM_METRIC 1 /* curved trilinear cells: metric w detJ J^-1 J^-T stored per quad. point */
+#define CW_GEOM_RECOMPUTE 2 /* curved trilinear cells: metric recomputed at every quadrature point
+                               from 21 trilinear-map coefficients per cell (Sec. 6, J and det J) */
 
 /* precisions (vector storage / metric storage / arithmetic) */
 #define CW_PREC_F64 0        /* FP64 / FP64 / double-float (FP32 pair, ~47-bit) arithmetic */
@@ -120,8 +122,11 @@ cw_status cw_mesh_destroy(cw_mesh m);
 /*
  * Create an operator of degree p on a mesh (Sec. 2.1). Allocates and fills the geometry
  * (CW_GEOM_METRIC: ncomp values per quadrature point, ncomp = 6 Laplace, 1 mass, 7 both, stored
- * in the metric precision; CW_GEOM_AFFINE: 4 doubles per cell, and the mesh must be Cartesian --
- * CW_ERR_ARG otherwise) and the 1D tables. Synchronous.
+ * in the metric precision; CW_GEOM_RECOMPUTE: the 21 coefficients a1..a7 of each cell's trilinear
+ * map, as float pairs for the FP64 precisions and floats otherwise -- no per-point storage, the
+ * metric is formed in the kernel; CW_GEOM_AFFINE: 4 doubles per cell, and the mesh must be
+ * Cartesian -- CW_ERR_ARG otherwise) and the 1D tables. Curved modes check det J > 0 at every
+ * quadrature point (CW_ERR_ARG otherwise). Synchronous.
  */
 cw_status cw_op_create(cw_mesh m, int degree, int kind, int geom, int prec, int bc, cw_op *out);
 cw_status cw_op_destroy(cw_op op);
@@ -136,7 +141,9 @@ int64_t cw_op_device_bytes(cw_op op);
  * metric tiles moved into shared memory with bulk asynchronous copies (TMA) at kernel entry; 2 the
  * input tile by TMA and the metric tile prefetched into L2 by a bulk prefetch (less shared memory,
  * more CTAs per SM). Results do not depend on the variant beyond rounding order. CW_PREC_F64_NATIVE has only
- * the default variant (CW_ERR_UNSUPPORTED otherwise).
+ * the default variant (CW_ERR_UNSUPPORTED otherwise). CW_GEOM_RECOMPUTE operators use the default
+ * cells per CTA (another choice gives CW_ERR_UNSUPPORTED); stages 1 and 2 both stage the input
+ * tile by TMA there (there is no metric tile).
  */
 cw_status cw_op_set_variant(cw_op op, int cells_per_cta, int stage);
 /* Current variant; choices2 (may be NULL) receives the two cells-per-CTA choices of the degree. */
@@ -184,7 +191,7 @@ cw_status cw_diagonal(cw_op op, double *d, void *stream);
 /*
  * Unassembled load vector b_K,i = sum_q w_q detJ f(x_q) phi_i(x_q) (FP64 cell-wise) for the
  * manufactured problems: which = 0: f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z); which = 1:
- * f = 2[y(1-y)z(1-z) + x(1-x)z(1-z) + x(1-x)y(1-y)]. Needs a CW_GEOM_METRIC or AFFINE op.
+ * f = 2[y(1-y)z(1-z) + x(1-x)z(1-z) + x(1-x)y(1-y)]. Formed from the mesh vertices (any geometry mode).
  */
 cw_status cw_load_vector(cw_op op, int which, double *b, void *stream);
 

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libcwfem.so")
 CW_OK, CW_ERR_ARG, CW_ERR_OOM, CW_ERR_CUDA = 0, 1, 2, 3
 CW_ERR_NOT_CONVERGED, CW_ERR_BREAKDOWN, CW_ERR_TIMEOUT, CW_ERR_UNSUPPORTED = 4, 5, 6, 7
 CW_LAPLACE, CW_MASS, CW_LAPLACE_MASS = 1, 2, 3
-CW_GEOM_AFFINE, CW_GEOM_METRIC = 0, 1
+CW_GEOM_AFFINE, CW_GEOM_METRIC, CW_GEOM_RECOMPUTE = 0, 1, 2
 CW_PREC_F64, CW_PREC_F64_NATIVE, CW_PREC_F32, CW_PREC_F32_BF16G, CW_PREC_BF16 = 0, 1, 2, 3, 4
 CW_BC_NONE, CW_BC_DIRICHLET0 = 0, 1
 CW_APPLY_LOCAL, CW_APPLY_ASSEMBLE = 0, 1

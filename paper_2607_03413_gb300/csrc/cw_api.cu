@@ -171,6 +171,51 @@ __global__ void metric_kernel(const double *__restrict__ V, int nx, int ny, int6
     if (kind & 2) store_g(g + (nc - 1) * n3, m[6]);
 }
 
+// det J > 0 at every quadrature point (recomputed geometry stores no per-point data)
+__global__ void detj_check_kernel(const double *__restrict__ V, int nx, int ny, int64_t E, int n, Rule1D rule,
+                                  int *__restrict__ bad)
+{
+    const int n3 = n * n * n;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= E * n3) return;
+    const int64_t e = t / n3;
+    const int q = (int)(t - e * n3), a = q % n, b = (q / n) % n, c = q / (n * n);
+    double J[3][3], X[3], m[7], det;
+    cell_jacobian(V, nx, ny, e, rule.xq[a], rule.xq[b], rule.xq[c], J, X);
+    qp_metric(J, 1.0, m, &det);
+    if (!(det > 0.0)) atomicOr(bad, 1);
+}
+
+// coefficients a1..a7 of the trilinear map of each cell from its 8 vertices X_{ijk} (i, j, k the
+// x, y, z bits): a1 = X100 - X000, a2 = X010 - X000, a3 = X001 - X000, a4 = X110 - X100 - X010 + X000,
+// a5 = X101 - X100 - X001 + X000, a6 = X011 - X010 - X001 + X000,
+// a7 = X111 - X110 - X101 - X011 + X100 + X010 + X001 - X000; formed in FP64, stored rounded
+template <class GS>
+__global__ void trilinear_coef_kernel(const double *__restrict__ V, int nx, int ny, int64_t E, GS *__restrict__ coef)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    const int64_t cx = e % nx, cy = (e / nx) % ny, cz = e / ((int64_t)nx * ny);
+    GS *o = coef + e * kTriCoef;
+    for (int d = 0; d < 3; ++d) {
+        double X[2][2][2];
+        for (int v = 0; v < 8; ++v) {
+            const int b0 = v & 1, b1 = (v >> 1) & 1, b2 = (v >> 2) & 1;
+            const int64_t vid = ((cz + b2) * (ny + 1) + (cy + b1)) * (int64_t)(nx + 1) + (cx + b0);
+            X[b0][b1][b2] = V[vid * 3 + d];
+        }
+        const double a[7] = {
+            X[1][0][0] - X[0][0][0],
+            X[0][1][0] - X[0][0][0],
+            X[0][0][1] - X[0][0][0],
+            X[1][1][0] - X[1][0][0] - X[0][1][0] + X[0][0][0],
+            X[1][0][1] - X[1][0][0] - X[0][0][1] + X[0][0][0],
+            X[0][1][1] - X[0][1][0] - X[0][0][1] + X[0][0][0],
+            X[1][1][1] - X[1][1][0] - X[1][0][1] - X[0][1][1] + X[1][0][0] + X[0][1][0] + X[0][0][1] - X[0][0][0]};
+        for (int i = 0; i < 7; ++i) store_g(o + 3 * i + d, a[i]);
+    }
+}
+
 // Cartesian per-cell scalars (a_x, a_y, a_z, a_m), masked by the operator kind
 __global__ void affine_kernel(const double *__restrict__ V, int nx, int ny, int64_t E, int kind, double *__restrict__ geo)
 {
@@ -668,7 +713,8 @@ cw_status cw_op_create(cw_mesh mh, int degree, int kind, int geom, int prec, int
     if (!m) return fail(CW_ERR_ARG, "cw_op_create: NULL mesh");
     if (degree < 1 || degree > kMaxDegree) return fail(CW_ERR_ARG, "cw_op_create: degree must be in 1..7");
     if (kind < 1 || kind > 3) return fail(CW_ERR_ARG, "cw_op_create: bad kind");
-    if (geom != CW_GEOM_AFFINE && geom != CW_GEOM_METRIC) return fail(CW_ERR_ARG, "cw_op_create: bad geometry mode");
+    if (geom != CW_GEOM_AFFINE && geom != CW_GEOM_METRIC && geom != CW_GEOM_RECOMPUTE)
+        return fail(CW_ERR_ARG, "cw_op_create: bad geometry mode");
     if (prec < CW_PREC_F64 || prec > CW_PREC_BF16) return fail(CW_ERR_ARG, "cw_op_create: bad precision");
     if (bc != CW_BC_NONE && bc != CW_BC_DIRICHLET0) return fail(CW_ERR_ARG, "cw_op_create: bad bc");
     if (geom == CW_GEOM_AFFINE && !m->cartesian)
@@ -707,6 +753,31 @@ cw_status cw_op_create(cw_mesh mh, int degree, int kind, int geom, int prec, int
             else
                 metric_kernel<__nv_bfloat16><<<blocks, 256>>>(m->d_verts, m->nx, m->ny, op->E, op->n, kind, rule,
                                                               static_cast<__nv_bfloat16 *>(op->d_geo), d_bad);
+            e = cudaGetLastError();
+        }
+        int bad = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
+        cudaFree(d_bad);
+        if (e == cudaSuccess && bad) {
+            cudaFree(op->d_geo);
+            delete op;
+            return fail(CW_ERR_ARG, "cw_op_create: non-positive Jacobian determinant at a quadrature point");
+        }
+    } else if (geom == CW_GEOM_RECOMPUTE) {
+        const bool f64 = metric_is_f64(prec);
+        op->geo_bytes = op->E * kTriCoef * (int64_t)(f64 ? sizeof(df64s) : sizeof(float));
+        e = cudaMalloc(&op->d_geo, op->geo_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(d_bad, 0, sizeof(int));
+        if (e == cudaSuccess) {
+            const int64_t nthr = op->E * n3;
+            detj_check_kernel<<<(unsigned)((nthr + 255) / 256), 256>>>(m->d_verts, m->nx, m->ny, op->E, op->n, rule,
+                                                                        d_bad);
+            const unsigned cb = (unsigned)((op->E + 255) / 256);
+            if (f64)
+                trilinear_coef_kernel<df64s><<<cb, 256>>>(m->d_verts, m->nx, m->ny, op->E, static_cast<df64s *>(op->d_geo));
+            else
+                trilinear_coef_kernel<float><<<cb, 256>>>(m->d_verts, m->nx, m->ny, op->E, static_cast<float *>(op->d_geo));
             e = cudaGetLastError();
         }
         int bad = 0;
@@ -862,6 +933,8 @@ cw_status cw_op_set_variant(cw_op oh, int cells_per_cta, int stage)
     if (stage < 0 || stage > 2) return fail(CW_ERR_ARG, "cw_op_set_variant: stage must be 0, 1 or 2");
     if (op->prec == CW_PREC_F64_NATIVE && (cells_per_cta != 0 || stage != 0))
         return fail(CW_ERR_UNSUPPORTED, "cw_op_set_variant: CW_PREC_F64_NATIVE has only the default variant");
+    if (op->geom == CW_GEOM_RECOMPUTE && cells_per_cta != 0 && cells_per_cta != ch[0])
+        return fail(CW_ERR_UNSUPPORTED, "cw_op_set_variant: CW_GEOM_RECOMPUTE uses the default cells per CTA");
     op->cpb = cells_per_cta == ch[0] ? 0 : cells_per_cta;
     op->stage = stage;
     return CW_OK;
@@ -901,8 +974,11 @@ cw_status cw_op_autotune(cw_op oh, const void *x, void *y, int reps, void *strea
     CW_CUDA_TRY(cudaEventCreate(&e1));
     float best = 1e30f;
     int bc = 0, bs = op->stage;
-    const int nstage = op->geom == CW_GEOM_METRIC ? 3 : 1;
-    for (int ci = 0; ci < 2; ++ci)
+    // curved: both tile sizes x three staging modes; recomputed geometry: default tile, direct or
+    // TMA-staged input; Cartesian: both tile sizes
+    const int nstage = op->geom == CW_GEOM_METRIC ? 3 : (op->geom == CW_GEOM_RECOMPUTE ? 2 : 1);
+    const int ncpb = op->geom == CW_GEOM_RECOMPUTE ? 1 : 2;
+    for (int ci = 0; ci < ncpb; ++ci)
         for (int st = 0; st < nstage; ++st) {
             op->cpb = ci == 0 ? 0 : ch[1];
             op->stage = st;

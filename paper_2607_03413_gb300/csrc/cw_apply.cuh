@@ -60,7 +60,13 @@ struct TabMetric {
     C B[N][N];  // B[q][m] = l_m(xi_q): Gauss-Lobatto basis at the Gauss points
     C D[N][N];  // D[q][r] = derivative at xi_q of the Lagrange basis on the Gauss points
     EOMat<N, C> Bf, Bt, Df, Dt;  // even-odd forms of B, B^T (s = +1), D, D^T (s = -1)
+    C xq[N], wq[N];              // Gauss points and weights on [0,1] (recomputed geometry)
 };
+
+// Recomputed geometry: per cell the 21 coefficients a1..a7 (3 components each) of the trilinear
+// map x(xi) = a0 + a1 xi + a2 eta + a3 zeta + a4 xi eta + a5 xi zeta + a6 eta zeta + a7 xi eta zeta,
+// layout [cell][7][3]; a0 is not needed (only derivatives enter the metric).
+constexpr int kTriCoef = 21;
 
 template <int N, class C>
 struct TabAffine {
@@ -238,12 +244,17 @@ __host__ __device__ constexpr size_t metric_smem_bytes(int nc, int stage)
 // x-interfaces between cells of this tile before the store (the two end values of each x-line are
 // exchanged through shared memory and summed as that pass sums them); the interfaces between tiles
 // are left to the DSS.
-template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool DOT = false>
+// RC: geo holds the trilinear coefficients (kTriCoef per cell) and the metric of every quadrature
+// point is recomputed from them (Sec. 6: J, det J, J^-1 at the point): G = (w / det J) [c_a . c_b]
+// with c_0 = J_eta x J_zeta, c_1 = J_zeta x J_xi, c_2 = J_xi x J_eta (the rows of det J J^-1), and
+// the mass coefficient w det J.
+template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool DOT = false, bool RC = false>
 __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__restrict__ y, const GS *__restrict__ geo,
                                             int64_t ncells, int kind, const TabMetric<N, typename Ar::C> &tab,
                                             int64_t tile, int cpt, unsigned char *smem_raw, df64 *dot = nullptr,
                                             int asm_nx = 0)
 {
+    static_assert(!(RC && STAGE == 1), "recomputed geometry has no metric tile to stage");
     using T = typename Ar::T;
     using L = Lines<N>;
     constexpr int N2 = N * N, N3 = N2 * N, CS = L::CS;
@@ -295,8 +306,10 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
         bar = reinterpret_cast<uint64_t *>(smem_raw + (3 * CPB * CS * sizeof(T) + 15) / 16 * 16);
         VS *sX = reinterpret_cast<VS *>(S0 + CPB * CS);
         const VS *xsrc = x + cell0 * N3;
-        const GS *gsrc = geo + cell0 * NC * N3;
-        const uint32_t xb = CPB * N3 * sizeof(VS), gb = CPB * NC * N3 * sizeof(GS);
+        constexpr int GV = RC ? kTriCoef : 0;  // geometry values per cell (RC), else NC * N3
+        const int gpc = RC ? GV : NC * N3;
+        const GS *gsrc = geo + cell0 * gpc;
+        const uint32_t xb = CPB * N3 * sizeof(VS), gb = CPB * gpc * sizeof(GS);
         const bool full = cell0 + CPB <= ncells;
         const bool ok = full && aligned16(xsrc) && aligned16(sX) && (xb % 16 == 0);
         if (t == 0 && full && aligned16(gsrc) && (gb % 16 == 0)) bulk_prefetch_l2(gsrc, gb);
@@ -368,14 +381,98 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
             if (g_smem) g_smem = mbar_wait_bounded(bar + 1, 0);
         }
         {
-            const GS *gc = g_smem ? gs + r : geo + (act ? cell : 0) * (NC * N3) + r;
+            const GS *gc = g_smem ? gs + r : geo + (act ? cell : 0) * (RC ? kTriCoef : NC * N3) + (RC ? 0 : r);
+            // RC: the pencil's Jacobian columns as J_xi = P0 + zeta P1, J_eta = Q0 + zeta Q1, J_zeta = Z
+            T P0[3], P1[3], Q0[3], Q1[3], Z[3], wab;
+            if constexpr (RC) {
+                T xi = tab.xq[0], eta = tab.xq[0], wa = tab.wq[0], wb = tab.wq[0];
+#pragma unroll
+                for (int m = 1; m < N; ++m) {
+                    if (ra == m) xi = tab.xq[m], wa = tab.wq[m];
+                    if (rb == m) eta = tab.xq[m], wb = tab.wq[m];
+                }
+                wab = Ar::norm(Ar::mul(wa, wb));
+                const T xe = Ar::norm(Ar::mul(xi, eta));
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const T a1 = Ar::from(gc[0 + d]), a2 = Ar::from(gc[3 + d]), a3 = Ar::from(gc[6 + d]);
+                    const T a4 = Ar::from(gc[9 + d]), a5 = Ar::from(gc[12 + d]), a6 = Ar::from(gc[15 + d]);
+                    const T a7 = Ar::from(gc[18 + d]);
+                    T t = a1;
+                    Ar::mad(t, a4, eta);
+                    P0[d] = Ar::norm(t);
+                    t = a5;
+                    Ar::mad(t, a7, eta);
+                    P1[d] = Ar::norm(t);
+                    t = a2;
+                    Ar::mad(t, a4, xi);
+                    Q0[d] = Ar::norm(t);
+                    t = a6;
+                    Ar::mad(t, a7, xi);
+                    Q1[d] = Ar::norm(t);
+                    t = a3;
+                    Ar::mad(t, a5, xi);
+                    Ar::mad(t, a6, eta);
+                    Ar::mad(t, a7, xe);
+                    Z[d] = Ar::norm(t);
+                }
+            }
 #pragma unroll
             for (int k = 0; k < N; ++k) {
                 const GS *g = gc + N2 * k;
+                T gxx, gyy, gzz, gxy, gxz, gyz, cmr;
+                if constexpr (RC) {
+                    const T zeta = tab.xq[k];
+                    T jx[3], jy[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        T t = P0[d];
+                        Ar::mad(t, P1[d], zeta);
+                        jx[d] = Ar::norm(t);
+                        t = Q0[d];
+                        Ar::mad(t, Q1[d], zeta);
+                        jy[d] = Ar::norm(t);
+                    }
+                    auto cross = [](const T (&a)[3], const T (&b)[3], T (&c)[3]) {
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+                            T t = Ar::mul(a[d1], b[d2]);
+                            Ar::mad(t, Ar::neg(a[d2]), b[d1]);
+                            c[d] = Ar::norm(t);
+                        }
+                    };
+                    auto dot3 = [](const T (&a)[3], const T (&b)[3]) {
+                        T t = Ar::mul(a[0], b[0]);
+                        Ar::mad(t, a[1], b[1]);
+                        Ar::mad(t, a[2], b[2]);
+                        return Ar::norm(t);
+                    };
+                    T c0[3], c1[3], c2[3];
+                    cross(jy, Z, c0);
+                    cross(Z, jx, c1);
+                    cross(jx, jy, c2);
+                    const T det = dot3(jx, c0);
+                    const T w = Ar::norm(Ar::mul(wab, tab.wq[k]));
+                    cmr = Ar::norm(Ar::mul(w, det));
+                    if (HAS_K) {
+                        const T sc = Ar::div(w, det);
+                        gxx = Ar::norm(Ar::mul(sc, dot3(c0, c0)));
+                        gyy = Ar::norm(Ar::mul(sc, dot3(c1, c1)));
+                        gzz = Ar::norm(Ar::mul(sc, dot3(c2, c2)));
+                        gxy = Ar::norm(Ar::mul(sc, dot3(c0, c1)));
+                        gxz = Ar::norm(Ar::mul(sc, dot3(c0, c2)));
+                        gyz = Ar::norm(Ar::mul(sc, dot3(c1, c2)));
+                    }
+                } else {
+                    if (HAS_K) {
+                        gxx = Ar::from(g[0 * N3]), gyy = Ar::from(g[1 * N3]);
+                        gzz = Ar::from(g[2 * N3]), gxy = Ar::from(g[3 * N3]);
+                        gxz = Ar::from(g[4 * N3]), gyz = Ar::from(g[5 * N3]);
+                    }
+                    if (HAS_M) cmr = Ar::from(g[(NC - 1) * N3]);
+                }
                 if (HAS_K) {
-                    const T gxx = Ar::from(g[0 * N3]), gyy = Ar::from(g[1 * N3]);
-                    const T gzz = Ar::from(g[2 * N3]), gxy = Ar::from(g[3 * N3]);
-                    const T gxz = Ar::from(g[4 * N3]), gyz = Ar::from(g[5 * N3]);
                     T hx = Ar::mul(gx[k], gxx), hy = Ar::mul(gx[k], gxy), hz = Ar::mul(gx[k], gxz);
                     Ar::mad(hx, gy[k], gxy);
                     Ar::mad(hy, gy[k], gyy);
@@ -393,7 +490,7 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
                     gz[k] = Ar::norm(hz);
                 }
                 if (HAS_M) {
-                    const T cm = Ar::from(g[(NC - 1) * N3]);
+                    const T cm = cmr;
                     acc[k] = Ar::norm(Ar::mul(u[k], cm));
                     if constexpr (DOT) df_mad(*dot, Ar::to_df(u[k]), Ar::to_df(acc[k]));  // c u^2
                 }
@@ -476,18 +573,19 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
     }
 }
 
-template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
+template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool RC = false>
 __global__ void __launch_bounds__(N *N *CPB) apply_metric_kernel(const VS *__restrict__ x, VS *__restrict__ y,
                                                                   const GS *__restrict__ geo, int64_t ncells,
                                                                   int kind, TabMetric<N, typename Ar::C> tab,
                                                                   int asm_nx)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    metric_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw, nullptr, asm_nx);
+    metric_tile<N, CPB, Ar, VS, GS, STAGE, false, RC>(x, y, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw, nullptr,
+                                                      asm_nx);
 }
 
 // y = A x and the CTA's partial of <x, A x> in part[blockIdx.x] (deterministic: fixed order in a CTA)
-template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
+template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool RC = false>
 __global__ void __launch_bounds__(N *N *CPB) apply_metric_dot_kernel(const VS *__restrict__ x, VS *__restrict__ y,
                                                                       const GS *__restrict__ geo, int64_t ncells,
                                                                       int kind, TabMetric<N, typename Ar::C> tab,
@@ -496,7 +594,7 @@ __global__ void __launch_bounds__(N *N *CPB) apply_metric_dot_kernel(const VS *_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double s_red[(N * N * CPB + 31) / 32];
     df64 acc{0.0f, 0.0f};
-    metric_tile<N, CPB, Ar, VS, GS, STAGE, true>(x, y, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw, &acc);
+    metric_tile<N, CPB, Ar, VS, GS, STAGE, true, RC>(x, y, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw, &acc);
     double v = df_to_double(acc);
     // N^2 * CPB is not always a multiple of 32: the last warp may hold only nw lanes
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

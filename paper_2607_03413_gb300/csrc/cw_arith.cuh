@@ -123,6 +123,26 @@ __device__ __forceinline__ void df_mad(df64 &acc, df64 a, df64 b)
     acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, e));
 }
 
+// a / b in double-float: quotient estimate q1 from the leading floats, the remainder a - q1 b
+// in double-float, one correction q2 from it, q1 + q2 renormalised (long division, as in
+// Dekker 1971); relative error about 2^-44.
+__device__ __forceinline__ df64 df_div(df64 a, df64 b)
+{
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    // r = a - q1 * b with the product exact in two floats
+    const float p = __fmul_rn(q1, b.hi);
+    const float pe = __fmaf_rn(q1, b.hi, -p);
+    float s, t;
+    two_sum(a.hi, -p, s, t);
+    const float rl = __fadd_rn(__fadd_rn(t, -pe), __fadd_rn(a.lo, -__fmul_rn(q1, b.lo)));
+    const float r = __fadd_rn(s, rl);
+    const float q2 = __fdiv_rn(r, b.hi);
+    df64 q;
+    q.hi = __fadd_rn(q1, q2);
+    q.lo = __fsub_rn(q2, __fsub_rn(q.hi, q1));
+    return q;
+}
+
 __device__ __forceinline__ df64 df_add(df64 a, df64 b)
 {
     float s, t;
@@ -195,6 +215,7 @@ struct ArDF {  // double-float arithmetic
     static __device__ __forceinline__ T sub(T a, T b) { return df_add(a, T{-b.hi, -b.lo}); }
     static __device__ __forceinline__ T neg(T a) { return T{-a.hi, -a.lo}; }
     static __device__ __forceinline__ T norm(T a) { return df_norm(a); }
+    static __device__ __forceinline__ T div(T a, T b) { return df_div(a, b); }
     static __device__ __forceinline__ T from(double v) { return split_f64(v); }
     static __device__ __forceinline__ T from(float v) { return T{v, 0.0f}; }
     static __device__ __forceinline__ T from(df64s v) { return T{v.hi, v.lo}; }
@@ -213,6 +234,7 @@ struct ArF64 {  // native FP64
     static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
     static __device__ __forceinline__ T neg(T a) { return -a; }
     static __device__ __forceinline__ T norm(T a) { return a; }
+    static __device__ __forceinline__ T div(T a, T b) { return a / b; }
     static __device__ __forceinline__ T from(double v) { return v; }
     static __device__ __forceinline__ T from(df64s v) { return widen_f32(v.hi) + widen_f32(v.lo); }
     static __device__ __forceinline__ void to(double &d, T a) { d = a; }
@@ -229,6 +251,7 @@ struct ArF32 {  // FP32
     static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
     static __device__ __forceinline__ T neg(T a) { return -a; }
     static __device__ __forceinline__ T norm(T a) { return a; }
+    static __device__ __forceinline__ T div(T a, T b) { return __fdiv_rn(a, b); }
     static __device__ __forceinline__ T from(float v) { return v; }
     static __device__ __forceinline__ T from(__nv_bfloat16 v) { return __bfloat162float(v); }
     static __device__ __forceinline__ void to(float &d, T a) { d = a; }

@@ -72,7 +72,22 @@ void fill_metric_tab(TabMetric<N, C> &t, const Tables1D &tb, MK mk)
     eo(t.Bt, Bt);
     eo(t.Df, D);
     eo(t.Dt, Dt);
+    for (int a = 0; a < N; ++a) {
+        t.xq[a] = mk(tb.xq[a]);
+        t.wq[a] = mk(tb.wq[a]);
+    }
 }
+
+// storage type of the recomputed geometry's coefficients: float pairs for the FP64 arithmetics,
+// float for FP32 arithmetic (whatever the vector and metric storage)
+template <class Ar>
+struct RCStore {
+    using type = df64s;
+};
+template <>
+struct RCStore<ArF32> {
+    using type = float;
+};
 
 // cells per CTA: the default (about 128-200 threads) and the alternative the tuner can pick
 template <int N>
@@ -96,13 +111,13 @@ static cudaError_t opt_in_smem(K kernel, size_t smem)
 
 // xfuse != nullptr: the kernel also applies the x pass of the DSS inside each tile and *xfuse
 // receives the tile size (cells), so the DSS x pass only has the interfaces between tiles left
-template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
+template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool RC = false>
 cudaError_t launch_metric(const Op &op, const void *x, void *y, cudaStream_t s, int *xfuse = nullptr)
 {
     TabMetric<N, typename Ar::C> tab;
     fill_metric_tab<N>(tab, op.tab, [](double v) { return MakeC<Ar>::from(v); });
     const size_t smem = metric_smem_bytes<N, CPB, typename Ar::T, GS>(metric_ncomp(op.kind), STAGE);
-    auto kern = apply_metric_kernel<N, CPB, Ar, VS, GS, STAGE>;
+    auto kern = apply_metric_kernel<N, CPB, Ar, VS, GS, STAGE, RC>;
     static size_t opted = 0;  // largest size opted in so far for this instantiation
     if (smem > opted) {
         cudaError_t e = opt_in_smem(kern, smem);
@@ -119,14 +134,14 @@ cudaError_t launch_metric(const Op &op, const void *x, void *y, cudaStream_t s, 
 
 // y = A x with the CTA partials of <x, y> written to part (default tile size, TMA staging);
 // *nblocks receives the number of partials
-template <int N, class Ar, class VS, class GS>
+template <int N, class Ar, class VS, class GS, bool RC = false>
 cudaError_t launch_metric_dot(const Op &op, const void *x, void *y, double *part, int64_t *nblocks, cudaStream_t s)
 {
-    constexpr int CPB = cpb_default<N>();
+    constexpr int CPB = cpb_default<N>(), ST = RC ? 2 : 1;
     TabMetric<N, typename Ar::C> tab;
     fill_metric_tab<N>(tab, op.tab, [](double v) { return MakeC<Ar>::from(v); });
-    const size_t smem = metric_smem_bytes<N, CPB, typename Ar::T, GS>(metric_ncomp(op.kind), 1);
-    auto kern = apply_metric_dot_kernel<N, CPB, Ar, VS, GS, 1>;
+    const size_t smem = metric_smem_bytes<N, CPB, typename Ar::T, GS>(metric_ncomp(op.kind), ST);
+    auto kern = apply_metric_dot_kernel<N, CPB, Ar, VS, GS, ST, RC>;
     static size_t opted = 0;
     if (smem > opted) {
         cudaError_t e = opt_in_smem(kern, smem);
@@ -140,19 +155,27 @@ cudaError_t launch_metric_dot(const Op &op, const void *x, void *y, double *part
     return cudaGetLastError();
 }
 
+template <class Ar, class VS, class GS, bool RC>
+cudaError_t launch_dot_degree_rc(const Op &op, const void *x, void *y, double *part, int64_t *nb, cudaStream_t s)
+{
+    switch (op.n) {
+    case 2: return launch_metric_dot<2, Ar, VS, GS, RC>(op, x, y, part, nb, s);
+    case 3: return launch_metric_dot<3, Ar, VS, GS, RC>(op, x, y, part, nb, s);
+    case 4: return launch_metric_dot<4, Ar, VS, GS, RC>(op, x, y, part, nb, s);
+    case 5: return launch_metric_dot<5, Ar, VS, GS, RC>(op, x, y, part, nb, s);
+    case 6: return launch_metric_dot<6, Ar, VS, GS, RC>(op, x, y, part, nb, s);
+    case 7: return launch_metric_dot<7, Ar, VS, GS, RC>(op, x, y, part, nb, s);
+    case 8: return launch_metric_dot<8, Ar, VS, GS, RC>(op, x, y, part, nb, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <class Ar, class VS, class GS>
 cudaError_t launch_dot_degree(const Op &op, const void *x, void *y, double *part, int64_t *nb, cudaStream_t s)
 {
-    switch (op.n) {
-    case 2: return launch_metric_dot<2, Ar, VS, GS>(op, x, y, part, nb, s);
-    case 3: return launch_metric_dot<3, Ar, VS, GS>(op, x, y, part, nb, s);
-    case 4: return launch_metric_dot<4, Ar, VS, GS>(op, x, y, part, nb, s);
-    case 5: return launch_metric_dot<5, Ar, VS, GS>(op, x, y, part, nb, s);
-    case 6: return launch_metric_dot<6, Ar, VS, GS>(op, x, y, part, nb, s);
-    case 7: return launch_metric_dot<7, Ar, VS, GS>(op, x, y, part, nb, s);
-    case 8: return launch_metric_dot<8, Ar, VS, GS>(op, x, y, part, nb, s);
-    }
-    return cudaErrorInvalidValue;
+    if (op.geom == CW_GEOM_RECOMPUTE)
+        return launch_dot_degree_rc<Ar, VS, typename RCStore<Ar>::type, true>(op, x, y, part, nb, s);
+    return launch_dot_degree_rc<Ar, VS, GS, false>(op, x, y, part, nb, s);
 }
 
 template <int N, int CPB, class Ar, class VS>
@@ -187,6 +210,12 @@ cudaError_t launch_variant(const Op &op, const void *x, void *y, cudaStream_t s,
         if constexpr (ALL_VARIANTS)
             if (op.cpb == A) return launch_affine<N, A, Ar, VS>(op, x, y, s);
         return launch_affine<N, D, Ar, VS>(op, x, y, s);
+    }
+    if (op.geom == CW_GEOM_RECOMPUTE) {  // default tile; direct loads or a TMA-staged input tile
+        using GC = typename RCStore<Ar>::type;
+        if constexpr (ALL_VARIANTS)
+            if (op.stage != 0) return launch_metric<N, D, Ar, VS, GC, 2, true>(op, x, y, s, xfuse);
+        return launch_metric<N, D, Ar, VS, GC, 0, true>(op, x, y, s, xfuse);
     }
     if constexpr (ALL_VARIANTS) {
         const bool alt = (op.cpb == A);

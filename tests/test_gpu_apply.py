@@ -49,6 +49,33 @@ def test_apply_metric_f64(cw, orc, p, kind, prec):
     assert rel_err(y, ref) <= TOL64
 
 
+@pytest.mark.parametrize("prec", [0, 1], ids=["df64", "f64native"])
+@pytest.mark.parametrize("kind", [1, 2, 3], ids=["K", "M", "KM"])
+@pytest.mark.parametrize("p", range(1, 8))
+def test_apply_recompute_f64(cw, orc, p, kind, prec):
+    """Metric recomputed at every quadrature point from the cell's trilinear coefficients: the same
+    operator as the oracle's element matrices."""
+    mesh = mesh_for(p)
+    x = orc.gather(mesh, p, synth.global_vector(mesh, p, seed=50 + p))
+    ref = orc.apply_local(mesh, p, kind, x)
+    y = run_apply(cw, mesh, p, kind, cw.CW_GEOM_RECOMPUTE, prec, x)
+    assert rel_err(y, ref) <= TOL64
+
+
+@pytest.mark.parametrize("prec,tol", [(2, 2e-6), (3, 2e-6), (4, 3e-2)], ids=["f32", "f32_bf16g", "bf16"])
+@pytest.mark.parametrize("p", [1, 3, 4, 7])
+def test_apply_recompute_reduced_precision_error(cw, orc, p, prec, tol):
+    """Recomputed geometry in FP32 arithmetic (coefficients stored as floats for every reduced
+    precision): error against the FP64 oracle, bounded by the vector storage precision."""
+    mesh = mesh_for(p)
+    x = orc.gather(mesh, p, synth.global_vector(mesh, p, seed=p))
+    ref = orc.apply_local(mesh, p, 3, x)
+    y = run_apply(cw, mesh, p, 3, cw.CW_GEOM_RECOMPUTE, prec, x)
+    err = rel_err(y, ref)
+    print(f"p={p} prec={prec} rel err {err:.3e}")
+    assert err <= tol
+
+
 @pytest.mark.parametrize("kind", [1, 2, 3], ids=["K", "M", "KM"])
 @pytest.mark.parametrize("p", range(1, 8))
 def test_apply_affine_f64(cw, orc, p, kind):
@@ -74,7 +101,8 @@ CPB_DEFAULT = {1: 32, 2: 16, 3: 8, 4: 8, 5: 4, 6: 4, 7: 2}
 @pytest.mark.parametrize("prec", [0, 1, 2, 4], ids=["df64", "f64native", "f32", "bf16"])
 @pytest.mark.parametrize("dims", [(4, 3, 5), (1, 3, 2), (2, 1, 1), (5, 1, 3), (9, 2, 2)])
 @pytest.mark.parametrize("p", [1, 2, 4, 7])
-def test_assemble_fused_x_matches_axis_passes(cw, p, dims, prec):
+@pytest.mark.parametrize("geom", [1, 2], ids=["stored", "recompute"])
+def test_assemble_fused_x_matches_axis_passes(cw, p, dims, prec, geom):
     """The assembled apply sums the x-interfaces inside each operator tile in the kernel's epilogue
     and leaves the rest to the DSS: bit-identical to a local apply followed by the three axis passes
     of Algorithm struct_dss, for every tile size and staging mode (tiles that straddle x-rows and a
@@ -82,9 +110,11 @@ def test_assemble_fused_x_matches_axis_passes(cw, p, dims, prec):
     import torch
     mesh = synth.box_mesh(*dims, perturb=0.1)
     M = cw.Mesh.from_synth(mesh)
-    op = cw.Operator(M, p, 3, cw.CW_GEOM_METRIC, prec)
+    op = cw.Operator(M, p, 3, geom, prec)
     x = torch.from_numpy(synth.cellwise_random(mesh, p, seed=40 + p)).cuda().to(op.vec_dtype)
     variants = [(0, 0)] if prec == 1 else [(c, st) for c in (CPB_DEFAULT[p], CPB_DEFAULT[p] // 2) for st in (0, 1, 2)]
+    if geom == 2 and prec != 1:  # recomputed geometry: default tile only
+        variants = [(CPB_DEFAULT[p], st) for st in (0, 1, 2)]
     for cpb, stage in variants:
         if cpb:
             op.set_variant(cpb, stage)

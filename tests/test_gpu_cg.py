@@ -92,6 +92,28 @@ def test_iterative_refinement_reaches_fp64_accuracy(cw, orc, mode):
     assert rel_err(to_np(uir), to_np(u64)) <= 1e-8
 
 
+@pytest.mark.parametrize("mode", [0, 1], ids=["f64", "ir_f32"])
+def test_recomputed_geometry_solve(cw, orc, mode):
+    """The solver on an operator whose metric is recomputed at the quadrature points: the first
+    iterates equal the assembled PCG's, and the converged solution equals the stored-metric one."""
+    import torch
+    p = 3
+    mesh = synth.box_mesh(5, 4, 3, perturb=0.15)
+    M, op = make(cw, mesh, p, geom=cw.CW_GEOM_RECOMPUTE)
+    _, op_s = make(cw, mesh, p)
+    b = op.load_vector(which=0)
+    if mode == 0:
+        A = orc.assemble_global(mesh, p, 1)
+        _, _, _, its = orc.pcg_assembled(A, orc.scatter_add(mesh, p, to_np(b)), orc.boundary_mask_global(mesh, p),
+                                         tol=1e-30, maxit=4, record=True)
+        u, st, rc = op.cg_solve(b, rtol=1e-30, maxit=4, mode=mode, check=False)
+        assert rel_err(to_np(u), orc.gather(mesh, p, its[4])) <= 1e-10
+    u, st, _ = op.cg_solve(b, rtol=1e-10, maxit=5000, mode=mode)
+    us, ss, _ = op_s.cg_solve(b, rtol=1e-10, maxit=5000, mode=mode)
+    assert st.rel_residual <= 1e-10 and ss.rel_residual <= 1e-10
+    assert rel_err(to_np(u), to_np(us)) <= 1e-8
+
+
 def test_discretisation_error_matches_oracle(cw, orc):
     import torch
     p = 2
