@@ -464,15 +464,13 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
                         gxz = Ar::norm(Ar::mul(sc, dot3(c0, c2)));
                         gyz = Ar::norm(Ar::mul(sc, dot3(c1, c2)));
                     }
-                } else {
-                    if (HAS_K) {
+                }
+                if (HAS_K) {
+                    if constexpr (!RC) {
                         gxx = Ar::from(g[0 * N3]), gyy = Ar::from(g[1 * N3]);
                         gzz = Ar::from(g[2 * N3]), gxy = Ar::from(g[3 * N3]);
                         gxz = Ar::from(g[4 * N3]), gyz = Ar::from(g[5 * N3]);
                     }
-                    if (HAS_M) cmr = Ar::from(g[(NC - 1) * N3]);
-                }
-                if (HAS_K) {
                     T hx = Ar::mul(gx[k], gxx), hy = Ar::mul(gx[k], gxy), hz = Ar::mul(gx[k], gxz);
                     Ar::mad(hx, gy[k], gxy);
                     Ar::mad(hy, gy[k], gyy);
@@ -490,6 +488,7 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
                     gz[k] = Ar::norm(hz);
                 }
                 if (HAS_M) {
+                    if constexpr (!RC) cmr = Ar::from(g[(NC - 1) * N3]);
                     const T cm = cmr;
                     acc[k] = Ar::norm(Ar::mul(u[k], cm));
                     if constexpr (DOT) df_mad(*dot, Ar::to_df(u[k]), Ar::to_df(acc[k]));  // c u^2
