@@ -64,10 +64,10 @@ def peaks():
 # dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture per variant of a 40^3-cell case
 # (64,000 cells), to be scaled by the cell count of a launch. Variants not listed report null.
 DF64_KM_P4_TRAFFIC_PER_CELL = {
-    (8, 0): (512.082176e6 + 55.454976e6) / 64000,
-    (8, 1): (512.255488e6 + 55.196928e6) / 64000,
-    (8, 2): (512.073472e6 + 55.251712e6) / 64000,
-    (4, 2): (512.071424e6 + 55.187456e6) / 64000,
+    (8, 0): (512.065024e6 + 55.775744e6) / 64000,
+    (8, 1): (512.071424e6 + 55.251200e6) / 64000,
+    (8, 2): (512.166144e6 + 55.302144e6) / 64000,
+    (4, 2): (512.070400e6 + 55.568128e6) / 64000,
 }
 
 # FP32 issue-rate roofline for double-float arithmetic: 152 SMs x 128 FP32 lanes x 2.07 GHz,
@@ -303,7 +303,7 @@ def gpu_arm(args, rank, local, world):
             "unit": "TFLOP/s", "frac": round(achieved_tflops / DF64_PEAK_TFLOPS, 4), "traffic": traffic,
             "traffic_note": "bytes per launch, ncu on a 40^3 case of the same variant scaled by cells (null for "
                             "variants not profiled)",
-            "kernel": f"apply_metric_kernel<N=5, cells/CTA={variant[0]}, staged={variant[1]}, double-float>",
+            "kernel": f"apply_metric_kernel_capped<N=5, cells/CTA={variant[0]}, staged={variant[1]}, double-float>",
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 12 instructions per double-float MAD",
             "hbm": {"achieved": round(by / (kern_ms * 1e-3) / 1e9, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(by / (kern_ms * 1e-3) / 1e9 / hbm, 4), "peak_source": hbm_src}}

@@ -572,11 +572,39 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
     }
 }
 
+// Register caps for the double-float kernels (as CTAs per SM for the launch bounds): stored metric
+// at n = 5 to 72 registers, which it fits without spilling, so that 4 CTAs of 200 threads fit per
+// SM (left alone the allocator takes 78 and loses one); recomputed geometry to 128 (2 CTAs at n = 5
+// instead of 1). Other n keep the plain kernel: larger n spill under a 72 cap, smaller n already fit
+// and ran slower with the hint (a minimum-blocks hint is not neutral, even a hint of 1).
+template <class Ar, int N, bool RC>
+constexpr bool df_capped()
+{
+    return std::is_same<Ar, ArDF>::value && (RC || N == 5);
+}
+template <int THREADS, bool RC>
+constexpr int df_min_blocks()
+{
+    constexpr int warps = (THREADS + 31) / 32;
+    constexpr int b = 65536 / (warps * 32 * (RC ? 128 : 72));
+    return b > 0 ? b : 1;
+}
+
 template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool RC = false>
 __global__ void __launch_bounds__(N *N *CPB) apply_metric_kernel(const VS *__restrict__ x, VS *__restrict__ y,
                                                                   const GS *__restrict__ geo, int64_t ncells,
                                                                   int kind, TabMetric<N, typename Ar::C> tab,
                                                                   int asm_nx)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    metric_tile<N, CPB, Ar, VS, GS, STAGE, false, RC>(x, y, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw, nullptr,
+                                                      asm_nx);
+}
+
+template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool RC = false>
+__global__ void __launch_bounds__(N *N *CPB, (df_min_blocks<N * N * CPB, RC>()))
+    apply_metric_kernel_capped(const VS *__restrict__ x, VS *__restrict__ y, const GS *__restrict__ geo,
+                               int64_t ncells, int kind, TabMetric<N, typename Ar::C> tab, int asm_nx)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     metric_tile<N, CPB, Ar, VS, GS, STAGE, false, RC>(x, y, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw, nullptr,

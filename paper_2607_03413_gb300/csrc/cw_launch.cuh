@@ -111,13 +111,21 @@ static cudaError_t opt_in_smem(K kernel, size_t smem)
 
 // xfuse != nullptr: the kernel also applies the x pass of the DSS inside each tile and *xfuse
 // receives the tile size (cells), so the DSS x pass only has the interfaces between tiles left
+// the plain or the register-capped instantiation (only the one used is compiled)
+template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool RC>
+constexpr auto metric_kernel_ptr()
+{
+    if constexpr (df_capped<Ar, N, RC>()) return apply_metric_kernel_capped<N, CPB, Ar, VS, GS, STAGE, RC>;
+    else return apply_metric_kernel<N, CPB, Ar, VS, GS, STAGE, RC>;
+}
+
 template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool RC = false>
 cudaError_t launch_metric(const Op &op, const void *x, void *y, cudaStream_t s, int *xfuse = nullptr)
 {
     TabMetric<N, typename Ar::C> tab;
     fill_metric_tab<N>(tab, op.tab, [](double v) { return MakeC<Ar>::from(v); });
     const size_t smem = metric_smem_bytes<N, CPB, typename Ar::T, GS>(metric_ncomp(op.kind), STAGE);
-    auto kern = apply_metric_kernel<N, CPB, Ar, VS, GS, STAGE, RC>;
+    auto kern = metric_kernel_ptr<N, CPB, Ar, VS, GS, STAGE, RC>();
     static size_t opted = 0;  // largest size opted in so far for this instantiation
     if (smem > opted) {
         cudaError_t e = opt_in_smem(kern, smem);
