@@ -819,7 +819,7 @@ cw_status cw_op_destroy(cw_op oh)
     for (int i = 0; i < 3; ++i)
         if (op->h_st[i]) cudaStreamDestroy(op->h_st[i]);
     for (int a = 0; a < 2; ++a)
-        for (int k = 0; k < 16; ++k)
+        for (int k = 0; k < Op::kMaxSlabs; ++k)
             if (op->h_ev[a][k]) cudaEventDestroy(op->h_ev[a][k]);
     if (op->h_done) cudaEventDestroy(op->h_done);
     cudaFree(op->d_geo);
@@ -1035,7 +1035,8 @@ cw_status cw_apply_host(cw_op oh, const void *x_host, void *y_host, int flags, v
         CW_CUDA_TRY(cudaMalloc(&op->h_dy, op->L * es));
         for (int i = 0; i < 3; ++i) CW_CUDA_TRY(cudaStreamCreateWithFlags(&op->h_st[i], cudaStreamNonBlocking));
         for (int a = 0; a < 2; ++a)
-            for (int k = 0; k < 16; ++k) CW_CUDA_TRY(cudaEventCreateWithFlags(&op->h_ev[a][k], cudaEventDisableTiming));
+            for (int k = 0; k < Op::kMaxSlabs; ++k)
+                CW_CUDA_TRY(cudaEventCreateWithFlags(&op->h_ev[a][k], cudaEventDisableTiming));
         CW_CUDA_TRY(cudaEventCreateWithFlags(&op->h_done, cudaEventDisableTiming));
         op->owned_bytes += 2 * op->L * (int64_t)es;
     }
@@ -1045,7 +1046,7 @@ cw_status cw_apply_host(cw_op oh, const void *x_host, void *y_host, int flags, v
     for (int i = 0; i < 3; ++i) CW_CUDA_TRY(cudaStreamWaitEvent(op->h_st[i], op->h_done, 0));
     const Mesh &m = *op->mesh;
     const int64_t plane = (int64_t)m.nx * m.ny;  // cells per z-layer
-    const int planes = std::max(1, (m.nz + 15) / 16);  // at most 16 slabs (the event arrays)
+    const int planes = std::max(1, (m.nz + Op::kMaxSlabs - 1) / Op::kMaxSlabs);  // at most kMaxSlabs slabs
     const int nslab = (m.nz + planes - 1) / planes;
     const size_t gbytes_per_cell = op->geo_bytes / op->E;
     unsigned char *dx = static_cast<unsigned char *>(op->h_dx), *dy = static_cast<unsigned char *>(op->h_dy);

@@ -44,6 +44,10 @@ template <>
 struct EOPair<df64> {
     using type = df64p;
 };
+template <>
+struct EOPair<float> {
+    using type = float2;
+};
 
 template <int N, class C>
 struct EOMat {
@@ -144,6 +148,23 @@ __device__ __forceinline__ void contract_eo(const EOMat<N, typename Ar::C> &M, c
             out[a] = Ar::norm(Ar::add(ye, yo));
             const T d = Ar::sub(ye, yo);
             out[N - 1 - a] = Ar::norm(S > 0 ? d : Ar::neg(d));
+        }
+    } else if constexpr (std::is_same<Ar, ArF32>::value) {
+        // FP32: the same pairing with FFMA2 (lane x even, lane y odd)
+        float2 eo[H];
+#pragma unroll
+        for (int b = 0; b < H; ++b) eo[b] = make_float2(e[b], o[b]);
+        float2 xm;
+        if constexpr (N % 2 == 1) xm = make_float2(in[H], in[H]);
+#pragma unroll
+        for (int a = 0; a < H; ++a) {
+            float2 y2 = __fmul2_rn(eo[0], M.P[a][0]);
+#pragma unroll
+            for (int b = 1; b < H; ++b) y2 = __ffma2_rn(eo[b], M.P[a][b], y2);
+            if constexpr (N % 2 == 1) y2 = __ffma2_rn(xm, M.PM[a], y2);
+            out[a] = y2.x + y2.y;
+            const T d = y2.x - y2.y;
+            out[N - 1 - a] = S > 0 ? d : -d;
         }
     } else {
 #pragma unroll

@@ -48,7 +48,8 @@ struct Op {
     // host-buffer apply (cw_apply_host): device staging vectors, streams and events, lazily
     void *h_dx = nullptr, *h_dy = nullptr;
     cudaStream_t h_st[3] = {nullptr, nullptr, nullptr};
-    cudaEvent_t h_ev[2][16] = {};
+    static constexpr int kMaxSlabs = 16;  // 32 measured slower (more, smaller copies)
+    cudaEvent_t h_ev[2][kMaxSlabs] = {};
     cudaEvent_t h_done = nullptr;
     int cpb = 0;          // apply kernel variant: cells per CTA (0 = default for the degree)
     int stage = 1;        // apply kernel variant: TMA staging of the input and metric tiles

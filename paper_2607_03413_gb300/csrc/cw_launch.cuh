@@ -66,6 +66,14 @@ void fill_metric_tab(TabMetric<N, C> &t, const Tables1D &tb, MK mk)
                 for (int b = 0; b < (H > 0 ? H : 1); ++b) E.P[a][b] = pair(E.E[a][b], E.O[a][b]);
                 E.PM[a] = pair(E.Mid[a], df64{0.0f, 0.0f});
             }
+            if constexpr (std::is_same<C, float>::value) {
+                for (int b = 0; b < (H > 0 ? H : 1); ++b) {
+                    E.P[a][b].x = E.E[a][b];
+                    E.P[a][b].y = E.O[a][b];
+                }
+                E.PM[a].x = E.Mid[a];
+                E.PM[a].y = 0.0f;
+            }
         }
     };
     eo(t.Bf, B);
