@@ -367,7 +367,7 @@ __global__ void scale_by_valence_kernel(VS *__restrict__ v, int nx, int ny, int 
     const int loc = (int)(t - e * n3), i = loc % n, j = (loc / n) % n, k = loc / (n * n);
     const int64_t cx = e % nx, cy = (e / nx) % ny, cz = e / ((int64_t)nx * ny);
     const int val = node_valence(cx, cy, cz, i, j, k, p, nx, ny, nz);
-    if (val > 1) v[t] = MulOp<VS>::mul(v[t], 1.0 / val);
+    if (val > 1) v[t] = MulOp<VS>::mul(v[t], val == 2 ? 0.5 : (val == 4 ? 0.25 : 0.125));  // exact 1/val
 }
 
 // dst = src with the x pass of Algorithm struct_dss applied: an entry on an interior x-face adds its

@@ -159,7 +159,9 @@ __device__ __forceinline__ void precond_one(V &r, V &w, V d, uint8_t kap, df64 &
 {
     const V wi = w;
     const V zi = d * wi;
-    const V ri = wi / V(kap);
+    // kappa is 1, 2, 4 or 8: multiplying by its reciprocal is exact and bit-identical to dividing,
+    // and keeps the FP64 divide sequence (dozens of slow-pipe FP64 operations) out of the pass
+    const V ri = wi * V(kap == 1 ? 1.0f : (kap == 2 ? 0.5f : (kap == 4 ? 0.25f : 0.125f)));
     w = zi;
     r = ri;
     df_mad(a1, as_df(ri), as_df(zi));
