@@ -145,9 +145,11 @@ __device__ __forceinline__ void contract_eo(const EOMat<N, typename Ar::C> &M, c
             for (int b = 1; b < H; ++b) dfp_mad(y2, eo[b], M.P[a][b]);
             if constexpr (N % 2 == 1) dfp_mad(y2, xm, M.PM[a]);
             const T ye = dfp_x(y2), yo = dfp_y(y2);
-            out[a] = Ar::norm(Ar::add(ye, yo));
+            // outputs left unnormalised (|lo| within a few ulp of hi): every consumer is a
+            // double-float operation or the final conversion, which take that form as it is
+            out[a] = Ar::add(ye, yo);
             const T d = Ar::sub(ye, yo);
-            out[N - 1 - a] = Ar::norm(S > 0 ? d : Ar::neg(d));
+            out[N - 1 - a] = S > 0 ? d : Ar::neg(d);
         }
     } else if constexpr (std::is_same<Ar, ArF32>::value) {
         // FP32: the same pairing with FFMA2 (lane x even, lane y odd)
@@ -186,12 +188,12 @@ __device__ __forceinline__ void contract_eo(const EOMat<N, typename Ar::C> &M, c
             T ye = Ar::mul(in[H], M.Mid[H]);
 #pragma unroll
             for (int b = 0; b < H; ++b) Ar::mad(ye, e[b], M.E[H][b]);
-            out[H] = Ar::norm(ye);
+            out[H] = ye;
         } else {
             T yo = Ar::mul(o[0], M.O[H][0]);
 #pragma unroll
             for (int b = 1; b < H; ++b) Ar::mad(yo, o[b], M.O[H][b]);
-            out[H] = Ar::norm(yo);
+            out[H] = yo;
         }
     }
 }
@@ -504,14 +506,14 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
                         df_mad(*dot, Ar::to_df(gy[k]), Ar::to_df(hy));
                         df_mad(*dot, Ar::to_df(gz[k]), Ar::to_df(hz));
                     }
-                    gx[k] = Ar::norm(hx);
-                    gy[k] = Ar::norm(hy);
-                    gz[k] = Ar::norm(hz);
+                    gx[k] = hx;  // unnormalised, as the contraction outputs
+                    gy[k] = hy;
+                    gz[k] = hz;
                 }
                 if (HAS_M) {
                     if constexpr (!RC) cmr = Ar::from(g[(NC - 1) * N3]);
                     const T cm = cmr;
-                    acc[k] = Ar::norm(Ar::mul(u[k], cm));
+                    acc[k] = Ar::mul(u[k], cm);
                     if constexpr (DOT) df_mad(*dot, Ar::to_df(u[k]), Ar::to_df(acc[k]));  // c u^2
                 }
             }
@@ -539,7 +541,7 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
                 CW_LDZ(s1, v);
                 CW_LDZ(s2, w);
 #pragma unroll
-                for (int k = 0; k < N; ++k) acc[k] = Ar::norm(Ar::add(acc[k], Ar::add(v[k], w[k])));
+                for (int k = 0; k < N; ++k) acc[k] = Ar::add(acc[k], Ar::add(v[k], w[k]));
             }
         }
         // (5) integrate back: B^T along z (registers), y and x as line owners
