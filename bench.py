@@ -361,6 +361,31 @@ def gpu_arm(args, rank, local, world):
     if recomp:
         out["recomputed_metric"] = recomp
 
+    # the small Cartesian case (Q2, 8^3 affine cells, Laplace, FP64): latency per call, LOCAL and
+    # ASSEMBLE, back-to-back calls on one stream
+    if args.mixed:
+        m8 = synth.box_mesh(8)
+        M8 = cw.Mesh.from_synth(m8)
+        o = cw.Operator(M8, 2, cw.CW_LAPLACE, cw.CW_GEOM_AFFINE, cw.CW_PREC_F64)
+        xx = o.gather(torch.from_numpy(synth.global_vector(m8, 2, seed=0)).cuda())
+        yy = o.empty()
+        lat = {}
+        for name, fl in (("local_us", cw.CW_APPLY_LOCAL), ("assemble_us", cw.CW_APPLY_ASSEMBLE)):
+            for _ in range(20):
+                cw.cw_apply(o.handle, xx, yy, fl, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            a, b = event_pair()
+            a.record(stream)
+            for _ in range(200):
+                cw.cw_apply(o.handle, xx, yy, fl, stream=stream.cuda_stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            lat[name] = round(a.elapsed_time(b) / 200 * 1e3, 2)
+        out["small_affine"] = {"workload": "Laplace apply, Q2, 8^3 Cartesian cells, FP64, 13,824 cell-wise values",
+                               **lat}
+        o.close()
+        M8.close()
+
     if args.sweep:
         out["sweep"] = degree_sweep(cw, stream, hbm, args)
     if args.cg:
