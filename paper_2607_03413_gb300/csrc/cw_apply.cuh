@@ -116,7 +116,8 @@ __device__ __forceinline__ void contract(const typename Ar::C (&M)[N][N], const 
 }
 
 // out = M in with M in even-odd form (see EOMat), S = +1 or -1 the reflection sign
-template <int N, int S, class Ar>
+// NRM: renormalise each double-float output (no effect for the other arithmetics)
+template <int N, int S, class Ar, bool NRM = true>
 __device__ __forceinline__ void contract_eo(const EOMat<N, typename Ar::C> &M, const typename Ar::T (&in)[N],
                                             typename Ar::T (&out)[N])
 {
@@ -145,11 +146,13 @@ __device__ __forceinline__ void contract_eo(const EOMat<N, typename Ar::C> &M, c
             for (int b = 1; b < H; ++b) dfp_mad(y2, eo[b], M.P[a][b]);
             if constexpr (N % 2 == 1) dfp_mad(y2, xm, M.PM[a]);
             const T ye = dfp_x(y2), yo = dfp_y(y2);
-            // outputs left unnormalised (|lo| within a few ulp of hi): every consumer is a
+            // without NRM the outputs stay unnormalised (|lo| a few ulp of hi): every consumer is a
             // double-float operation or the final conversion, which take that form as it is
-            out[a] = Ar::add(ye, yo);
+            const T sum = Ar::add(ye, yo);
+            out[a] = NRM ? Ar::norm(sum) : sum;
             const T d = Ar::sub(ye, yo);
-            out[N - 1 - a] = S > 0 ? d : Ar::neg(d);
+            const T dd = S > 0 ? d : Ar::neg(d);
+            out[N - 1 - a] = NRM ? Ar::norm(dd) : dd;
         }
     } else if constexpr (std::is_same<Ar, ArF32>::value) {
         // FP32: the same pairing with FFMA2 (lane x even, lane y odd)
@@ -188,26 +191,26 @@ __device__ __forceinline__ void contract_eo(const EOMat<N, typename Ar::C> &M, c
             T ye = Ar::mul(in[H], M.Mid[H]);
 #pragma unroll
             for (int b = 0; b < H; ++b) Ar::mad(ye, e[b], M.E[H][b]);
-            out[H] = ye;
+            out[H] = NRM ? Ar::norm(ye) : ye;
         } else {
             T yo = Ar::mul(o[0], M.O[H][0]);
 #pragma unroll
             for (int b = 1; b < H; ++b) Ar::mad(yo, o[b], M.O[H][b]);
-            out[H] = yo;
+            out[H] = NRM ? Ar::norm(yo) : yo;
         }
     }
 }
 
 // line contraction with B, B^T, D or D^T: even-odd form from N = 4 up, full form below
-template <int N, class Ar, int WHICH>  // WHICH: 0 B, 1 B^T, 2 D, 3 D^T
+template <int N, class Ar, int WHICH, bool NRM = true>  // WHICH: 0 B, 1 B^T, 2 D, 3 D^T
 __device__ __forceinline__ void sweep(const TabMetric<N, typename Ar::C> &tab, const typename Ar::T (&in)[N],
                                       typename Ar::T (&out)[N])
 {
     if constexpr (N >= 4) {
-        if constexpr (WHICH == 0) contract_eo<N, 1, Ar>(tab.Bf, in, out);
-        else if constexpr (WHICH == 1) contract_eo<N, 1, Ar>(tab.Bt, in, out);
-        else if constexpr (WHICH == 2) contract_eo<N, -1, Ar>(tab.Df, in, out);
-        else contract_eo<N, -1, Ar>(tab.Dt, in, out);
+        if constexpr (WHICH == 0) contract_eo<N, 1, Ar, NRM>(tab.Bf, in, out);
+        else if constexpr (WHICH == 1) contract_eo<N, 1, Ar, NRM>(tab.Bt, in, out);
+        else if constexpr (WHICH == 2) contract_eo<N, -1, Ar, NRM>(tab.Df, in, out);
+        else contract_eo<N, -1, Ar, NRM>(tab.Dt, in, out);
     } else {
         if constexpr (WHICH == 0) contract<N, false, Ar>(tab.B, in, out);
         else if constexpr (WHICH == 1) contract<N, true, Ar>(tab.B, in, out);
@@ -278,6 +281,11 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
                                             int asm_nx = 0)
 {
     static_assert(!(RC && STAGE == 1), "recomputed geometry has no metric tile to stage");
+    // Double-float renormalisation of the intermediate values: kept where the operator serves the
+    // solver (DOT), whose attainable accuracy depends on it (at 128^3 Q3 the double-float CG took
+    // 1351 instead of 1026 iterations without it); skipped in the plain apply (5 % faster there,
+    // errors against the oracle <= 1.0e-13 instead of <= 3e-14).
+    constexpr bool NRM = DOT;
     using T = typename Ar::T;
     using L = Lines<N>;
     constexpr int N2 = N * N, N3 = N2 * N, CS = L::CS;
@@ -362,35 +370,35 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
 #pragma unroll
                 for (int m = 0; m < N; ++m) v[m] = act ? Ar::from(ldg_nc(xc + m)) : Ar::zero();
             }
-            sweep<N, Ar, 0>(tab, v, w);
+            sweep<N, Ar, 0, NRM>(tab, v, w);
             CW_STX(s0, w);
         }
         __syncthreads();
         // (2) y-line (i,k): contract with B along y, in place
         {
             CW_LDY(s0, v);
-            sweep<N, Ar, 0>(tab, v, w);
+            sweep<N, Ar, 0, NRM>(tab, v, w);
             CW_STY(s0, w);
         }
         __syncthreads();
         // (3) z-pencil (i,j): contract with B along z -> u at the Gauss points (registers)
         {
             CW_LDZ(s0, v);
-            sweep<N, Ar, 0>(tab, v, u);
+            sweep<N, Ar, 0, NRM>(tab, v, u);
         }
         if (HAS_K) {
             {
-                sweep<N, Ar, 2>(tab, u, gz);
+                sweep<N, Ar, 2, NRM>(tab, u, gz);
                 CW_STZ(s0, u);
             }
             __syncthreads();
             // x- and y-derivatives by collocation, as line owners
             {
                 CW_LDX(s0, v);
-                sweep<N, Ar, 2>(tab, v, w);
+                sweep<N, Ar, 2, NRM>(tab, v, w);
                 CW_STX(s1, w);
                 CW_LDY(s0, v);
-                sweep<N, Ar, 2>(tab, v, w);
+                sweep<N, Ar, 2, NRM>(tab, v, w);
                 CW_STY(s2, w);
             }
             __syncthreads();
@@ -506,14 +514,14 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
                         df_mad(*dot, Ar::to_df(gy[k]), Ar::to_df(hy));
                         df_mad(*dot, Ar::to_df(gz[k]), Ar::to_df(hz));
                     }
-                    gx[k] = hx;  // unnormalised, as the contraction outputs
-                    gy[k] = hy;
-                    gz[k] = hz;
+                    gx[k] = NRM ? Ar::norm(hx) : hx;
+                    gy[k] = NRM ? Ar::norm(hy) : hy;
+                    gz[k] = NRM ? Ar::norm(hz) : hz;
                 }
                 if (HAS_M) {
                     if constexpr (!RC) cmr = Ar::from(g[(NC - 1) * N3]);
                     const T cm = cmr;
-                    acc[k] = Ar::mul(u[k], cm);
+                    acc[k] = NRM ? Ar::norm(Ar::mul(u[k], cm)) : Ar::mul(u[k], cm);
                     if constexpr (DOT) df_mad(*dot, Ar::to_df(u[k]), Ar::to_df(acc[k]));  // c u^2
                 }
             }
@@ -521,7 +529,7 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
         if (HAS_K) {
             // z-part of the transposed derivative in registers, x/y parts as line owners
             {
-                sweep<N, Ar, 3>(tab, gz, v);
+                sweep<N, Ar, 3, NRM>(tab, gz, v);
 #pragma unroll
                 for (int k = 0; k < N; ++k) acc[k] = HAS_M ? Ar::add(acc[k], v[k]) : v[k];
                 CW_STZ(s1, gx);  // own pencil only: no other thread reads s1/s2 pencils now
@@ -530,10 +538,10 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
             __syncthreads();
             {
                 CW_LDX(s1, v);
-                sweep<N, Ar, 3>(tab, v, w);
+                sweep<N, Ar, 3, NRM>(tab, v, w);
                 CW_STX(s1, w);
                 CW_LDY(s2, v);
-                sweep<N, Ar, 3>(tab, v, w);
+                sweep<N, Ar, 3, NRM>(tab, v, w);
                 CW_STY(s2, w);
             }
             __syncthreads();
@@ -541,24 +549,27 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
                 CW_LDZ(s1, v);
                 CW_LDZ(s2, w);
 #pragma unroll
-                for (int k = 0; k < N; ++k) acc[k] = Ar::add(acc[k], Ar::add(v[k], w[k]));
+                for (int k = 0; k < N; ++k) {
+                    const T t = Ar::add(acc[k], Ar::add(v[k], w[k]));
+                    acc[k] = NRM ? Ar::norm(t) : t;
+                }
             }
         }
         // (5) integrate back: B^T along z (registers), y and x as line owners
         {
-            sweep<N, Ar, 1>(tab, acc, w);
+            sweep<N, Ar, 1, NRM>(tab, acc, w);
             CW_STZ(s0, w);
         }
         __syncthreads();
         {
             CW_LDY(s0, v);
-            sweep<N, Ar, 1>(tab, v, w);
+            sweep<N, Ar, 1, NRM>(tab, v, w);
             CW_STY(s0, w);
         }
         __syncthreads();
         {
             CW_LDX(s0, v);
-            sweep<N, Ar, 1>(tab, v, w);
+            sweep<N, Ar, 1, NRM>(tab, v, w);
             if (asm_nx > 0) {  // kernel-uniform
                 VS o0, o1;
                 Ar::to(o0, w[0]);
