@@ -361,6 +361,21 @@ def gpu_arm(args, rank, local, world):
     if recomp:
         out["recomputed_metric"] = recomp
 
+    # the other operator kinds of the same workload (FP64, double-float): stored and recomputed metric
+    kinds = {}
+    for kname, kind in ((("laplace", cw.CW_LAPLACE), ("mass", cw.CW_MASS)) if args.mixed else ()):
+        kinds[kname] = {}
+        for gname, geom in (("stored", cw.CW_GEOM_METRIC), ("recomputed", cw.CW_GEOM_RECOMPUTE)):
+            o = cw.Operator(M, P, kind, geom, cw.CW_PREC_F64)
+            xx = o.gather(ug)
+            yy = o.empty()
+            o.autotune(xx, yy, reps=3)
+            sm, km = time_apply(cw, o, xx, yy, args.steps, args.warmup, stream)
+            kinds[kname][gname] = {"dofs_per_s": o.L / (sm * 1e-3), "ms_per_step": sm, "apply_kernel_ms": km}
+            o.close()
+    if kinds:
+        out["kinds_f64"] = kinds
+
     # the small Cartesian case (Q2, 8^3 affine cells, Laplace, FP64): latency per call, LOCAL and
     # ASSEMBLE, back-to-back calls on one stream
     if args.mixed:
@@ -578,6 +593,24 @@ def reference_arm(args, rank, world):
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def oracle_cg_time(n=16, p=3):
+    """The oracle's assembled Jacobi-PCG (scipy sparse, host cores) on the Poisson problem at the
+    largest mesh it solves in a few seconds: the same method as the GPU solve, 16^3 curved cells Q3."""
+    import oracle as orc
+    orc.build()
+    orc.lib()
+    mesh = synth.box_mesh(n, perturb=0.1)
+    t0 = time.perf_counter()
+    b = orc.load_vector(mesh, p, orc.PROBLEM_SINE)
+    A = orc.assemble_global(mesh, p, 1)
+    t1 = time.perf_counter()
+    _, its, rel, _ = orc.pcg_assembled(A, orc.scatter_add(mesh, p, b), orc.boundary_mask_global(mesh, p), tol=1e-10)
+    t2 = time.perf_counter()
+    return {"workload": f"Poisson Q{p}, {n}^3 curved cells, assembled Jacobi-PCG to 1e-10",
+            "assembly_s": round(t1 - t0, 3), "solve_s": round(t2 - t1, 3), "iterations": its,
+            "rel_residual": rel}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -605,15 +638,14 @@ def main():
             print(json.dumps(out))
         return
     rank, local, world = dist_init(args)
-    if False:
-        pass
-    else:
-        out = gpu_arm(args, rank, local, world)
-        if rank == 0 and world == 1 and args.cpu:
-            rate, ncell, dt = oracle_sample_rate(args.cpu_seconds)
-            out["cpu_baseline"] = {"value": rate, "unit": "DoF/s", "cores": cores(), "kind": "oracle",
-                                   "sample": f"{ncell} random cells of the 64^3 curved mesh, K+M p=4, "
-                                             f"element matrices built and applied per cell ({dt:.1f} s)"}
+    out = gpu_arm(args, rank, local, world)
+    if rank == 0 and world == 1 and args.cpu:
+        rate, ncell, dt = oracle_sample_rate(args.cpu_seconds)
+        out["cpu_baseline"] = {"value": rate, "unit": "DoF/s", "cores": cores(), "kind": "oracle",
+                               "sample": f"{ncell} random cells of the 64^3 curved mesh, K+M p=4, "
+                                         f"element matrices built and applied per cell ({dt:.1f} s)"}
+        if args.cg:
+            out["cpu_baseline"]["cg"] = oracle_cg_time()
     if rank == 0 and out is not None:
         print(json.dumps(out))
     if world > 1:
