@@ -21,6 +21,21 @@ def lib():
     return ctypes.CDLL(build.LIB)
 
 
+def declared_constants():
+    src = open(os.path.join(ROOT, "include", "cwfem.h")).read()
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"^#define (CW_[A-Z0-9_]+) (\d+)", src, re.M)}
+    consts.update({m.group(1): int(m.group(2)) for m in re.finditer(r"^\s+(CW_[A-Z_]+) = (\d+)", src, re.M)})
+    return consts
+
+
+def test_binding_constants_match_the_header():
+    import paper_2607_03413_gb300 as pkg
+    consts = declared_constants()
+    assert len(consts) >= 30
+    for name, value in consts.items():
+        assert getattr(pkg, name) == value, name
+
+
 def test_header_declares_the_binding_names():
     import paper_2607_03413_gb300 as pkg
     assert declared_functions() == sorted(pkg.EXPORTED)
