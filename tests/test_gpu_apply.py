@@ -228,15 +228,16 @@ def test_autotune_keeps_a_valid_variant(cw, orc):
     assert rel_err(to_np(y2), ref) <= TOL64
 
 
+@pytest.mark.parametrize("geom", [1, 2], ids=["stored", "recompute"])
 @pytest.mark.parametrize("assemble", [False, True])
 @pytest.mark.parametrize("prec", [0, 2], ids=["df64", "f32"])
-def test_apply_host_buffers(cw, orc, prec, assemble):
+def test_apply_host_buffers(cw, orc, prec, assemble, geom):
     """cw_apply_host (host input and output, chunked and pipelined) equals cw_apply on device data."""
     import torch
     p = 3
-    mesh = synth.box_mesh(5, 4, 19, perturb=0.2)  # 19 z-layers: slabs of 3 layers and a ragged last one
+    mesh = synth.box_mesh(5, 4, 19, perturb=0.2)  # 19 z-layers: slabs of 2 layers and a ragged last one
     M = cw.Mesh.from_synth(mesh)
-    op = cw.Operator(M, p, 3, cw.CW_GEOM_METRIC, prec)
+    op = cw.Operator(M, p, 3, geom, prec)
     x = op.gather(torch.from_numpy(synth.global_vector(mesh, p, seed=3)).cuda())
     ref = op.apply(x, assemble=assemble)
     xh = x.cpu().pin_memory()
