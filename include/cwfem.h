@@ -160,7 +160,12 @@ cw_status cw_gather(cw_op op, const double *u_global, void *x, void *stream);
 
 /*
  * y = A x (flags = CW_APPLY_LOCAL) or y = S A x (CW_APPLY_ASSEMBLE). x primal, y dual;
- * both cell-wise device arrays of the op's vector type; x and y must not alias.
+ * both cell-wise device arrays of the op's vector type; x and y must not alias (CW_ERR_ARG).
+ * Sec. 2.1 (matrix-free evaluation of the element integrals) and, for ASSEMBLE, Algorithm
+ * struct_dss: for curved cells the operator kernel already sums the x-interfaces between the cells
+ * of each of its tiles (same sums as the DSS x pass, bit-identical result); the x pass between
+ * tiles and the y and z passes follow on `stream`. Asynchronous; errors of the launch are returned,
+ * device faults surface at the next synchronisation.
  */
 cw_status cw_apply(cw_op op, const void *x, void *y, int flags, void *stream);
 
