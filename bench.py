@@ -12,7 +12,8 @@ time-to-1e-10 (plain FP64 Jacobi-PCG vs FP64 iterative refinement around an FP32
 the batched apply (16 RHS on Q5 64^3 + 48 uneven problems in one persistent launch).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-sweep] [--no-cg]
-                  [--no-batched] [--no-mixed] [--no-e2e] [--no-cpu] [--no-tune] [--variant C,S] [--cells N] [--prec P]
+                  [--no-batched] [--no-mixed] [--no-e2e] [--no-cpu] [--no-tune] [--variant C,S] [--cg-mode M]
+                  [--cells N] [--prec P]
 
 --impl reference times the FP64 CPU oracle (explicit element matrices) on a bounded cell sample of
 the same workload on the host cores.
@@ -524,6 +525,8 @@ def cg_bench(cw, args):
            "unit": "s"}
     names = [("ir_f32", cw.CW_CG_IR_F32), ("ir_bf16_metric", cw.CW_CG_IR_BF16), ("f64_doublefloat", cw.CW_CG_F64),
              ("f64_native", cw.CW_CG_F64_NATIVE)]
+    if args.cg_mode >= 0:  # one mode only (profiling cases)
+        names = [nm for nm in names if nm[1] == args.cg_mode]
     for name, mode in names:
         op.cg_solve(b, u, rtol=1e-3, maxit=200, mode=mode, check=False)  # warm-up: allocations, graphs
         torch.cuda.synchronize()
@@ -531,8 +534,9 @@ def cg_bench(cw, args):
         res[name] = {"seconds": st.seconds, "iterations": st.iterations, "outer": st.outer_iterations,
                      "rel_residual": st.rel_residual, "status": int(rc),
                      "ms_per_iteration": 1e3 * st.seconds / max(1, st.iterations)}
-    res["speedup_ir_f32_vs_f64_native"] = res["f64_native"]["seconds"] / res["ir_f32"]["seconds"]
-    res["speedup_ir_f32_vs_f64_doublefloat"] = res["f64_doublefloat"]["seconds"] / res["ir_f32"]["seconds"]
+    if len(names) == 4:
+        res["speedup_ir_f32_vs_f64_native"] = res["f64_native"]["seconds"] / res["ir_f32"]["seconds"]
+        res["speedup_ir_f32_vs_f64_doublefloat"] = res["f64_doublefloat"]["seconds"] / res["ir_f32"]["seconds"]
     op.close()
     M.close()
     return res
@@ -625,6 +629,7 @@ def main():
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
     ap.add_argument("--no-tune", dest="tune", action="store_false", help="default kernel variant, no autotuning")
     ap.add_argument("--variant", default="", help="cells_per_cta,stage of the main step's kernel (profiling cases)")
+    ap.add_argument("--cg-mode", type=int, default=-1, help="CW_CG_* mode: time this solver mode only (profiling cases)")
     ap.add_argument("--cells", type=int, default=NCELL, help="cells per direction (profiling cases)")
     ap.add_argument("--prec", type=int, default=0, help="CW_PREC_* of the main step (profiling cases)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
