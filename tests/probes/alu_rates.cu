@@ -75,6 +75,20 @@ __global__ void k_df(float *out, float bh, float bl)
     out[blockIdx.x * blockDim.x + threadIdx.x] = s[0].h + s[1].h + s[2].h + s[3].h + s[0].l + s[1].l + s[2].l + s[3].l;
 }
 
+// FP64 -> (hi, lo) float pair with conversion instructions (F2F, on the FP64 pipe) and a DADD
+__global__ void k_split(float *out, const double *in)
+{
+    double v = in[threadIdx.x];  // in holds blockDim.x values
+    float acc = 0.0f;
+    for (int it = 0; it < kIters / 16; ++it) {
+        const float h = (float)v;
+        const float l = (float)(v - (double)h);
+        acc += h + l;
+        v += 1e-9;
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
 static float timed(void (*launch)(void), cudaEvent_t a, cudaEvent_t b)
 {
     launch();  // warm-up
@@ -89,7 +103,7 @@ static float timed(void (*launch)(void), cudaEvent_t a, cudaEvent_t b)
 
 static int g_blocks, g_threads;
 static float *g_o32;
-static double *g_o64;
+static double *g_o64, *g_in;
 
 int main()
 {
@@ -100,6 +114,8 @@ int main()
     const double n = (double)g_blocks * g_threads;
     if (cudaMalloc(&g_o32, (size_t)n * sizeof(float)) != cudaSuccess) return 1;
     if (cudaMalloc(&g_o64, (size_t)n * sizeof(double)) != cudaSuccess) return 1;
+    if (cudaMalloc(&g_in, g_threads * sizeof(double)) != cudaSuccess) return 1;
+    cudaMemset(g_in, 0, g_threads * sizeof(double));
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
@@ -107,11 +123,13 @@ int main()
     const float t32x2 = timed([] { k_f32x2<<<g_blocks, g_threads>>>(g_o32, 1.0001f, 0.5f); }, a, b);
     const float t64 = timed([] { k_f64<<<g_blocks, g_threads>>>(g_o64, 1.0001, 0.5); }, a, b);
     const float tdf = timed([] { k_df<<<g_blocks, g_threads>>>(g_o32, 1.0001f, 1e-9f); }, a, b);
+    const float tsp = timed([] { k_split<<<g_blocks, g_threads>>>(g_o32, g_in); }, a, b);
     printf("SMs %d\n", nsm);
     printf("fp32_fma_tflops %.2f\n", 2.0 * 8 * kIters * n / t32 / 1e9);
     printf("fp32_ffma2_tflops %.2f\n", 2.0 * 8 * kIters * n / t32x2 / 1e9);
     printf("fp64_dfma_tflops %.3f\n", 2.0 * 8 * (kIters / 16) * n / t64 / 1e9);
     printf("df64_mad_tper_s %.3f\n", 4.0 * (kIters / 8) * n / tdf / 1e9);
+    printf("f2f_split_gper_s %.1f\n", 1.0 * (kIters / 16) * n / tsp / 1e6);
     const cudaError_t e = cudaGetLastError();
     printf("status %s\n", cudaGetErrorString(e));
     return e == cudaSuccess ? 0 : 1;
