@@ -29,7 +29,11 @@ cw_status fail(cw_status st, const std::string &msg)
 cw_status cuda_fail(cudaError_t e, const char *where)
 {
     set_error(std::string(where) + ": " + cudaGetErrorString(e));
-    return e == cudaErrorMemoryAllocation ? CW_ERR_OOM : CW_ERR_CUDA;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();  // not sticky: clear it, or the next launch check would report it again
+        return CW_ERR_OOM;
+    }
+    return CW_ERR_CUDA;
 }
 
 size_t vec_elem_size(int prec)

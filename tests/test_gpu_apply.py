@@ -246,3 +246,16 @@ def test_apply_host_buffers(cw, orc, prec, assemble, geom):
         cw.cw_apply_host(op.handle, xh, yh, cw.CW_APPLY_ASSEMBLE if assemble else cw.CW_APPLY_LOCAL)
         torch.cuda.synchronize()
         assert torch.equal(yh, ref.cpu())
+
+
+def test_create_reports_device_oom(cw):
+    """An operator whose metric cannot fit in device memory (p=7, K+M, 240^3 cells: 396 GB of
+    FP64 metric) fails with CW_ERR_OOM from cw_op_create, and the library stays usable."""
+    mesh = synth.box_mesh(240)
+    M = cw.Mesh.from_synth(mesh)
+    with pytest.raises(cw.CwError) as ei:
+        cw.Operator(M, 7, cw.CW_LAPLACE_MASS, cw.CW_GEOM_METRIC, cw.CW_PREC_F64)
+    assert ei.value.status == cw.CW_ERR_OOM
+    small = synth.box_mesh(2, 2, 2, perturb=0.1)
+    op = cw.Operator(cw.Mesh.from_synth(small), 2, 1, cw.CW_GEOM_METRIC, cw.CW_PREC_F64)
+    assert op.L == 8 * 27
