@@ -476,7 +476,7 @@ struct LineIO<4, float> {
 template <int N, class V>
 __global__ void __launch_bounds__(kRedThreads) k_precond_yz_fin(
     const V *__restrict__ w, V *__restrict__ r, V *__restrict__ zo, const V *__restrict__ dinv,
-    const uint8_t *__restrict__ kappa, uint32_t nlines, int nx, int ny, int nz, FastDiv fd_nx, FastDiv fd_ny,
+    uint32_t nlines, int nx, int ny, int nz, FastDiv fd_nx, FastDiv fd_ny,
     double *__restrict__ part, double *__restrict__ scal, int *__restrict__ flags, int stage)
 {
     if (stage == STAGE_RHO && flags[F_DONE]) return;  // an iteration after convergence
@@ -489,8 +489,12 @@ __global__ void __launch_bounds__(kRedThreads) k_precond_yz_fin(
         const int rl = static_cast<int>(l - e * N2), j = rl % N, k = rl / N;
         const uint32_t q = fd_nx.div(e), cz = fd_ny.div(q);
         const int cy = static_cast<int>(q - cz * static_cast<uint32_t>(ny));
+        const int cx = static_cast<int>(e - q * static_cast<uint32_t>(nx));
         const int oy = (j == 0 && cy > 0) ? -(sx - P * N) : ((j == P && cy < ny - 1) ? (sx - P * N) : 0);
         const int oz = (k == 0 && cz > 0) ? -(sxy - P * N2) : ((k == P && (int)cz < nz - 1) ? (sxy - P * N2) : 0);
+        // valences of the line's entries from the same neighbour tests (no valence array read)
+        const int kyz = (oy ? 2 : 1) * (oz ? 2 : 1);
+        const int k0 = kyz * (cx > 0 ? 2 : 1), kp = kyz * (cx < nx - 1 ? 2 : 1);
         const V *b = w + static_cast<size_t>(l) * N;
         V sv[N], t[N];
         IO::ld(b, sv);
@@ -514,7 +518,8 @@ __global__ void __launch_bounds__(kRedThreads) k_precond_yz_fin(
         V dv[N], rv[N];
         IO::ld(dinv + o, dv);
 #pragma unroll
-        for (int m = 0; m < N; ++m) precond_one(rv[m], sv[m], dv[m], kappa[o + m], a1, a2);
+        for (int m = 0; m < N; ++m)
+            precond_one(rv[m], sv[m], dv[m], static_cast<uint8_t>(m == 0 ? k0 : (m == P ? kp : kyz)), a1, a2);
         IO::st(r + o, rv);
         IO::st(zo + o, sv);
     }
@@ -524,14 +529,14 @@ __global__ void __launch_bounds__(kRedThreads) k_precond_yz_fin(
 }
 
 template <class V>
-static cudaError_t launch_precond_yz(const Op &op, const V *w, V *r, V *zo, const V *dinv, const uint8_t *kappa,
-                                     double *part, double *scal, int *flags, int stage, cudaStream_t s)
+static cudaError_t launch_precond_yz(const Op &op, const V *w, V *r, V *zo, const V *dinv, double *part,
+                                     double *scal, int *flags, int stage, cudaStream_t s)
 {
     const Mesh &m = *op.mesh;
     const uint32_t nl = static_cast<uint32_t>(op.L / op.n);
     const FastDiv fx = FastDiv::make(m.nx), fy = FastDiv::make(m.ny);
 #define CW_PYZ(NN)                                                                                     \
-    k_precond_yz_fin<NN, V><<<kRedBlocks, kRedThreads, 0, s>>>(w, r, zo, dinv, kappa, nl, m.nx, m.ny, m.nz, fx, fy, \
+    k_precond_yz_fin<NN, V><<<kRedBlocks, kRedThreads, 0, s>>>(w, r, zo, dinv, nl, m.nx, m.ny, m.nz, fx, fy, \
                                                               part, scal, flags, stage)
     switch (op.n) {
     case 2: CW_PYZ(2); break;
@@ -661,7 +666,7 @@ static cudaError_t cg_iteration(const Op &aop, int ak, CgLevel &lv, U *u, CgScra
             // pass has read it)
             e = dss_from_axpy(aop, r, q, c.scal + S_ALPHA, c.flags + F_ACTIVE, z, s, true);
             if (e != cudaSuccess) return e;
-            e = launch_precond_yz<V>(aop, z, r, q, dinv, c.kappa, c.partials, c.scal, c.flags, STAGE_RHO, s);
+            e = launch_precond_yz<V>(aop, z, r, q, dinv, c.partials, c.scal, c.flags, STAGE_RHO, s);
             if (e != cudaSuccess) return e;
             k_pupdate_u<V, U><<<vec_grid(), 256, 0, s>>>(u, p, q, L, c.scal, c.flags);
             return cudaGetLastError();
