@@ -58,7 +58,7 @@ typedef enum {
     CW_ERR_NOT_CONVERGED = 4, /* solver hit maxit before the tolerance */
     CW_ERR_BREAKDOWN = 5,     /* CG breakdown: <p,Ap> <= 0 or a non-finite scalar */
     CW_ERR_TIMEOUT = 6,       /* a bounded device wait expired */
-    CW_ERR_UNSUPPORTED = 7    /* valid request that this build does not implement */
+    CW_ERR_UNSUPPORTED = 7    /* valid request that this library does not implement */
 } cw_status;
 
 /* operator kinds */
