@@ -117,6 +117,17 @@ const char *cw_last_error(void);
  * image of [0,1]^3 through its 8 vertices. nx, ny, nz >= 1. The mesh must outlive its operators.
  */
 cw_status cw_mesh_create(int nx, int ny, int nz, const double *verts_host, cw_mesh *out);
+
+/*
+ * Box mesh of the unit cube (the cube meshes of Sec. 7, generated here): nx*ny*nz cells, vertex
+ * (ix, iy, iz) at (ix/nx, iy/ny, iz/nz) moved by perturb*h * sin(2 pi f0 X) sin(2 pi f1 Y)
+ * sin(2 pi f2 Z) * dir (h = 1/max(nx, ny, nz), dir normalised; the displacement vanishes on the cube's
+ * faces, which are kept exact). freq: 3 integers or NULL for (1, 1, 1); direction: 3 doubles or NULL
+ * for (1, 1, 1)/sqrt(3). perturb = 0 gives the Cartesian mesh (usable with CW_GEOM_AFFINE).
+ * CW_ERR_ARG for sizes < 1, a zero or non-finite direction or a non-finite perturb.
+ */
+cw_status cw_mesh_create_box(int nx, int ny, int nz, double perturb, const int *freq, const double *direction,
+                             cw_mesh *out);
 cw_status cw_mesh_destroy(cw_mesh m);
 
 /*

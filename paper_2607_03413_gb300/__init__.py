@@ -29,7 +29,7 @@ CW_BATCH_GROUPED, CW_BATCH_SINGLE = 0, 1
 
 # exported symbols declared in include/cwfem.h (checked by the CPU test suite)
 EXPORTED = [
-    "cw_status_string", "cw_last_error", "cw_mesh_create", "cw_mesh_destroy", "cw_op_create",
+    "cw_status_string", "cw_last_error", "cw_mesh_create", "cw_mesh_create_box", "cw_mesh_destroy", "cw_op_create",
     "cw_op_destroy", "cw_op_cellwise_len", "cw_op_global_len", "cw_op_device_bytes", "cw_gather",
     "cw_apply", "cw_dss", "cw_diagonal", "cw_load_vector", "cw_cg_solve", "cw_op_set_variant",
     "cw_op_get_variant", "cw_op_autotune", "cw_cg_solve_noalloc", "cw_batch_create", "cw_batch_destroy",
@@ -68,6 +68,7 @@ def load(path: str = LIB_PATH):
         "cw_status_string": ([i32], ctypes.c_char_p),
         "cw_last_error": ([], ctypes.c_char_p),
         "cw_mesh_create": ([i32, i32, i32, vp, ctypes.POINTER(vp)], i32),
+        "cw_mesh_create_box": ([i32, i32, i32, ctypes.c_double, vp, vp, ctypes.POINTER(vp)], i32),
         "cw_mesh_destroy": ([vp], i32),
         "cw_op_create": ([vp, i32, i32, i32, i32, i32, ctypes.POINTER(vp)], i32),
         "cw_op_destroy": ([vp], i32),
@@ -136,6 +137,17 @@ def cw_mesh_create(nx, ny, nz, verts_host):
     assert v.size == (nx + 1) * (ny + 1) * (nz + 1) * 3
     h = ctypes.c_void_p()
     _check(L.cw_mesh_create(nx, ny, nz, v.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)), "cw_mesh_create")
+    return h
+
+
+def cw_mesh_create_box(nx, ny, nz, perturb=0.0, freq=None, direction=None):
+    L = load()
+    f = (ctypes.c_int * 3)(*freq) if freq is not None else None
+    d = (ctypes.c_double * 3)(*direction) if direction is not None else None
+    h = ctypes.c_void_p()
+    _check(L.cw_mesh_create_box(nx, ny, nz, float(perturb), ctypes.cast(f, ctypes.c_void_p) if f else None,
+                                ctypes.cast(d, ctypes.c_void_p) if d else None, ctypes.byref(h)),
+           "cw_mesh_create_box")
     return h
 
 
@@ -291,6 +303,16 @@ class Mesh:
     @classmethod
     def from_synth(cls, m):
         return cls(m.nx, m.ny, m.nz, m.verts)
+
+    @classmethod
+    def box(cls, nx, ny=None, nz=None, perturb=0.0, freq=None, direction=None):
+        """The unit-cube box mesh generated by the library (cw_mesh_create_box)."""
+        ny = nx if ny is None else ny
+        nz = nx if nz is None else nz
+        self = cls.__new__(cls)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.handle = cw_mesh_create_box(nx, ny, nz, perturb, freq, direction)
+        return self
 
     def close(self):
         if self.handle:

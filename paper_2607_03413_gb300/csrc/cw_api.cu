@@ -700,6 +700,46 @@ cw_status cw_mesh_create(int nx, int ny, int nz, const double *verts_host, cw_me
     return CW_OK;
 }
 
+cw_status cw_mesh_create_box(int nx, int ny, int nz, double perturb, const int *freq, const double *direction,
+                             cw_mesh *out)
+{
+    if (!out) return fail(CW_ERR_ARG, "cw_mesh_create_box: out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(CW_ERR_ARG, "cw_mesh_create_box: sizes must be >= 1");
+    if (!std::isfinite(perturb)) return fail(CW_ERR_ARG, "cw_mesh_create_box: non-finite perturbation");
+    const int f[3] = {freq ? freq[0] : 1, freq ? freq[1] : 1, freq ? freq[2] : 1};
+    double d[3] = {1.0, 1.0, 1.0};
+    if (direction) d[0] = direction[0], d[1] = direction[1], d[2] = direction[2];
+    const double dn = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (!(dn > 0.0) || !std::isfinite(dn)) return fail(CW_ERR_ARG, "cw_mesh_create_box: zero or non-finite direction");
+    for (double &c : d) c /= dn;
+    const double h = 1.0 / std::max(nx, std::max(ny, nz));
+    const double pi = 3.14159265358979323846;
+    std::vector<double> v((size_t)(nx + 1) * (ny + 1) * (nz + 1) * 3);
+    for (int vz = 0; vz <= nz; ++vz)
+        for (int vy = 0; vy <= ny; ++vy)
+            for (int vx = 0; vx <= nx; ++vx) {
+                double *c = &v[(((size_t)vz * (ny + 1) + vy) * (nx + 1) + vx) * 3];
+                const double X = vx / (double)nx, Y = vy / (double)ny, Z = vz / (double)nz;
+                c[0] = X;
+                c[1] = Y;
+                c[2] = Z;
+                if (perturb != 0.0) {
+                    const double sv = std::sin(2.0 * pi * f[0] * X) * std::sin(2.0 * pi * f[1] * Y) *
+                                      std::sin(2.0 * pi * f[2] * Z);
+                    for (int a = 0; a < 3; ++a) c[a] += perturb * h * sv * d[a];
+                    // the boundary stays the unit cube exactly
+                    if (vx == 0) c[0] = 0.0;
+                    if (vx == nx) c[0] = 1.0;
+                    if (vy == 0) c[1] = 0.0;
+                    if (vy == ny) c[1] = 1.0;
+                    if (vz == 0) c[2] = 0.0;
+                    if (vz == nz) c[2] = 1.0;
+                }
+            }
+    return cw_mesh_create(nx, ny, nz, v.data(), out);
+}
+
 cw_status cw_mesh_destroy(cw_mesh mh)
 {
     Mesh *m = reinterpret_cast<Mesh *>(mh);

@@ -59,3 +59,13 @@ def test_status_strings_and_argument_errors(lib):
     assert L.cw_apply(None, None, None, 0, None) == pkg.CW_ERR_ARG
     assert L.cw_op_cellwise_len(None) == -1
     assert b"NULL" in L.cw_last_error()
+
+
+def test_box_mesh_argument_errors(lib):
+    import paper_2607_03413_gb300 as pkg
+    L = pkg.load()
+    h = ctypes.c_void_p()
+    assert L.cw_mesh_create_box(0, 2, 2, 0.1, None, None, ctypes.byref(h)) == pkg.CW_ERR_ARG
+    zero = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    assert L.cw_mesh_create_box(2, 2, 2, 0.1, None, ctypes.cast(zero, ctypes.c_void_p), ctypes.byref(h)) == pkg.CW_ERR_ARG
+    assert L.cw_mesh_create_box(2, 2, 2, float("nan"), None, None, ctypes.byref(h)) == pkg.CW_ERR_ARG

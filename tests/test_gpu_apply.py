@@ -259,3 +259,21 @@ def test_create_reports_device_oom(cw):
     small = synth.box_mesh(2, 2, 2, perturb=0.1)
     op = cw.Operator(cw.Mesh.from_synth(small), 2, 1, cw.CW_GEOM_METRIC, cw.CW_PREC_F64)
     assert op.L == 8 * 27
+
+
+@pytest.mark.parametrize("perturb,freq,direction", [(0.1, None, None), (0.2, (2, 1, 3), (0.3, -1.0, 0.5)),
+                                                    (0.0, None, None)])
+def test_box_mesh_from_the_library(cw, orc, perturb, freq, direction):
+    """cw_mesh_create_box builds the same deformed cube as the input generator: the operator on it
+    matches the oracle on the generator's mesh."""
+    p = 3
+    kw = {} if freq is None else {"freq": freq, "direction": direction}
+    mesh = synth.box_mesh(4, 3, 5, perturb=perturb, **kw)
+    x = orc.gather(mesh, p, synth.global_vector(mesh, p, seed=7))
+    ref = orc.apply_local(mesh, p, 3, x)
+    import torch
+    M = cw.Mesh.box(4, 3, 5, perturb=perturb, freq=freq, direction=direction)
+    geom = cw.CW_GEOM_AFFINE if perturb == 0.0 else cw.CW_GEOM_METRIC
+    op = cw.Operator(M, p, 3, geom, cw.CW_PREC_F64)
+    y = to_np(op.apply(torch.from_numpy(x).cuda()))
+    assert rel_err(y, ref) <= TOL64
