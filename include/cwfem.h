@@ -246,7 +246,7 @@ cw_status cw_cg_solve(cw_op op, const double *b, double *u, double rtol, int max
 typedef struct cw_batch_s *cw_batch;
 cw_status cw_batch_create(const cw_op *ops, const int *nrhs, const void *const *x, void *const *y, int nprob,
                           cw_batch *out);
-cw_status cw_batch_destroy(cw_batch b);
+cw_status cw_batch_destroy(cw_batch b); /* waits for the device to finish first */
 /* total cell-wise values one launch processes: sum_i nrhs[i] * cw_op_cellwise_len(ops[i]) */
 int64_t cw_batch_values(cw_batch b);
 /* one launch: clears the work counter and starts the persistent kernel on `stream` */
@@ -254,7 +254,8 @@ cw_status cw_batch_launch(cw_batch b, void *stream);
 /* the same two operations captured once into a CUDA graph (on an internal stream) and replayed on
    `stream`; changing a variant re-captures at the next call */
 cw_status cw_batch_graph_launch(cw_batch b, void *stream);
-/* launch mode (CW_BATCH_GROUPED or CW_BATCH_SINGLE); variants are kept per mode */
+/* launch mode (CW_BATCH_GROUPED or CW_BATCH_SINGLE); variants are kept per mode. This call and
+   cw_batch_set_variant rewrite the device-side problem table and so wait for the device first */
 cw_status cw_batch_set_mode(cw_batch b, int mode);
 /* kernel variant of one degree in the current mode (see above); cells_per_tile (may be NULL)
    receives the resulting cells per tile */
@@ -264,6 +265,17 @@ cw_status cw_batch_get_variant(cw_batch b, int degree, int *variant, int *cells_
    launches of the whole batch on `stream` (overwriting every y) and keeps the fastest;
    synchronises */
 cw_status cw_batch_autotune(cw_batch b, int reps, void *stream, float *best_ms);
+
+/*
+ * One-shot batched apply: cw_batch_create over the same arguments (same requirements and argument
+ * errors; default mode and variants), one cw_batch_launch on `stream`, then for flags ==
+ * CW_APPLY_ASSEMBLE a DSS sum (cw_dss, CW_DSS_SUM) of every right-hand side of every problem, so
+ * that y_i = S A_i x_i as in cw_apply. flags: CW_APPLY_LOCAL or CW_APPLY_ASSEMBLE, else CW_ERR_ARG.
+ * Synchronises `stream` and frees the batch before it returns; device errors come back here.
+ * Callers that apply the same batch repeatedly should keep a cw_batch instead (no set-up per call).
+ */
+cw_status cw_apply_batched(const cw_op *ops, const void *const *x, void *const *y, const int *nrhs, int nprob,
+                           int flags, void *stream);
 
 /*
  * Allocation-free variant of cw_cg_solve. The paper has no counterpart; this entry point exists

@@ -34,7 +34,7 @@ EXPORTED = [
     "cw_apply", "cw_dss", "cw_diagonal", "cw_load_vector", "cw_cg_solve", "cw_op_set_variant",
     "cw_op_get_variant", "cw_op_autotune", "cw_cg_solve_noalloc", "cw_batch_create", "cw_batch_destroy",
     "cw_batch_values", "cw_batch_launch", "cw_batch_graph_launch", "cw_batch_set_variant",
-    "cw_batch_get_variant", "cw_batch_autotune", "cw_batch_set_mode", "cw_apply_host",
+    "cw_batch_get_variant", "cw_batch_autotune", "cw_batch_set_mode", "cw_apply_batched", "cw_apply_host",
 ]
 
 
@@ -95,6 +95,8 @@ def load(path: str = LIB_PATH):
         "cw_batch_get_variant": ([vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "cw_batch_autotune": ([vp, i32, vp, ctypes.POINTER(ctypes.c_float)], i32),
         "cw_batch_set_mode": ([vp, i32], i32),
+        "cw_apply_batched": ([ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i32), i32,
+                              i32, vp], i32),
         "cw_apply_host": ([vp, vp, vp, i32, vp], i32),
     }
     for name, (args, res) in sig.items():
@@ -286,6 +288,14 @@ def cw_batch_autotune(b, reps=3, stream=None):
     ms = ctypes.c_float()
     _check(load().cw_batch_autotune(b, reps, _stream(stream), ctypes.byref(ms)), "cw_batch_autotune")
     return ms.value
+
+
+def cw_apply_batched(ops, xs, ys, nrhs, flags=CW_APPLY_LOCAL, stream=None):
+    n = len(ops)
+    VP = ctypes.c_void_p * n
+    _check(load().cw_apply_batched(VP(*[o.value if isinstance(o, ctypes.c_void_p) else o for o in ops]),
+                                   VP(*[_ptr(x).value for x in xs]), VP(*[_ptr(y).value for y in ys]),
+                                   (ctypes.c_int * n)(*nrhs), n, flags, _stream(stream)), "cw_apply_batched")
 
 
 # ------------------------------------------------------------------ convenience ----

@@ -41,6 +41,9 @@ struct Batch {
 
 static void batch_free(Batch *b)
 {
+    // launches still in flight (on the caller's stream or the group streams) read d_probs and
+    // d_counter: let them finish before the memory goes back
+    cudaDeviceSynchronize();
     if (b->graph) cudaGraphExecDestroy(b->graph);
     cudaFree(b->d_probs);
     cudaFree(b->d_counter);
@@ -99,6 +102,9 @@ static cw_status batch_rebuild(Batch &b)
         if (per_sm < 1) return fail(CW_ERR_UNSUPPORTED, "cw_batch: kernel does not fit on an SM");
         b.grid = sms * per_sm;
     }
+    // the table is rewritten in place: a launch still running on a non-blocking stream, which a
+    // synchronous copy does not wait for, may be reading it
+    CW_CUDA_TRY(cudaDeviceSynchronize());
     CW_CUDA_TRY(cudaMemcpy(b.d_probs, b.h_probs.data(), b.h_probs.size() * sizeof(BatchProb), cudaMemcpyHostToDevice));
     if (b.graph) {
         cudaGraphExecDestroy(b.graph);
@@ -282,9 +288,17 @@ cw_status cw_batch_autotune(cw_batch bh, int reps, void *stream, float *best_ms)
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     bool present[9] = {false};
     for (Op *o : b->ops) present[o->n] = true;
-    cudaEvent_t e0, e1;
-    CW_CUDA_TRY(cudaEventCreate(&e0));
-    CW_CUDA_TRY(cudaEventCreate(&e1));
+    struct Events {  // destroyed on every return path
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ~Events()
+        {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+        }
+    } ev;
+    CW_CUDA_TRY(cudaEventCreate(&ev.e0));
+    CW_CUDA_TRY(cudaEventCreate(&ev.e1));
+    cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     float best_all = 0.0f;
     for (int n = 2; n <= 8; ++n) {  // coordinate descent over the degrees present
         if (!present[n]) continue;
@@ -311,11 +325,32 @@ cw_status cw_batch_autotune(cw_batch bh, int reps, void *stream, float *best_ms)
         *knob = bh_;
         best_all = best;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     cw_status st = batch_rebuild(*b);
     if (best_ms) *best_ms = best_all;
     return st;
+}
+
+cw_status cw_apply_batched(const cw_op *ops, const void *const *x, void *const *y, const int *nrhs, int nprob,
+                           int flags, void *stream)
+{
+    if (flags != CW_APPLY_LOCAL && flags != CW_APPLY_ASSEMBLE)
+        return fail(CW_ERR_ARG, "cw_apply_batched: flags must be CW_APPLY_LOCAL or CW_APPLY_ASSEMBLE");
+    cw_batch b = nullptr;
+    cw_status st = cw_batch_create(ops, nrhs, x, y, nprob, &b);
+    if (st != CW_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = cw_batch_launch(b, stream);
+    for (int i = 0; st == CW_OK && flags == CW_APPLY_ASSEMBLE && i < nprob; ++i) {
+        const Op *o = reinterpret_cast<const Op *>(ops[i]);
+        const size_t bytes = (size_t)o->L * (o->prec == CW_PREC_F64 ? sizeof(double) : sizeof(float));
+        for (int r = 0; st == CW_OK && r < nrhs[i]; ++r)
+            st = cw_dss(ops[i], static_cast<char *>(y[i]) + r * bytes, CW_DSS_SUM, stream);
+    }
+    const cudaError_t e = cudaStreamSynchronize(s);
+    cw_batch_destroy(b);
+    if (st != CW_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "cw_apply_batched");
+    return CW_OK;
 }
 
 }  // extern "C"

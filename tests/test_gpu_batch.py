@@ -87,6 +87,34 @@ def test_batch_matches_oracle_and_autotunes(cw, orc, mode):
         assert rel_err(to_np(y[r]), ref) <= 1e-12, (n, p)
 
 
+@pytest.mark.parametrize("prec", [0, 2], ids=["df64", "f32"])
+def test_apply_batched_one_shot(cw, orc, prec):
+    """cw_apply_batched: LOCAL equals a launch of a kept batch; ASSEMBLE equals the oracle's S A x."""
+    import torch
+    meshes, ops, xs, ys, nrhs = make_batch(cw, prec, SPECS)
+    B = cw.Batch(ops, nrhs, xs, ys)
+    B.launch()
+    torch.cuda.synchronize()
+    kept = [y.clone() for y in ys]
+    B.close()
+    handles = [o.handle for o in ops]
+    for y in ys:
+        y.fill_(float("nan"))
+    cw.cw_apply_batched(handles, xs, ys, nrhs, cw.CW_APPLY_LOCAL)
+    for y, k in zip(ys, kept):
+        assert torch.equal(y, k)
+    for y in ys:
+        y.fill_(float("nan"))
+    cw.cw_apply_batched(handles, xs, ys, nrhs, cw.CW_APPLY_ASSEMBLE)
+    tol = 1e-12 if prec == 0 else 1e-5
+    for (m, _), x, y, R, (n, p, _, kind) in zip(meshes, xs, ys, nrhs, SPECS):
+        for r in range(R):
+            ref = orc.dss(m, p, orc.apply_local(m, p, kind, to_np(x[r])))
+            assert rel_err(to_np(y[r]), ref) <= tol, (n, p, r)
+    with pytest.raises(cw.CwError):  # flags outside LOCAL / ASSEMBLE
+        cw.cw_apply_batched(handles, xs, ys, nrhs, 7)
+
+
 def test_batch_argument_errors(cw):
     import torch
     m = synth.box_mesh(2, perturb=0.1)
