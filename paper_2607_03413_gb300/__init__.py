@@ -303,6 +303,16 @@ _VEC_DTYPE = {CW_PREC_F64: "float64", CW_PREC_F64_NATIVE: "float64", CW_PREC_F32
               CW_PREC_F32_BF16G: "float32", CW_PREC_BF16: "bfloat16"}
 
 
+def _vec(t, n, dtype, what):
+    """Checks a vector argument against the length and dtype the C call assumes for it (the C ABI
+    takes bare pointers and cannot see either)."""
+    if t.dtype != dtype:
+        raise TypeError(f"{what}: expected dtype {dtype}, got {t.dtype}")
+    if t.numel() != n:
+        raise ValueError(f"{what}: expected {n} values, got {t.numel()}")
+    return t
+
+
 class Mesh:
     """Owns a cw_mesh handle built from a vertex array [(nz+1),(ny+1),(nx+1),3]."""
 
@@ -356,13 +366,23 @@ class Operator:
         import torch
         return torch.empty(self.L, dtype=self.vec_dtype, device="cuda")
 
+    def _cw(self, t, what):  # a cell-wise vector in the operator's storage type
+        return _vec(t, self.L, self.vec_dtype, what)
+
+    def _f64(self, t, what):  # a cell-wise FP64 vector (diagonal, load vector, solver vectors)
+        import torch
+        return _vec(t, self.L, torch.float64, what)
+
     def gather(self, u_global, x=None):
-        x = self.empty() if x is None else x
+        import torch
+        _vec(u_global, self.NG, torch.float64, "gather: u_global")
+        x = self.empty() if x is None else self._cw(x, "gather: x")
         cw_gather(self.handle, u_global, x)
         return x
 
     def apply(self, x, y=None, assemble=False):
-        y = self.empty() if y is None else y
+        self._cw(x, "apply: x")
+        y = self.empty() if y is None else self._cw(y, "apply: y")
         cw_apply(self.handle, x, y, CW_APPLY_ASSEMBLE if assemble else CW_APPLY_LOCAL)
         return y
 
@@ -373,10 +393,10 @@ class Operator:
         return cw_op_get_variant(self.handle)
 
     def autotune(self, x, y, reps=5):
-        return cw_op_autotune(self.handle, x, y, reps)
+        return cw_op_autotune(self.handle, self._cw(x, "autotune: x"), self._cw(y, "autotune: y"), reps)
 
     def dss(self, v, average=False):
-        cw_dss(self.handle, v, CW_DSS_AVERAGE if average else CW_DSS_SUM)
+        cw_dss(self.handle, self._cw(v, "dss: v"), CW_DSS_AVERAGE if average else CW_DSS_SUM)
         return v
 
     def diagonal(self):
@@ -393,7 +413,8 @@ class Operator:
 
     def cg_solve(self, b, u=None, rtol=1e-10, maxit=10000, mode=CW_CG_F64, check=True):
         import torch
-        u = torch.empty(self.L, dtype=torch.float64, device="cuda") if u is None else u
+        self._f64(b, "cg_solve: b")
+        u = torch.empty(self.L, dtype=torch.float64, device="cuda") if u is None else self._f64(u, "cg_solve: u")
         rc, st = cw_cg_solve(self.handle, b, u, rtol, maxit, mode, check=check)
         return u, st, rc
 
@@ -414,6 +435,11 @@ class Batch:
 
     def __init__(self, ops, nrhs, xs, ys):
         self.ops, self.nrhs, self.xs, self.ys = list(ops), list(nrhs), list(xs), list(ys)
+        if not (len(self.ops) == len(self.nrhs) == len(self.xs) == len(self.ys)):
+            raise ValueError("Batch: ops, nrhs, xs and ys differ in length")
+        for i, (o, r, x, y) in enumerate(zip(self.ops, self.nrhs, self.xs, self.ys)):
+            _vec(x, r * o.L, o.vec_dtype, f"Batch: xs[{i}]")
+            _vec(y, r * o.L, o.vec_dtype, f"Batch: ys[{i}]")
         self.handle = cw_batch_create([o.handle for o in self.ops], self.nrhs, self.xs, self.ys)
         self.values = cw_batch_values(self.handle)
 

@@ -69,3 +69,35 @@ def test_box_mesh_argument_errors(lib):
     zero = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
     assert L.cw_mesh_create_box(2, 2, 2, 0.1, None, ctypes.cast(zero, ctypes.c_void_p), ctypes.byref(h)) == pkg.CW_ERR_ARG
     assert L.cw_mesh_create_box(2, 2, 2, float("nan"), None, None, ctypes.byref(h)) == pkg.CW_ERR_ARG
+
+
+def test_binding_checks_vector_lengths_and_dtypes():
+    """The Python wrappers reject a vector of the wrong length or dtype before the C call, which
+    could not tell (it takes bare pointers). Host-only: the checks run before any device work."""
+    import torch
+    import paper_2607_03413_gb300 as cw
+    op = cw.Operator.__new__(cw.Operator)  # no library handle: the checks must fire first
+    op.handle, op.L, op.NG, op.prec = None, 10, 27, cw.CW_PREC_F32
+    good = torch.zeros(10, dtype=torch.float32)
+    with pytest.raises(ValueError):
+        op.apply(torch.zeros(9, dtype=torch.float32))
+    with pytest.raises(TypeError):
+        op.apply(torch.zeros(10, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        op.apply(good, torch.zeros(11, dtype=torch.float32))
+    with pytest.raises(ValueError):
+        op.dss(torch.zeros(20, dtype=torch.float32))
+    with pytest.raises(TypeError):  # the global input is FP64 whatever the storage precision
+        op.gather(torch.zeros(27, dtype=torch.float32), good)
+    with pytest.raises(ValueError):
+        op.gather(torch.zeros(26, dtype=torch.float64), good)
+    with pytest.raises(TypeError):  # solver vectors are FP64
+        op.cg_solve(good)
+    with pytest.raises(ValueError):
+        op.cg_solve(torch.zeros(10, dtype=torch.float64), torch.zeros(5, dtype=torch.float64))
+    with pytest.raises(ValueError):  # a batch's vectors hold nrhs cell-wise vectors
+        cw.Batch([op], [2], [good], [good])
+    with pytest.raises(ValueError):
+        cw.Batch([op], [1, 1], [good], [good])
+    with pytest.raises(TypeError):
+        cw.Batch([op], [1], [good], [torch.zeros(10, dtype=torch.bfloat16)])
