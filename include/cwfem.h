@@ -114,7 +114,9 @@ const char *cw_last_error(void);
 /*
  * Create a mesh from host vertex coordinates verts[((vz*(ny+1) + vy)*(nx+1) + vx)*3 + d]
  * (double, (nx+1)(ny+1)(nz+1)*3 entries, copied to the device). Cell (cx,cy,cz) is the trilinear
- * image of [0,1]^3 through its 8 vertices. nx, ny, nz >= 1. The mesh must outlive its operators.
+ * image of [0,1]^3 through its 8 vertices. 1 <= nx, ny, nz <= 65535 and nx*ny*nz <= 2^31, else
+ * CW_ERR_ARG; CW_ERR_OOM if the host or device copy cannot be allocated. The mesh must outlive its
+ * operators.
  */
 cw_status cw_mesh_create(int nx, int ny, int nz, const double *verts_host, cw_mesh *out);
 
@@ -124,7 +126,8 @@ cw_status cw_mesh_create(int nx, int ny, int nz, const double *verts_host, cw_me
  * sin(2 pi f2 Z) * dir (h = 1/max(nx, ny, nz), dir normalised; the displacement vanishes on the cube's
  * faces, which are kept exact). freq: 3 integers or NULL for (1, 1, 1); direction: 3 doubles or NULL
  * for (1, 1, 1)/sqrt(3). perturb = 0 gives the Cartesian mesh (usable with CW_GEOM_AFFINE).
- * CW_ERR_ARG for sizes < 1, a zero or non-finite direction or a non-finite perturb.
+ * CW_ERR_ARG for sizes outside the limits of cw_mesh_create, a zero or non-finite direction or a
+ * non-finite perturb.
  */
 cw_status cw_mesh_create_box(int nx, int ny, int nz, double perturb, const int *freq, const double *direction,
                              cw_mesh *out);
@@ -137,7 +140,9 @@ cw_status cw_mesh_destroy(cw_mesh m);
  * map, as float pairs for the FP64 precisions and floats otherwise -- no per-point storage, the
  * metric is formed in the kernel; CW_GEOM_AFFINE: 4 doubles per cell, and the mesh must be
  * Cartesian -- CW_ERR_ARG otherwise) and the 1D tables. Curved modes check det J > 0 at every
- * quadrature point (CW_ERR_ARG otherwise). Synchronous.
+ * quadrature point (CW_ERR_ARG otherwise). CW_ERR_UNSUPPORTED where one DSS axis pass would have
+ * 2^32 or more face-node pairs ((p+1)^2 * ny * (nx-1), (p+1)^2 * nx * (ny-1) or (p+1)^2 * nx * (nz-1)).
+ * Synchronous.
  */
 cw_status cw_op_create(cw_mesh m, int degree, int kind, int geom, int prec, int bc, cw_op *out);
 cw_status cw_op_destroy(cw_op op);

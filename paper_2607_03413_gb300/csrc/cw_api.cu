@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -672,13 +673,21 @@ cw_status cw_mesh_create(int nx, int ny, int nz, const double *verts_host, cw_me
     if (!out) return fail(CW_ERR_ARG, "cw_mesh_create: out is NULL");
     *out = nullptr;
     if (nx < 1 || ny < 1 || nz < 1 || !verts_host) return fail(CW_ERR_ARG, "cw_mesh_create: bad sizes or NULL vertices");
-    const int64_t nv = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+    if (nx > kMaxCellsPerDir || ny > kMaxCellsPerDir || nz > kMaxCellsPerDir)
+        return fail(CW_ERR_ARG, "cw_mesh_create: more than 65535 cells in one direction");
+    const int64_t nv = ((int64_t)nx + 1) * ((int64_t)ny + 1) * ((int64_t)nz + 1);
     if ((int64_t)nx * ny * nz > (int64_t)1 << 31) return fail(CW_ERR_ARG, "cw_mesh_create: more than 2^31 cells");
-    Mesh *m = new Mesh;
+    Mesh *m = new (std::nothrow) Mesh;
+    if (!m) return fail(CW_ERR_OOM, "cw_mesh_create: host allocation failed");
     m->nx = nx;
     m->ny = ny;
     m->nz = nz;
-    m->h_verts.assign(verts_host, verts_host + nv * 3);
+    try {
+        m->h_verts.assign(verts_host, verts_host + nv * 3);
+    } catch (const std::bad_alloc &) {
+        delete m;
+        return fail(CW_ERR_OOM, "cw_mesh_create: host allocation failed");
+    }
     // Cartesian test: x depends on vx only, y on vy only, z on vz only
     bool cart = true;
     for (int64_t vz = 0; vz <= nz && cart; ++vz)
@@ -706,6 +715,9 @@ cw_status cw_mesh_create_box(int nx, int ny, int nz, double perturb, const int *
     if (!out) return fail(CW_ERR_ARG, "cw_mesh_create_box: out is NULL");
     *out = nullptr;
     if (nx < 1 || ny < 1 || nz < 1) return fail(CW_ERR_ARG, "cw_mesh_create_box: sizes must be >= 1");
+    if (nx > kMaxCellsPerDir || ny > kMaxCellsPerDir || nz > kMaxCellsPerDir)
+        return fail(CW_ERR_ARG, "cw_mesh_create_box: more than 65535 cells in one direction");
+    if ((int64_t)nx * ny * nz > (int64_t)1 << 31) return fail(CW_ERR_ARG, "cw_mesh_create_box: more than 2^31 cells");
     if (!std::isfinite(perturb)) return fail(CW_ERR_ARG, "cw_mesh_create_box: non-finite perturbation");
     const int f[3] = {freq ? freq[0] : 1, freq ? freq[1] : 1, freq ? freq[2] : 1};
     double d[3] = {1.0, 1.0, 1.0};
@@ -715,7 +727,12 @@ cw_status cw_mesh_create_box(int nx, int ny, int nz, double perturb, const int *
     for (double &c : d) c /= dn;
     const double h = 1.0 / std::max(nx, std::max(ny, nz));
     const double pi = 3.14159265358979323846;
-    std::vector<double> v((size_t)(nx + 1) * (ny + 1) * (nz + 1) * 3);
+    std::vector<double> v;
+    try {
+        v.resize((size_t)(nx + 1) * (ny + 1) * (nz + 1) * 3);
+    } catch (const std::bad_alloc &) {
+        return fail(CW_ERR_OOM, "cw_mesh_create_box: host allocation failed");
+    }
     for (int vz = 0; vz <= nz; ++vz)
         for (int vy = 0; vy <= ny; ++vy)
             for (int vx = 0; vx <= nx; ++vx) {
@@ -763,6 +780,13 @@ cw_status cw_op_create(cw_mesh mh, int degree, int kind, int geom, int prec, int
     if (bc != CW_BC_NONE && bc != CW_BC_DIRICHLET0) return fail(CW_ERR_ARG, "cw_op_create: bad bc");
     if (geom == CW_GEOM_AFFINE && !m->cartesian)
         return fail(CW_ERR_ARG, "cw_op_create: CW_GEOM_AFFINE needs a Cartesian (axis-aligned) mesh");
+    {  // the DSS axis passes index one plane of face nodes with 32 bits
+        const int64_t n2 = (int64_t)(degree + 1) * (degree + 1);
+        const int64_t plane[3] = {n2 * m->ny * (m->nx - 1), n2 * m->nx * (m->ny - 1), n2 * m->nx * (m->nz - 1)};
+        for (int64_t c : plane)
+            if (c >= ((int64_t)1 << 32))
+                return fail(CW_ERR_UNSUPPORTED, "cw_op_create: a DSS plane holds 2^32 or more face-node pairs");
+    }
     Op *op = new Op;
     op->mesh = m;
     op->p = degree;

@@ -10,6 +10,8 @@
 namespace cw {
 
 constexpr int kMaxDegree = 7;
+// cells per mesh direction: the DSS launches put one direction on the grid's y extent (<= 65535)
+constexpr int kMaxCellsPerDir = 65535;
 constexpr int kMaxN = kMaxDegree + 1;
 
 // 1D tables of one degree, in double (built from long-double rules by cw_tables.cpp)

@@ -71,6 +71,18 @@ def test_box_mesh_argument_errors(lib):
     assert L.cw_mesh_create_box(2, 2, 2, float("nan"), None, None, ctypes.byref(h)) == pkg.CW_ERR_ARG
 
 
+def test_mesh_size_limits(lib):
+    """At most 65535 cells per direction and 2^31 cells: rejected on the host before any device call."""
+    import paper_2607_03413_gb300 as pkg
+    L = pkg.load()
+    h = ctypes.c_void_p()
+    dummy = (ctypes.c_double * 3)()
+    for dims in ((65536, 1, 1), (1, 65536, 1), (1, 1, 65536), (2 ** 31 - 1, 1, 1), (2048, 2048, 1024)):
+        assert L.cw_mesh_create(*dims, ctypes.cast(dummy, ctypes.c_void_p), ctypes.byref(h)) == pkg.CW_ERR_ARG, dims
+        assert L.cw_mesh_create_box(*dims, 0.0, None, None, ctypes.byref(h)) == pkg.CW_ERR_ARG, dims
+        assert not h.value
+
+
 def test_binding_checks_vector_lengths_and_dtypes():
     """The Python wrappers reject a vector of the wrong length or dtype before the C call, which
     could not tell (it takes bare pointers). Host-only: the checks run before any device work."""
