@@ -9,7 +9,10 @@ Pieces:
     S = G G^T, the assembled diagonal, the load vector and error norms;
   * this module: ctypes wrappers, the global sparse matrix A_CG = G^T A G assembled by
     brute force (Sec. 2.1, Eq. (constrained_system)), and an assembled Jacobi-preconditioned CG on
-    the interior DoFs (homogeneous Dirichlet), plus a sparse direct solve.
+    the interior DoFs (homogeneous Dirichlet), plus a sparse direct solve;
+  * ``oracle.mg``: the geometric multigrid of a uniform mesh hierarchy (Sec. 3 and 5): cell-wise
+    transfers, the cell-wise damped Jacobi smoother in its literal and fused forms, the V-cycle and
+    the V-cycle-preconditioned CG, beside the classical assembled V-cycle they are equivalent to.
 """
 import ctypes
 import os
@@ -61,6 +64,9 @@ def lib():
         L.orc_load_vector.argtypes = [c_int, c_int, c_int, dp, c_int, c_int, dp]
         L.orc_error_norms.argtypes = [c_int, c_int, c_int, dp, c_int, c_int, c_int, dp, dp]
         L.orc_node_coords.argtypes = [c_int, c_int, c_int, dp, c_int, dp]
+        L.orc_prolong_1d.argtypes = [c_int, dp, dp]
+        L.orc_prolong.argtypes = [c_int, c_int, c_int, c_int, dp, dp]
+        L.orc_restrict.argtypes = [c_int, c_int, c_int, c_int, dp, dp]
         _lib = L
     return _lib
 

@@ -17,7 +17,10 @@
  *    stiffness summation S = G G^T (Sec. 4.1, Eq. (dss_operator)) by global index;
  *  - the assembled diagonal d = G^T diag(A_K) (Sec. 4.1, Eq. (jacobi_recap));
  *  - the load vector b_K,i = sum_q w_q detJ f(x_q) phi_i(x_q) and L2 / H1 errors against the
- *    manufactured solution u = sin(pi x) sin(pi y) sin(pi z), f = 3 pi^2 u.
+ *    manufactured solution u = sin(pi x) sin(pi y) sin(pi z), f = 3 pi^2 u;
+ *  - the cell-wise inter-grid transfers of a uniform mesh hierarchy (Sec. 3, Algorithms
+ *    prolongation and restriction): per parent cell and child, the Kronecker product of the 1D
+ *    child prolongation matrices, written out entry by entry.
  *
  * Conventions: reference cell [0,1]^3; local DoF index i + n*(j + n*k) with i along x;
  * cells numbered cx + nx*(cy + ny*cz); vertices V[((vz*(ny+1) + vy)*(nx+1) + vx)*3 + d];
@@ -522,4 +525,96 @@ void orc_node_coords(int nx, int ny, int nz, const double *V, int p, double *xyz
                 }
     }
     (void)nz;
+}
+
+/* ------------------------------------------------ inter-grid transfers ---- */
+
+/* The 1D prolongation matrices of the two children of an interval (Sec. 3, inter-grid transfers):
+   child b in {0, 1} covers [b/2, (b+1)/2] of the parent's reference interval, so its node xi_i
+   sits at (xi_i + b)/2 there, and P_b[i][a] = l_a((xi_i + b)/2) with l_a the parent's Lagrange
+   basis on the Gauss-Lobatto nodes. */
+void orc_prolong_1d(int p, double *P0, double *P1)
+{
+    const int n = p + 1;
+    double xi[ORC_MAXN], l[ORC_MAXN], dl[ORC_MAXN];
+    orc_gll(p, xi);
+    for (int b = 0; b < 2; ++b)
+        for (int i = 0; i < n; ++i) {
+            orc_lagrange(n, xi, 0.5 * (xi[i] + b), l, dl);
+            for (int a = 0; a < n; ++a) (b ? P1 : P0)[i * n + a] = l[a];
+        }
+}
+
+/* Child c = bx + 2 by + 4 bz of coarse cell (cx, cy, cz) is fine cell (2cx+bx, 2cy+by, 2cz+bz) of
+   the 2ncx x 2ncy x 2ncz mesh; bit d of c selects P_0 or P_1 along axis d. */
+static int64_t child_cell(int ncx, int ncy, int64_t cx, int64_t cy, int64_t cz, int c)
+{
+    const int64_t nfx = 2 * (int64_t)ncx, nfy = 2 * (int64_t)ncy;
+    return (2 * cx + (c & 1)) + nfx * ((2 * cy + ((c >> 1) & 1)) + nfy * (2 * cz + ((c >> 2) & 1)));
+}
+
+/* Algorithm prolongation: for every coarse cell K and child K_c,
+   u_f|K_c = (P_bz (x) P_by (x) P_bx) u_c|K, the Kronecker product written out entry by entry:
+   u_f[i,j,k] = sum_{a,b,c} P_bx[i][a] P_by[j][b] P_bz[k][c] u_c[a,b,c]. Every fine cell is the
+   child of exactly one coarse cell, so the zero-initialised accumulation of the algorithm is an
+   assignment here. */
+void orc_prolong(int ncx, int ncy, int ncz, int p, const double *uc, double *uf)
+{
+    const int n = p + 1, n3 = n * n * n;
+    double P[2][ORC_MAXN * ORC_MAXN];
+    orc_prolong_1d(p, P[0], P[1]);
+    const int64_t E = (int64_t)ncx * ncy * ncz;
+#pragma omp parallel for
+    for (int64_t e = 0; e < E; ++e) {
+        const int64_t cx = e % ncx, cy = (e / ncx) % ncy, cz = e / ((int64_t)ncx * ncy);
+        const double *u = uc + e * n3;
+        for (int ch = 0; ch < 8; ++ch) {
+            const double *Px = P[ch & 1], *Py = P[(ch >> 1) & 1], *Pz = P[(ch >> 2) & 1];
+            double *y = uf + child_cell(ncx, ncy, cx, cy, cz, ch) * n3;
+            for (int k = 0; k < n; ++k)
+                for (int j = 0; j < n; ++j)
+                    for (int i = 0; i < n; ++i) {
+                        double s = 0.0;
+                        for (int c = 0; c < n; ++c)
+                            for (int b = 0; b < n; ++b)
+                                for (int a = 0; a < n; ++a)
+                                    s += Px[i * n + a] * Py[j * n + b] * Pz[k * n + c] * u[a + n * (b + n * c)];
+                        y[i + n * (j + n * k)] = s;
+                    }
+        }
+    }
+    (void)ncz;
+}
+
+/* Algorithm restriction: for every coarse cell K, r_c|K = sum over its children K_c of
+   (P_bz^T (x) P_by^T (x) P_bx^T) r_f|K_c, i.e.
+   r_c[a,b,c] = sum_c sum_{i,j,k} P_bx[i][a] P_by[j][b] P_bz[k][c] r_f|K_c[i,j,k]. Acts on raw
+   (unassembled) dual vectors: no assembly and no weights. */
+void orc_restrict(int ncx, int ncy, int ncz, int p, const double *rf, double *rc)
+{
+    const int n = p + 1, n3 = n * n * n;
+    double P[2][ORC_MAXN * ORC_MAXN];
+    orc_prolong_1d(p, P[0], P[1]);
+    const int64_t E = (int64_t)ncx * ncy * ncz;
+#pragma omp parallel for
+    for (int64_t e = 0; e < E; ++e) {
+        const int64_t cx = e % ncx, cy = (e / ncx) % ncy, cz = e / ((int64_t)ncx * ncy);
+        double *r = rc + e * n3;
+        for (int q = 0; q < n3; ++q) r[q] = 0.0;
+        for (int ch = 0; ch < 8; ++ch) {
+            const double *Px = P[ch & 1], *Py = P[(ch >> 1) & 1], *Pz = P[(ch >> 2) & 1];
+            const double *y = rf + child_cell(ncx, ncy, cx, cy, cz, ch) * n3;
+            for (int c = 0; c < n; ++c)
+                for (int b = 0; b < n; ++b)
+                    for (int a = 0; a < n; ++a) {
+                        double s = 0.0;
+                        for (int k = 0; k < n; ++k)
+                            for (int j = 0; j < n; ++j)
+                                for (int i = 0; i < n; ++i)
+                                    s += Px[i * n + a] * Py[j * n + b] * Pz[k * n + c] * y[i + n * (j + n * k)];
+                        r[a + n * (b + n * c)] += s;
+                    }
+        }
+    }
+    (void)ncz;
 }

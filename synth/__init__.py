@@ -15,7 +15,7 @@ from dataclasses import dataclass
 import math
 import numpy as np
 
-__all__ = ["Mesh", "box_mesh", "global_vector", "cellwise_random", "batched_problem_list",
+__all__ = ["Mesh", "box_mesh", "refine", "global_vector", "cellwise_random", "batched_problem_list",
            "global_len", "cellwise_len"]
 
 
@@ -60,6 +60,32 @@ def box_mesh(nx, ny=None, nz=None, perturb=0.0, freq=(1, 1, 1), direction=None) 
         verts[0, :, :, 2] = 0.0
         verts[-1, :, :, 2] = 1.0
     return Mesh(nx, ny, nz, np.ascontiguousarray(verts), affine=(perturb == 0.0))
+
+
+def refine(mesh: Mesh) -> Mesh:
+    """The next level of a uniform mesh hierarchy: every cell split into 2 x 2 x 2 children by its
+    own trilinear map (Sec. 3: nested meshes, each cell of a level obtained by refining a cell of
+    the previous one). Child vertices are the parent map at the half points, i.e. along every axis
+    the old vertex rows are kept and the midpoint of each pair of neighbours is inserted; the
+    children are trilinear images again, so the finite-element spaces of the levels are nested."""
+    v = mesh.verts
+    for axis in (2, 1, 0):  # x, y, z vertex index (array axes 2, 1, 0)
+        n = v.shape[axis]
+        shape = list(v.shape)
+        shape[axis] = 2 * n - 1
+        w = np.empty(shape)
+        even = [slice(None)] * 4
+        odd = [slice(None)] * 4
+        even[axis] = slice(0, None, 2)
+        odd[axis] = slice(1, None, 2)
+        lo = [slice(None)] * 4
+        hi = [slice(None)] * 4
+        lo[axis] = slice(0, n - 1)
+        hi[axis] = slice(1, n)
+        w[tuple(even)] = v
+        w[tuple(odd)] = 0.5 * (v[tuple(lo)] + v[tuple(hi)])
+        v = w
+    return Mesh(2 * mesh.nx, 2 * mesh.ny, 2 * mesh.nz, np.ascontiguousarray(v), affine=mesh.affine)
 
 
 def global_len(mesh: Mesh, p: int) -> int:
