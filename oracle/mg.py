@@ -149,20 +149,29 @@ def coarse_solve(level, b):
     return gather(level.mesh, level.p, ug)
 
 
-def vcycle(levels, l, b, u, nu1=2, nu2=2, omega=0.7, fused=False):
-    """Algorithm mg_vcycle on cell-wise vectors: b raw dual, u continuous primal; returns u."""
+def stored(x, dtype):
+    """x as held in memory of the given precision (FP64: unchanged; FP32: rounded to nearest)."""
+    return x if dtype == np.float64 else x.astype(dtype).astype(np.float64)
+
+
+def vcycle(levels, l, b, u, nu1=2, nu2=2, omega=0.7, fused=False, dtype=np.float64):
+    """Algorithm mg_vcycle on cell-wise vectors: b raw dual, u continuous primal; returns u.
+    ``dtype`` is the storage precision of every vector of the cycle (FP32 for the mixed-precision
+    cycle: each step's result is rounded to it; the arithmetic of a step stays FP64)."""
     L = levels[l]
+    b = stored(b, dtype)
     if l == 0:
-        return coarse_solve(L, b)
+        return stored(coarse_solve(L, b), dtype)
     sm = smooth_fused if fused else smooth
+    u = stored(u, dtype)
     for _ in range(nu1):
-        u = sm(L, b, u, omega)
-    r = b - L.apply(u)
-    bc = restrict(levels[l - 1].mesh, L.p, r)
-    e = vcycle(levels, l - 1, bc, np.zeros_like(bc), nu1, nu2, omega, fused)
-    u = u + prolong(levels[l - 1].mesh, L.p, e)
+        u = stored(sm(L, b, u, omega), dtype)
+    r = stored(b - L.apply(u), dtype)
+    bc = stored(restrict(levels[l - 1].mesh, L.p, r), dtype)
+    e = vcycle(levels, l - 1, bc, np.zeros_like(bc), nu1, nu2, omega, fused, dtype)
+    u = stored(u + prolong(levels[l - 1].mesh, L.p, e), dtype)
     for _ in range(nu2):
-        u = sm(L, b, u, omega)
+        u = stored(sm(L, b, u, omega), dtype)
     return u
 
 
@@ -183,15 +192,27 @@ def vcycle_assembled(levels, l, b, u, nu1=2, nu2=2, omega=0.7):
 
 
 # ------------------------------------------------------------------ MG-PCG
-def mg_pcg(levels, b, tol=1e-10, maxit=200, nu1=2, nu2=2, omega=0.7, fused=False):
+def energy_measure(level, b, u):
+    """eta(u) = <b - A u, u> (Eq. (energy_measure)): raw residual paired with the continuous iterate."""
+    return float((b - level.apply(u)) @ u)
+
+
+def mg_pcg(levels, b, tol=1e-10, maxit=200, nu1=2, nu2=2, omega=0.7, fused=False, dtype=np.float64):
     """CG on the finest level, cell-wise primal-dual form (residual raw, iterate and direction
     continuous), preconditioned by one V-cycle from a zero initial guess (Sec. 5: the cycle then
-    starts from the residual itself). Returns (u, iterations, sqrt(<r,z>/<r_0,z_0>))."""
+    starts from the residual itself). The CG runs in FP64; ``dtype`` is the storage precision of
+    the V-cycle (FP32: the mixed-precision preconditioner the paper names as the next gain, Sec. 8).
+    A reduced-precision cycle is fed the averaged residual S-bar r (Eq. (averaging_dss)): the raw
+    residual's copies are O(1) partial integrals whose sum is tiny, and rounding them would destroy
+    the assembled residual; the average has the same assembly (the cycle reads its input only
+    through G^T) with every copy small. Returns (u, iterations, sqrt(<r,z>/<r_0,z_0>))."""
     top = len(levels) - 1
     L = levels[top]
 
     def precond(r):
-        return vcycle(levels, top, r, np.zeros_like(r), nu1, nu2, omega, fused)
+        if dtype != np.float64:
+            r = average(L, r)
+        return vcycle(levels, top, r, np.zeros_like(r), nu1, nu2, omega, fused, dtype)
 
     u = np.zeros_like(b)
     r = b.copy()
