@@ -44,3 +44,25 @@ def test_reference_arm_other_ranks_do_no_work():
     import bench
     args = argparse.Namespace(steps=1, warmup=3)
     assert bench.reference_arm(args, rank=1, world=2) is None
+
+
+def test_reference_arm_json_contract():
+    """Rank 0 of the reference arm times the oracle on the host cores and returns the contract's
+    line: the base keys, "impl": "reference", a cpu_baseline describing the run and an e2e entry
+    with no host-device bytes."""
+    import argparse
+    import json
+
+    import bench
+    r = bench.reference_arm(argparse.Namespace(steps=1, warmup=3), rank=0, world=1)
+    json.dumps(r)  # serialisable as one line
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert k in r, k
+    assert r["impl"] == "reference" and r["value"] > 0 and r["steps"] == 1 and r["warmup"] == 3
+    assert r["higher_is_better"] is True and r["vs_baseline"] is None and "workload" in r["config"]
+    cb = r["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == r["value"] and cb["cores"] >= 1 and cb["sample"]
+    e = r["e2e"]
+    assert e["value"] == r["value"] and e["unit"] == r["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
