@@ -3,9 +3,10 @@
 // One CTA owns a tile of CPB consecutive cells; a cell is worked by N*N threads. A thread plays
 // three roles in turn: owner of an x-line (j,k), of a y-line (i,k) and of a z-pencil (i,j), with
 // (r % N, r / N) as its pair of indices, r in [0, N*N). 1D contractions along the owned line run
-// in registers; switching axis goes through shared memory (padded row pitch PI = N|1 keeps line
-// accesses free of bank conflicts). The 1D tables are kernel parameters (constant bank) so every
-// contraction coefficient is an immediate operand.
+// in registers; switching axis goes through shared memory (the odd row pitch PI = N|1 spreads a
+// cell's line accesses over the banks; where two cells share a warp, as at N = 5, some conflicts
+// remain). The 1D tables are kernel parameters (constant bank) so every contraction coefficient is
+// an immediate operand.
 //
 // Curved cells (Sec. 6, "the general cell-wise Laplacian: evaluate gradients, apply the physics,
 // integrate gradients"), per cell with u the nodal values:

@@ -1,6 +1,6 @@
 // cw_arith.cuh -- arithmetic types for the cell-wise operator kernels.
 //
-// GB300 executes native FP64 FMA at about 1/64 of the FP32 rate (measured 1.0 TFLOP/s FP64 vs
+// GB300 executes native FP64 FMA at about 1/73 of the FP32 rate (measured 1.0 TFLOP/s FP64 vs
 // 73 TFLOP/s FP32), so the FP64 operator path computes in double-float arithmetic: a value is an
 // unevaluated sum hi + lo of two floats (Dekker 1971; error-free TwoSum of Knuth and the
 // FMA-based TwoProduct, as collected by Muller et al., "Handbook of Floating-Point Arithmetic").
