@@ -53,6 +53,23 @@ def test_dss_identities(orc, p):
     assert np.allclose(Sbar(Gu), Gu, atol=1e-14)
 
 
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_valence_and_scaling_identities(orc, p):
+    """Eq. (jacobi_recap): G D_CG^-1 = D_cell^-1 G (scaling intertwines with the gather), and
+    Eq. (valence_baking): S_bar K_cell D_cell^-1 = D_cell^-1 S on raw vectors."""
+    mesh = synth.box_mesh(3, 2, 3, perturb=0.2)
+    d = orc.diagonal(mesh, p, 1)
+    u = synth.global_vector(mesh, p, seed=11)
+    dinv_cell = orc.gather(mesh, p, 1.0 / d)
+    assert np.array_equal(orc.gather(mesh, p, (1.0 / d) * u), dinv_cell * orc.gather(mesh, p, u))
+    kcell = orc.gather(mesh, p, valence_closed_form(mesh, p))
+    r = synth.cellwise_random(mesh, p, seed=12)
+    kappa_g = orc.scatter_add(mesh, p, np.ones_like(r))
+    lhs = orc.gather(mesh, p, orc.scatter_add(mesh, p, kcell * dinv_cell * r) / kappa_g)
+    rhs = dinv_cell * orc.dss(mesh, p, r)
+    assert np.abs(lhs - rhs).max() < 1e-14 * np.abs(rhs).max()
+
+
 def test_pairing_identity(orc):
     """<f~, G u> = <G^T f~, u> (Sec. 2.1, Eq. (pairing_global))."""
     mesh = synth.box_mesh(2, 3, 3, perturb=0.2)
