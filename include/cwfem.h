@@ -131,6 +131,15 @@ cw_status cw_mesh_create(int nx, int ny, int nz, const double *verts_host, cw_me
  */
 cw_status cw_mesh_create_box(int nx, int ny, int nz, double perturb, const int *freq, const double *direction,
                              cw_mesh *out);
+/*
+ * Vertex array of the uniform refinement of a mesh (the next level of a multigrid hierarchy, Sec. 3:
+ * every cell split into 2 x 2 x 2 children by its own trilinear map, so the finite-element spaces of
+ * the two meshes are nested). verts: the (nx+1)(ny+1)(nz+1)*3 doubles of cw_mesh_create's layout;
+ * out: (2nx+1)(2ny+1)(2nz+1)*3 doubles in the same layout, caller-owned, to pass to cw_mesh_create
+ * with 2nx, 2ny, 2nz. Host only (no device work). CW_ERR_ARG for NULL pointers or a refined mesh
+ * outside cw_mesh_create's limits; CW_ERR_OOM if host scratch cannot be allocated.
+ */
+cw_status cw_mesh_refine_vertices(int nx, int ny, int nz, const double *verts, double *out);
 cw_status cw_mesh_destroy(cw_mesh m);
 
 /*

@@ -35,6 +35,7 @@ EXPORTED = [
     "cw_op_get_variant", "cw_op_autotune", "cw_cg_solve_noalloc", "cw_batch_create", "cw_batch_destroy",
     "cw_batch_values", "cw_batch_launch", "cw_batch_graph_launch", "cw_batch_set_variant",
     "cw_batch_get_variant", "cw_batch_autotune", "cw_batch_set_mode", "cw_apply_batched", "cw_apply_host",
+    "cw_mesh_refine_vertices",
 ]
 
 
@@ -98,6 +99,7 @@ def load(path: str = LIB_PATH):
         "cw_apply_batched": ([ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i32), i32,
                               i32, vp], i32),
         "cw_apply_host": ([vp, vp, vp, i32, vp], i32),
+        "cw_mesh_refine_vertices": ([i32, i32, i32, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -151,6 +153,17 @@ def cw_mesh_create_box(nx, ny, nz, perturb=0.0, freq=None, direction=None):
                                 ctypes.cast(d, ctypes.c_void_p) if d else None, ctypes.byref(h)),
            "cw_mesh_create_box")
     return h
+
+
+def cw_mesh_refine_vertices(nx, ny, nz, verts):
+    """Vertex array [(2nz+1),(2ny+1),(2nx+1),3] of the uniform refinement (host only)."""
+    import numpy as np
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    assert v.size == (nx + 1) * (ny + 1) * (nz + 1) * 3
+    out = np.empty((2 * nz + 1, 2 * ny + 1, 2 * nx + 1, 3))
+    _check(load().cw_mesh_refine_vertices(nx, ny, nz, v.ctypes.data_as(ctypes.c_void_p),
+                                          out.ctypes.data_as(ctypes.c_void_p)), "cw_mesh_refine_vertices")
+    return out
 
 
 def cw_mesh_destroy(h):
@@ -317,8 +330,10 @@ class Mesh:
     """Owns a cw_mesh handle built from a vertex array [(nz+1),(ny+1),(nx+1),3]."""
 
     def __init__(self, nx, ny, nz, verts):
+        import numpy as np
         self.nx, self.ny, self.nz = nx, ny, nz
-        self.handle = cw_mesh_create(nx, ny, nz, verts)
+        self.verts = np.ascontiguousarray(verts, dtype=np.float64)  # kept for refine()
+        self.handle = cw_mesh_create(nx, ny, nz, self.verts)
 
     @classmethod
     def from_synth(cls, m):
@@ -331,8 +346,16 @@ class Mesh:
         nz = nx if nz is None else nz
         self = cls.__new__(cls)
         self.nx, self.ny, self.nz = nx, ny, nz
+        self.verts = None  # generated in the library
         self.handle = cw_mesh_create_box(nx, ny, nz, perturb, freq, direction)
         return self
+
+    def refine(self):
+        """The next level of a uniform hierarchy (every cell split into 2 x 2 x 2 by its trilinear map)."""
+        if self.verts is None:
+            raise ValueError("refine() needs a mesh built from a vertex array (Mesh(...) or from_synth)")
+        return Mesh(2 * self.nx, 2 * self.ny, 2 * self.nz,
+                    cw_mesh_refine_vertices(self.nx, self.ny, self.nz, self.verts))
 
     def close(self):
         if self.handle:

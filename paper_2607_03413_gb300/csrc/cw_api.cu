@@ -757,6 +757,52 @@ cw_status cw_mesh_create_box(int nx, int ny, int nz, double perturb, const int *
     return cw_mesh_create(nx, ny, nz, v.data(), out);
 }
 
+cw_status cw_mesh_refine_vertices(int nx, int ny, int nz, const double *verts, double *out)
+{
+    if (!verts || !out) return fail(CW_ERR_ARG, "cw_mesh_refine_vertices: NULL pointer");
+    if (nx < 1 || ny < 1 || nz < 1 || 2 * (int64_t)nx > kMaxCellsPerDir || 2 * (int64_t)ny > kMaxCellsPerDir ||
+        2 * (int64_t)nz > kMaxCellsPerDir || 8 * (int64_t)nx * ny * nz > (int64_t)1 << 31)
+        return fail(CW_ERR_ARG, "cw_mesh_refine_vertices: sizes outside the mesh limits after refinement");
+    // the parent cell's trilinear map at the half points is separable: along each axis in turn keep
+    // the vertex rows and insert the midpoint of every pair of neighbours
+    int64_t dims[3] = {(int64_t)nx + 1, (int64_t)ny + 1, (int64_t)nz + 1};
+    std::vector<double> a, b;
+    try {
+        a.assign(verts, verts + dims[0] * dims[1] * dims[2] * 3);
+    } catch (const std::bad_alloc &) {
+        return fail(CW_ERR_OOM, "cw_mesh_refine_vertices: host allocation failed");
+    }
+    for (int ax = 0; ax < 3; ++ax) {
+        int64_t nd[3] = {dims[0], dims[1], dims[2]};
+        nd[ax] = 2 * dims[ax] - 1;
+        try {
+            b.resize((size_t)(nd[0] * nd[1] * nd[2] * 3));
+        } catch (const std::bad_alloc &) {
+            return fail(CW_ERR_OOM, "cw_mesh_refine_vertices: host allocation failed");
+        }
+        for (int64_t z = 0; z < nd[2]; ++z)
+            for (int64_t y = 0; y < nd[1]; ++y)
+                for (int64_t x = 0; x < nd[0]; ++x) {
+                    int64_t s[3] = {x, y, z};
+                    const int64_t o = s[ax];
+                    s[ax] = o / 2;
+                    const double *lo = &a[((s[2] * dims[1] + s[1]) * dims[0] + s[0]) * 3];
+                    double *d = &b[((z * nd[1] + y) * nd[0] + x) * 3];
+                    if (o % 2 == 0) {
+                        for (int c = 0; c < 3; ++c) d[c] = lo[c];
+                    } else {
+                        s[ax] = o / 2 + 1;
+                        const double *hi = &a[((s[2] * dims[1] + s[1]) * dims[0] + s[0]) * 3];
+                        for (int c = 0; c < 3; ++c) d[c] = 0.5 * (lo[c] + hi[c]);
+                    }
+                }
+        a.swap(b);
+        dims[ax] = nd[ax];
+    }
+    std::memcpy(out, a.data(), a.size() * sizeof(double));
+    return CW_OK;
+}
+
 cw_status cw_mesh_destroy(cw_mesh mh)
 {
     Mesh *m = reinterpret_cast<Mesh *>(mh);

@@ -113,3 +113,24 @@ def test_binding_checks_vector_lengths_and_dtypes():
         cw.Batch([op], [1, 1], [good], [good])
     with pytest.raises(TypeError):
         cw.Batch([op], [1], [good], [torch.zeros(10, dtype=torch.bfloat16)])
+
+
+@pytest.mark.parametrize("perturb", [0.0, 0.3])
+def test_mesh_refine_vertices_host(lib, perturb):
+    """cw_mesh_refine_vertices (host only) gives the input generator's refinement bit for bit: the
+    old vertices kept, midpoints of neighbours inserted axis by axis (pinned by closed forms in the
+    multigrid oracle tests)."""
+    import numpy as np
+
+    import paper_2607_03413_gb300 as pkg
+    import synth
+    m = synth.box_mesh(3, 2, 4, perturb=perturb)
+    out = pkg.cw_mesh_refine_vertices(m.nx, m.ny, m.nz, m.verts)
+    assert np.array_equal(out, synth.refine(m).verts)
+    twice = pkg.cw_mesh_refine_vertices(6, 4, 8, out)
+    assert np.array_equal(twice, synth.refine(synth.refine(m)).verts)
+    L = pkg.load()
+    dummy = (ctypes.c_double * 3)()
+    p = ctypes.cast(dummy, ctypes.c_void_p)
+    assert L.cw_mesh_refine_vertices(40000, 1, 1, p, p) == pkg.CW_ERR_ARG  # 80000 cells in x
+    assert L.cw_mesh_refine_vertices(1, 1, 1, None, p) == pkg.CW_ERR_ARG
