@@ -12,7 +12,9 @@ Pieces:
     the interior DoFs (homogeneous Dirichlet), plus a sparse direct solve;
   * ``oracle.mg``: the geometric multigrid of a uniform mesh hierarchy (Sec. 3 and 5): cell-wise
     transfers, the cell-wise damped Jacobi smoother in its literal and fused forms, the V-cycle and
-    the V-cycle-preconditioned CG, beside the classical assembled V-cycle they are equivalent to.
+    the V-cycle-preconditioned CG, beside the classical assembled V-cycle they are equivalent to;
+  * ``oracle.dist``: the DSS and the Jacobi-PCG of a mesh split into z-slabs over torch.distributed
+    ranks (face-layer exchange per slab interface, sums over ranks for the inner products).
 """
 import ctypes
 import os
