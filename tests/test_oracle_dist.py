@@ -59,3 +59,35 @@ def test_distributed_dss_and_pcg(orc, world):
         got = np.concatenate([res[r][1][k] for r in range(world)])
         ref = orc.gather(mesh, P, its[k])
         assert np.abs(got - ref).max() <= 1e-10 * max(np.abs(ref).max(), 1e-300), k
+
+
+def _lost_rank_main(rank, world, port, out):
+    import datetime
+
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:  # this rank leaves between steps, before the exchange, without a word
+        out[rank] = "left"
+        return
+    from oracle import dist as od
+    mesh = mesh_case()
+    slab = od.Slab(mesh, rank, world)
+    try:
+        od.dss(slab, P, slab.part(synth.cellwise_random(mesh, P, seed=1), P))
+        out[rank] = "completed"
+    except Exception as e:  # the lost peer surfaces as an error of the exchange, not a hang
+        out[rank] = "error: " + type(e).__name__
+
+
+@pytest.mark.timeout(180)
+def test_lost_rank_is_reported_not_hung(orc):
+    """Failure detection on the host: a rank that leaves before the face-layer exchange makes its
+    neighbour's exchange fail with an error (peer closed, or the process-group timeout)."""
+    import torch.multiprocessing as mp
+    port = _free_port()
+    with mp.get_context("spawn").Manager() as m:
+        out = m.dict()
+        mp.spawn(_lost_rank_main, args=(2, port, out), nprocs=2, join=True)
+        res = dict(out)
+    assert res[1] == "left" and res[0].startswith("error"), res
