@@ -415,8 +415,26 @@ class Operator:
     def variant(self):
         return cw_op_get_variant(self.handle)
 
-    def autotune(self, x, y, reps=5):
-        return cw_op_autotune(self.handle, self._cw(x, "autotune: x"), self._cw(y, "autotune: y"), reps)
+    def autotune(self, x, y, reps=5, cache=None):
+        """Time every kernel variant and keep the fastest; returns its time per apply in ms. With a
+        ``TuneCache`` (or a path to one) an earlier choice for the same device, operator and size is
+        set without timing (the returned time is then the cached one)."""
+        self._cw(x, "autotune: x")
+        self._cw(y, "autotune: y")
+        if cache is None:
+            return cw_op_autotune(self.handle, x, y, reps)
+        from .tune_cache import TuneCache, device_name
+        tc = cache if isinstance(cache, TuneCache) else TuneCache(cache)
+        key = tc.key("op", device_name(), self.degree, self.kind, self.geom, self.prec, self.L)
+        hit = tc.get(key)
+        if hit is not None:
+            self.set_variant(hit["cells_per_cta"], hit["stage"])
+            return hit["ms"]
+        ms = cw_op_autotune(self.handle, x, y, reps)
+        cpb, stage, choices = self.variant()
+        # 0 = the degree's default tile (the only value some operators accept back)
+        tc.put(key, {"cells_per_cta": 0 if cpb == choices[0] else cpb, "stage": stage, "ms": ms})
+        return ms
 
     def dss(self, v, average=False):
         cw_dss(self.handle, self._cw(v, "dss: v"), CW_DSS_AVERAGE if average else CW_DSS_SUM)
@@ -465,15 +483,36 @@ class Batch:
             _vec(y, r * o.L, o.vec_dtype, f"Batch: ys[{i}]")
         self.handle = cw_batch_create([o.handle for o in self.ops], self.nrhs, self.xs, self.ys)
         self.values = cw_batch_values(self.handle)
+        self.mode = CW_BATCH_GROUPED
 
     def launch(self, graph=False, stream=None):
         (cw_batch_graph_launch if graph else cw_batch_launch)(self.handle, stream)
 
-    def autotune(self, reps=3):
-        return cw_batch_autotune(self.handle, reps)
+    def autotune(self, reps=3, cache=None, mode=None):
+        """Per-degree autotuning of the current mode (``mode`` sets it first); returns the batch time
+        in ms. With a ``TuneCache`` (or a path) an earlier choice for the same device, mode and batch
+        composition is set without timing."""
+        if mode is not None:
+            self.set_mode(mode)
+        if cache is None:
+            return cw_batch_autotune(self.handle, reps)
+        from .tune_cache import TuneCache, device_name
+        tc = cache if isinstance(cache, TuneCache) else TuneCache(cache)
+        comp = sorted((o.degree, o.kind, o.prec, o.L, r) for o, r in zip(self.ops, self.nrhs))
+        key = tc.key("batch", device_name(), self.mode, comp)
+        hit = tc.get(key)
+        if hit is not None:
+            for degree, variant in hit["variants"].items():
+                self.set_variant(int(degree), variant)
+            return hit["ms"]
+        ms = cw_batch_autotune(self.handle, reps)
+        variants = {str(d): self.variant(d)[0] for d in sorted({o.degree for o in self.ops})}
+        tc.put(key, {"variants": variants, "ms": ms})
+        return ms
 
     def set_mode(self, mode):
         cw_batch_set_mode(self.handle, mode)
+        self.mode = mode
 
     def set_variant(self, degree, variant):
         cw_batch_set_variant(self.handle, degree, variant)

@@ -134,3 +134,65 @@ def test_mesh_refine_vertices_host(lib, perturb):
     p = ctypes.cast(dummy, ctypes.c_void_p)
     assert L.cw_mesh_refine_vertices(40000, 1, 1, p, p) == pkg.CW_ERR_ARG  # 80000 cells in x
     assert L.cw_mesh_refine_vertices(1, 1, 1, None, p) == pkg.CW_ERR_ARG
+
+
+def test_tune_cache_round_trip_and_replay(tmp_path, monkeypatch):
+    """The JSON tuning cache: atomic save, reload, foreign files ignored; a cache hit sets the stored
+    variant without timing, a miss times once and stores the choice (tuner calls faked on the host)."""
+    import json
+
+    import torch
+
+    import paper_2607_03413_gb300 as cw
+    from paper_2607_03413_gb300 import tune_cache
+    path = tmp_path / "tune.json"
+    tc = tune_cache.TuneCache(str(path))
+    assert tc.entries == {}
+    tc.put(tc.key("op", "dev", 4, 3), {"cells_per_cta": 0, "stage": 2, "ms": 1.5})
+    assert json.loads(path.read_text())["entries"] and not list(tmp_path.glob("*.tmp*"))
+    assert tune_cache.TuneCache(str(path)).get(tc.key("op", "dev", 4, 3))["stage"] == 2
+    path.write_text("not json")
+    assert tune_cache.TuneCache(str(path)).entries == {}
+
+    calls = []
+    monkeypatch.setattr(tune_cache, "device_name", lambda: "fake-gpu")
+    monkeypatch.setattr(cw, "cw_op_autotune", lambda h, x, y, reps: calls.append("tune") or 0.25)
+    monkeypatch.setattr(cw, "cw_op_get_variant", lambda h: (16, 2, (8, 16)))
+    monkeypatch.setattr(cw, "cw_op_set_variant", lambda h, c, s: calls.append(("set", c, s)))
+    op = cw.Operator.__new__(cw.Operator)
+    op.handle, op.L, op.NG, op.prec = None, 10, 27, cw.CW_PREC_F64
+    op.degree, op.kind, op.geom = 4, cw.CW_LAPLACE_MASS, cw.CW_GEOM_METRIC
+    x = torch.zeros(10, dtype=torch.float64)
+    y = torch.zeros(10, dtype=torch.float64)
+    path2 = str(tmp_path / "ops.json")
+    assert op.autotune(x, y, cache=path2) == 0.25 and calls == ["tune"]
+    assert op.autotune(x, y, cache=path2) == 0.25 and calls == ["tune", ("set", 16, 2)]
+    op.L = 20  # another size is another entry
+    with pytest.raises(ValueError):
+        op.autotune(x, y, cache=path2)  # (vectors of the old length are rejected first)
+    x2, y2 = torch.zeros(20, dtype=torch.float64), torch.zeros(20, dtype=torch.float64)
+    op.autotune(x2, y2, cache=path2)
+    assert calls[-1] == "tune" and len(tune_cache.TuneCache(path2).entries) == 2
+
+
+def test_batch_tune_cache_replay(tmp_path, monkeypatch):
+    """Batch.autotune with a cache: the per-degree variants of a batch composition are stored after
+    one timing run and set again without timing (tuner calls faked on the host)."""
+    import types
+
+    import paper_2607_03413_gb300 as cw
+    from paper_2607_03413_gb300 import tune_cache
+    calls = []
+    monkeypatch.setattr(tune_cache, "device_name", lambda: "fake-gpu")
+    monkeypatch.setattr(cw, "cw_batch_autotune", lambda h, reps: calls.append("tune") or 3.0)
+    monkeypatch.setattr(cw, "cw_batch_get_variant", lambda h, d: ({2: 4, 5: 1}[d], 8))
+    monkeypatch.setattr(cw, "cw_batch_set_variant", lambda h, d, v: calls.append(("set", d, v)))
+    B = cw.Batch.__new__(cw.Batch)
+    B.handle, B.mode, B.nrhs = None, cw.CW_BATCH_GROUPED, [2, 1, 1]
+    B.ops = [types.SimpleNamespace(degree=d, kind=1, prec=0, L=L) for d, L in ((5, 100), (2, 27), (2, 54))]
+    path = str(tmp_path / "batch.json")
+    assert B.autotune(cache=path) == 3.0 and calls == ["tune"]
+    calls.clear()
+    assert B.autotune(cache=path) == 3.0
+    assert sorted(calls) == [("set", 2, 4), ("set", 5, 1)]
+    B.handle = None  # nothing to destroy
