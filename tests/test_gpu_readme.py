@@ -9,7 +9,7 @@ pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_readme_quick_start_runs():
+def test_readme_quick_start_runs(tmp_path, monkeypatch):
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -18,6 +18,7 @@ def test_readme_quick_start_runs():
     text = open(os.path.join(ROOT, "README.md")).read()
     block = re.search(r"```python\n(.*?)```", text, re.S).group(1)
     ns = {}
+    monkeypatch.chdir(tmp_path)  # files the example writes (its tuning cache) land here
     exec(compile(block, "README.md", "exec"), ns)
     torch.cuda.synchronize()
     cw = ns["cw"]
@@ -27,3 +28,4 @@ def test_readme_quick_start_runs():
     for o, x, y in zip(ns["ops"], ns["xs"], ns["ys"]):
         for r in range(x.shape[0]):
             assert torch.equal(y[r], o.apply(x[r]))
+    assert (tmp_path / "tune.json").exists()
