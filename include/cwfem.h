@@ -132,6 +132,14 @@ cw_status cw_mesh_create(int nx, int ny, int nz, const double *verts_host, cw_me
 cw_status cw_mesh_create_box(int nx, int ny, int nz, double perturb, const int *freq, const double *direction,
                              cw_mesh *out);
 /*
+ * The library's 1D rules on [0,1] for a degree p in 1..7 (host only): the p+1 Gauss-Lobatto nodes of
+ * the nodal basis (local DoF i of a cell along an axis sits at gll_nodes[i] of the reference cell,
+ * Sec. 2), and the p+1 Gauss points and weights of the operators' quadrature. Each output (may be
+ * NULL) receives p+1 doubles. CW_ERR_ARG for a degree outside 1..7.
+ */
+cw_status cw_rules_1d(int degree, double *gll_nodes, double *gauss_points, double *gauss_weights);
+
+/*
  * Vertex array of the uniform refinement of a mesh (the next level of a multigrid hierarchy, Sec. 3:
  * every cell split into 2 x 2 x 2 children by its own trilinear map, so the finite-element spaces of
  * the two meshes are nested). verts: the (nx+1)(ny+1)(nz+1)*3 doubles of cw_mesh_create's layout;

@@ -35,7 +35,7 @@ EXPORTED = [
     "cw_op_get_variant", "cw_op_autotune", "cw_cg_solve_noalloc", "cw_batch_create", "cw_batch_destroy",
     "cw_batch_values", "cw_batch_launch", "cw_batch_graph_launch", "cw_batch_set_variant",
     "cw_batch_get_variant", "cw_batch_autotune", "cw_batch_set_mode", "cw_apply_batched", "cw_apply_host",
-    "cw_mesh_refine_vertices",
+    "cw_mesh_refine_vertices", "cw_rules_1d",
 ]
 
 
@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
                               i32, vp], i32),
         "cw_apply_host": ([vp, vp, vp, i32, vp], i32),
         "cw_mesh_refine_vertices": ([i32, i32, i32, vp, vp], i32),
+        "cw_rules_1d": ([i32, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -164,6 +165,14 @@ def cw_mesh_refine_vertices(nx, ny, nz, verts):
     _check(load().cw_mesh_refine_vertices(nx, ny, nz, v.ctypes.data_as(ctypes.c_void_p),
                                           out.ctypes.data_as(ctypes.c_void_p)), "cw_mesh_refine_vertices")
     return out
+
+
+def cw_rules_1d(degree):
+    """(Gauss-Lobatto nodes, Gauss points, Gauss weights) on [0, 1], p+1 each (host only)."""
+    import numpy as np
+    out = [np.empty(degree + 1) for _ in range(3)]
+    _check(load().cw_rules_1d(degree, *[a.ctypes.data_as(ctypes.c_void_p) for a in out]), "cw_rules_1d")
+    return tuple(out)
 
 
 def cw_mesh_destroy(h):

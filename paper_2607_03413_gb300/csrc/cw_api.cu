@@ -757,6 +757,19 @@ cw_status cw_mesh_create_box(int nx, int ny, int nz, double perturb, const int *
     return cw_mesh_create(nx, ny, nz, v.data(), out);
 }
 
+cw_status cw_rules_1d(int degree, double *gll_nodes, double *gauss_points, double *gauss_weights)
+{
+    if (degree < 1 || degree > kMaxDegree) return fail(CW_ERR_ARG, "cw_rules_1d: degree must be in 1..7");
+    Tables1D t;
+    build_tables(degree, t);
+    for (int i = 0; i < t.n; ++i) {
+        if (gll_nodes) gll_nodes[i] = t.gll[i];
+        if (gauss_points) gauss_points[i] = t.xq[i];
+        if (gauss_weights) gauss_weights[i] = t.wq[i];
+    }
+    return CW_OK;
+}
+
 cw_status cw_mesh_refine_vertices(int nx, int ny, int nz, const double *verts, double *out)
 {
     if (!verts || !out) return fail(CW_ERR_ARG, "cw_mesh_refine_vertices: NULL pointer");

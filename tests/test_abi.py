@@ -196,3 +196,22 @@ def test_batch_tune_cache_replay(tmp_path, monkeypatch):
     assert B.autotune(cache=path) == 3.0
     assert sorted(calls) == [("set", 2, 4), ("set", 5, 1)]
     B.handle = None  # nothing to destroy
+
+
+@pytest.mark.parametrize("p", range(1, 8))
+def test_library_rules_match_the_oracle(lib, orc, p):
+    """The library's own 1D rules (long-double Newton, host only) against the oracle's pinned rules:
+    the Gauss-Lobatto nodes of the layout and the Gauss rule of the operators."""
+    import numpy as np
+
+    import paper_2607_03413_gb300 as pkg
+    gll, xq, wq = pkg.cw_rules_1d(p)
+    x_ref, w_ref = orc.gauss(p + 1)
+    assert np.abs(gll - orc.gll(p)).max() < 1e-15
+    assert np.abs(xq - x_ref).max() < 1e-15 and np.abs(wq - w_ref).max() < 1e-15
+
+
+def test_library_rules_argument_errors(lib):
+    import paper_2607_03413_gb300 as pkg
+    assert pkg.load().cw_rules_1d(0, None, None, None) == pkg.CW_ERR_ARG
+    assert pkg.load().cw_rules_1d(8, None, None, None) == pkg.CW_ERR_ARG
