@@ -140,6 +140,15 @@ cw_status cw_mesh_create_box(int nx, int ny, int nz, double perturb, const int *
 cw_status cw_rules_1d(int degree, double *gll_nodes, double *gauss_points, double *gauss_weights);
 
 /*
+ * The library's 1D matrices for degree p in 1..7 (host only), each (p+1) x (p+1), row-major, output
+ * pointers may be NULL: B[q][m] = l_m(x_q) and Bd[q][m] = l_m'(x_q) (the Gauss-Lobatto basis at the
+ * Gauss points), D[q][r] = g_r'(x_q) (the collocation derivative of the Lagrange basis g on the Gauss
+ * points), M1[i][j] = int_0^1 l_i l_j and K1[i][j] = int_0^1 l_i' l_j' (the 1D mass and stiffness
+ * matrices of the factored Cartesian form, Sec. 6). CW_ERR_ARG for a degree outside 1..7.
+ */
+cw_status cw_basis_1d(int degree, double *B, double *Bd, double *D, double *M1, double *K1);
+
+/*
  * Vertex array of the uniform refinement of a mesh (the next level of a multigrid hierarchy, Sec. 3:
  * every cell split into 2 x 2 x 2 children by its own trilinear map, so the finite-element spaces of
  * the two meshes are nested). verts: the (nx+1)(ny+1)(nz+1)*3 doubles of cw_mesh_create's layout;

@@ -35,7 +35,7 @@ EXPORTED = [
     "cw_op_get_variant", "cw_op_autotune", "cw_cg_solve_noalloc", "cw_batch_create", "cw_batch_destroy",
     "cw_batch_values", "cw_batch_launch", "cw_batch_graph_launch", "cw_batch_set_variant",
     "cw_batch_get_variant", "cw_batch_autotune", "cw_batch_set_mode", "cw_apply_batched", "cw_apply_host",
-    "cw_mesh_refine_vertices", "cw_rules_1d",
+    "cw_mesh_refine_vertices", "cw_rules_1d", "cw_basis_1d",
 ]
 
 
@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH):
         "cw_apply_host": ([vp, vp, vp, i32, vp], i32),
         "cw_mesh_refine_vertices": ([i32, i32, i32, vp, vp], i32),
         "cw_rules_1d": ([i32, vp, vp, vp], i32),
+        "cw_basis_1d": ([i32, vp, vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -172,6 +173,16 @@ def cw_rules_1d(degree):
     import numpy as np
     out = [np.empty(degree + 1) for _ in range(3)]
     _check(load().cw_rules_1d(degree, *[a.ctypes.data_as(ctypes.c_void_p) for a in out]), "cw_rules_1d")
+    return tuple(out)
+
+
+def cw_basis_1d(degree):
+    """(B, Bd, D, M1, K1), each (p+1) x (p+1): basis and derivative at the Gauss points, collocation
+    derivative on the Gauss points, 1D mass and stiffness matrices (host only)."""
+    import numpy as np
+    n = degree + 1
+    out = [np.empty((n, n)) for _ in range(5)]
+    _check(load().cw_basis_1d(degree, *[a.ctypes.data_as(ctypes.c_void_p) for a in out]), "cw_basis_1d")
     return tuple(out)
 
 

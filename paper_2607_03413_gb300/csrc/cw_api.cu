@@ -770,6 +770,23 @@ cw_status cw_rules_1d(int degree, double *gll_nodes, double *gauss_points, doubl
     return CW_OK;
 }
 
+cw_status cw_basis_1d(int degree, double *B, double *Bd, double *D, double *M1, double *K1)
+{
+    if (degree < 1 || degree > kMaxDegree) return fail(CW_ERR_ARG, "cw_basis_1d: degree must be in 1..7");
+    Tables1D t;
+    build_tables(degree, t);
+    for (int r = 0; r < t.n; ++r)
+        for (int c = 0; c < t.n; ++c) {
+            const int o = r * t.n + c;
+            if (B) B[o] = t.B[r][c];
+            if (Bd) Bd[o] = t.Bd[r][c];
+            if (D) D[o] = t.D[r][c];
+            if (M1) M1[o] = t.M1[r][c];
+            if (K1) K1[o] = t.K1[r][c];
+        }
+    return CW_OK;
+}
+
 cw_status cw_mesh_refine_vertices(int nx, int ny, int nz, const double *verts, double *out)
 {
     if (!verts || !out) return fail(CW_ERR_ARG, "cw_mesh_refine_vertices: NULL pointer");

@@ -215,3 +215,23 @@ def test_library_rules_argument_errors(lib):
     import paper_2607_03413_gb300 as pkg
     assert pkg.load().cw_rules_1d(0, None, None, None) == pkg.CW_ERR_ARG
     assert pkg.load().cw_rules_1d(8, None, None, None) == pkg.CW_ERR_ARG
+
+
+@pytest.mark.parametrize("p", range(1, 8))
+def test_library_basis_matrices_match_the_oracle(lib, orc, p):
+    """The library's 1D matrices against the same quantities formed from the oracle's pinned
+    primitives (Lagrange basis by the product formula, Gauss rule): basis and derivative at the Gauss
+    points, the collocation derivative on the Gauss points, the 1D mass and stiffness matrices."""
+    import numpy as np
+
+    import paper_2607_03413_gb300 as pkg
+    B, Bd, D, M1, K1 = pkg.cw_basis_1d(p)
+    xi = orc.gll(p)
+    xq, wq = orc.gauss(p + 1)
+    LB = np.array([orc.lagrange(xi, x)[0] for x in xq])
+    LBd = np.array([orc.lagrange(xi, x)[1] for x in xq])
+    LD = np.array([orc.lagrange(xq, x)[1] for x in xq])
+    assert np.abs(B - LB).max() < 1e-13 and np.abs(Bd - LBd).max() < 1e-12
+    assert np.abs(D - LD).max() < 1e-11
+    assert np.abs(M1 - LB.T @ np.diag(wq) @ LB).max() < 1e-14
+    assert np.abs(K1 - LBd.T @ np.diag(wq) @ LBd).max() < 1e-12 * max(1.0, np.abs(K1).max())
