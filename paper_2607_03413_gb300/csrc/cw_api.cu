@@ -1115,7 +1115,10 @@ cw_status cw_op_autotune(cw_op oh, const void *x, void *y, int reps, void *strea
     cpb_choices(op->p, ch);
     cudaEvent_t e0, e1;
     CW_CUDA_TRY(cudaEventCreate(&e0));
-    CW_CUDA_TRY(cudaEventCreate(&e1));
+    if (const cudaError_t ee = cudaEventCreate(&e1); ee != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ee, "cw_op_autotune");
+    }
     float best = 1e30f;
     int bc = 0, bs = op->stage;
     // curved: both tile sizes x three staging modes; recomputed geometry: default tile, direct or
