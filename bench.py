@@ -158,6 +158,61 @@ def max_over_ranks(v, world):
     return float(t.item())
 
 
+# ------------------------------------------------------------- oracle error samples ----
+class SampleBook:
+    """GPU outputs of the timed legs on a seeded sample of cells, kept so that the CPU-oracle leg can
+    report each result's error against the FP64 oracle after the GPU work (the oracle is never run
+    inside the GPU arm). Every entry is (where in the JSON line, mesh size N, degree p, kind, input
+    seed, sampled cells, sampled LOCAL output)."""
+
+    def __init__(self, ncells=48):
+        self.ncells = ncells
+        self.entries = []
+
+    def cells(self, N, seed):
+        rng = np.random.default_rng(1000 + seed)
+        E = N ** 3
+        pick = rng.choice(E, min(self.ncells, E), replace=False)
+        return np.unique(np.concatenate([pick, [0, N - 1, E - N, E - 1]]))
+
+    def add(self, where, N, p, kind, seed, y):
+        """y: the LOCAL output of the operator (device tensor, any precision)."""
+        import torch
+        cells = self.cells(N, p)
+        n3 = (p + 1) ** 3
+        idx = torch.from_numpy(cells).to(y.device)
+        got = y.view(-1, n3).index_select(0, idx).to(torch.float64).cpu().numpy()
+        self.entries.append((where, N, p, kind, seed, cells, got))
+
+
+def oracle_errors(book, out):
+    """Relative error max|y - y_oracle| / max|y_oracle| of every sampled output against the oracle's
+    LOCAL apply (explicit element matrices) on the same cells and the same input, written beside the
+    result it belongs to as ``rel_err_vs_oracle``."""
+    import oracle
+    oracle.build()
+    refs = {}
+    for where, N, p, kind, seed, cells, got in book.entries:
+        key = (N, p, kind, seed)
+        if key not in refs:
+            mesh = synth.box_mesh(N, perturb=0.1)
+            n3 = (p + 1) ** 3
+            ug = synth.global_vector(mesh, p, seed=seed)
+            gidx = oracle.global_index(mesh, p).reshape(mesh.ncells, n3)
+            x = np.zeros(mesh.ncells * n3)
+            x.reshape(mesh.ncells, n3)[cells] = ug[gidx[cells]]
+            del gidx, ug
+            refs[key] = oracle.apply_local(mesh, p, kind, x, cells)
+            del x
+        ref = refs[key]
+        err = float(np.abs(got - ref).max() / np.abs(ref).max())
+        d = out
+        for k in where:
+            d = d[k]
+        d["rel_err_vs_oracle"] = err
+        d["oracle_sample_cells"] = int(len(cells))
+
+
 # ---------------------------------------------------------------------------- GPU arm ----
 def event_pair():
     import torch
@@ -266,6 +321,9 @@ def gpu_arm(args, rank, local, world):
     torch.cuda.synchronize()
     step_ms = max_over_ranks(step_ms, world)
     clocks = clk.summary()
+    book = args.book
+    if book is not None:
+        book.add(("headline",), args.cells, P, KIND, rank, y)  # y holds the LOCAL output after timing
     units = op.L * world
     value = units / (step_ms * 1e-3)
 
@@ -323,6 +381,7 @@ def gpu_arm(args, rank, local, world):
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": 4 * args.steps,
+        "headline": {"what": "the timed step's operator, LOCAL output of the same kernel on the same input"},
     }
     del x, y
     op.close()
@@ -339,6 +398,8 @@ def gpu_arm(args, rank, local, world):
         gbs = bytes_per_value(prec, KIND) * o.L / (km * 1e-3) / 1e9
         mixed[name] = {"dofs_per_s": o.L / (sm * 1e-3), "ms_per_step": sm, "apply_kernel_ms": km,
                        "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+        if book is not None:
+            book.add(("mixed", name), args.cells, P, KIND, rank, yy)
         o.close()
     if mixed:
         out["mixed"] = mixed
@@ -358,6 +419,8 @@ def gpu_arm(args, rank, local, world):
         gbs = (2 * sv + 21 * sg / n ** 3) * o.L / (km * 1e-3) / 1e9
         recomp[name] = {"dofs_per_s": o.L / (sm * 1e-3), "ms_per_step": sm, "apply_kernel_ms": km,
                         "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4), "variant": o.variant()}
+        if book is not None:
+            book.add(("recomputed_metric", name), args.cells, P, KIND, rank, yy)
         o.close()
     if recomp:
         out["recomputed_metric"] = recomp
@@ -373,6 +436,8 @@ def gpu_arm(args, rank, local, world):
             o.autotune(xx, yy, reps=3)
             sm, km = time_apply(cw, o, xx, yy, args.steps, args.warmup, stream)
             kinds[kname][gname] = {"dofs_per_s": o.L / (sm * 1e-3), "ms_per_step": sm, "apply_kernel_ms": km}
+            if book is not None:
+                book.add(("kinds_f64", kname, gname), args.cells, P, kind, rank, yy)
             o.close()
     if kinds:
         out["kinds_f64"] = kinds
@@ -427,6 +492,8 @@ def degree_sweep(cw, stream, hbm, args):
             sm, km = time_apply(cw, o, x, y, max(3, args.steps // 2), 2, stream, assemble=False)
             gbs = bytes_per_value(prec, 1) * o.L / (km * 1e-3) / 1e9
             row[name] = {"dofs_per_s": o.L / (km * 1e-3), "hbm_frac": round(gbs / hbm, 4)}
+            if args.book is not None:
+                args.book.add(("sweep", f"p{p}", name), N, p, 1, 0, y)
             del x, y
             o.close()
         res[f"p{p}"] = {"cells": N ** 3, "values": N ** 3 * (p + 1) ** 3, **row}
@@ -522,7 +589,9 @@ def cg_bench(cw, args):
     b = op.load_vector(0)
     u = torch.empty_like(b)
     res = {"workload": f"Poisson Q{p}, {N}^3 curved cells, {op.L} cell-wise values, Jacobi-PCG, rtol 1e-10",
-           "unit": "s"}
+           "unit": "s",
+           "tolerance_measure": "||m G^T(b - A u)|| / ||m G^T b|| with A the IEEE FP64 operator (native FP64 "
+                                "arithmetic, metric stored as IEEE doubles)"}
     names = [("ir_f32", cw.CW_CG_IR_F32), ("ir_bf16_metric", cw.CW_CG_IR_BF16), ("f64_doublefloat", cw.CW_CG_F64),
              ("f64_native", cw.CW_CG_F64_NATIVE)]
     if args.cg_mode >= 0:  # one mode only (profiling cases)
@@ -533,7 +602,10 @@ def cg_bench(cw, args):
         _, st, rc = op.cg_solve(b, u, rtol=1e-10, maxit=20000, mode=mode, check=False)
         res[name] = {"seconds": st.seconds, "iterations": st.iterations, "outer": st.outer_iterations,
                      "rel_residual": st.rel_residual, "status": int(rc),
-                     "ms_per_iteration": 1e3 * st.seconds / max(1, st.iterations)}
+                     "ms_per_iteration": 1e3 * st.seconds / max(1, st.iterations),
+                     # the returned u's residual measured again with each FP64 operator of the library
+                     "rel_residual_ieee_fp64_operator": op.residual(b, u, cw.CW_PREC_F64_NATIVE),
+                     "rel_residual_doublefloat_operator": op.residual(b, u, cw.CW_PREC_F64)}
     if len(names) == 4:
         res["speedup_ir_f32_vs_f64_native"] = res["f64_native"]["seconds"] / res["ir_f32"]["seconds"]
         res["speedup_ir_f32_vs_f64_doublefloat"] = res["f64_doublefloat"]["seconds"] / res["ir_f32"]["seconds"]
@@ -643,8 +715,10 @@ def main():
             print(json.dumps(out))
         return
     rank, local, world = dist_init(args)
+    args.book = SampleBook() if (rank == 0 and world == 1 and args.cpu) else None
     out = gpu_arm(args, rank, local, world)
     if rank == 0 and world == 1 and args.cpu:
+        oracle_errors(args.book, out)
         rate, ncell, dt = oracle_sample_rate(args.cpu_seconds)
         out["cpu_baseline"] = {"value": rate, "unit": "DoF/s", "cores": cores(), "kind": "oracle",
                                "sample": f"{ncell} random cells of the 64^3 curved mesh, K+M p=4, "

@@ -73,8 +73,10 @@ typedef enum {
                                from 21 trilinear-map coefficients per cell (Sec. 6, J and det J) */
 
 /* precisions (vector storage / metric storage / arithmetic) */
-#define CW_PREC_F64 0        /* FP64 / FP64 / double-float (FP32 pair, ~47-bit) arithmetic */
-#define CW_PREC_F64_NATIVE 1 /* FP64 / FP64 / native FP64 FMA (reference speed baseline) */
+#define CW_PREC_F64 0        /* FP64 / FP64 as a rounded float pair (~48 bits) / double-float (FP32 pair,
+                                ~47-bit) arithmetic */
+#define CW_PREC_F64_NATIVE 1 /* FP64 / IEEE FP64 / native FP64 FMA: the plain IEEE FP64 operator (reference
+                                speed baseline; the operator of the solvers' outer residual) */
 #define CW_PREC_F32 2        /* FP32 / FP32 / FP32 */
 #define CW_PREC_F32_BF16G 3  /* FP32 / BF16 / FP32 */
 #define CW_PREC_BF16 4       /* BF16 / BF16 / FP32 accumulate */
@@ -92,11 +94,12 @@ typedef enum {
 #define CW_DSS_AVERAGE 1 /* v <- S_bar v = G (G^T G)^-1 G^T v */
 
 /* cg modes: every mode keeps u, b and the outer residual b - A u in FP64 (the residual evaluated
-   with the native-FP64 operator) and refines u += d with an inner Jacobi-PCG for A d = S_bar r */
+   with the IEEE FP64 operator: native FP64 arithmetic, metric stored as IEEE doubles) and refines
+   u += d with an inner Jacobi-PCG for A d = S_bar r */
 #define CW_CG_F64 0        /* inner CG in FP64 with the double-float operator */
 #define CW_CG_IR_F32 1     /* inner CG in FP32 (FP32 vectors and metric, FP64-accumulated dots) */
 #define CW_CG_IR_BF16 2    /* inner CG in FP32 with the metric stored in BF16 */
-#define CW_CG_F64_NATIVE 3 /* inner CG in FP64 with the native-FP64 operator (plain FP64 CG) */
+#define CW_CG_F64_NATIVE 3 /* inner CG in FP64 with the IEEE FP64 operator (plain FP64 CG) */
 
 typedef struct {
     int iterations;        /* total CG iterations (inner iterations summed for IR modes) */
@@ -162,8 +165,10 @@ cw_status cw_mesh_destroy(cw_mesh m);
 /*
  * Create an operator of degree p on a mesh (Sec. 2.1). Allocates and fills the geometry
  * (CW_GEOM_METRIC: ncomp values per quadrature point, ncomp = 6 Laplace, 1 mass, 7 both, stored
- * in the metric precision; CW_GEOM_RECOMPUTE: the 21 coefficients a1..a7 of each cell's trilinear
- * map, as float pairs for the FP64 precisions and floats otherwise -- no per-point storage, the
+ * in the metric precision -- rounded float pairs hi + lo for CW_PREC_F64, IEEE doubles for
+ * CW_PREC_F64_NATIVE; CW_GEOM_RECOMPUTE: the 21 coefficients a1..a7 of each cell's trilinear
+ * map, as float pairs for CW_PREC_F64, doubles for CW_PREC_F64_NATIVE and floats otherwise -- no
+ * per-point storage, the
  * metric is formed in the kernel; CW_GEOM_AFFINE: 4 doubles per cell, and the mesh must be
  * Cartesian -- CW_ERR_ARG otherwise) and the 1D tables. Curved modes check det J > 0 at every
  * quadrature point (CW_ERR_ARG otherwise). CW_ERR_UNSUPPORTED where one DSS axis pass would have
@@ -248,14 +253,26 @@ cw_status cw_load_vector(cw_op op, int which, double *b, void *stream);
  * cell-wise data from u = 0 (Sec. 4.1 Eq. (jacobi_recap); Sec. 4.4). b: FP64 cell-wise dual;
  * u: FP64 cell-wise primal output. Stops when rel_residual <= rtol or after maxit iterations
  * (CW_ERR_NOT_CONVERGED; u then holds the last iterate). mode selects the inner solver (see the
- * CW_CG_* modes); the relative residual is always measured with the native-FP64 operator. The
- * inner right-hand side is the averaged residual S_bar r (same assembly G^T r, every copy small),
- * so that rounding it to FP32 keeps the assembled residual. The first call on an op allocates the
- * solver vectors (and, for the CW_CG_IR_* modes, the FP32 inner operator). Synchronises `stream`.
- * stats may be NULL.
+ * CW_CG_* modes); the relative residual is always measured with the IEEE FP64 operator (a twin of
+ * op with precision CW_PREC_F64_NATIVE, its metric stored as doubles). The inner right-hand side
+ * is the averaged residual S_bar r (same assembly G^T r, every copy small), so that rounding it to
+ * FP32 keeps the assembled residual. The first call on an op allocates the solver vectors and the
+ * IEEE twin (and, for the CW_CG_IR_* modes, the FP32 inner operator); cw_op_device_bytes counts
+ * them. Synchronises `stream`. stats may be NULL. Errors of the inner solve (breakdown, CUDA
+ * failures) end the solve with their status.
  */
 cw_status cw_cg_solve(cw_op op, const double *b, double *u, double rtol, int maxit, int mode,
                       cw_cg_stats *stats, void *stream);
+
+/*
+ * Relative residual ||m G^T (b - A u)|| / ||m G^T b|| on interior DoFs (the measure of
+ * cw_cg_solve) of a cell-wise FP64 iterate u for the FP64 dual b, with A evaluated in precision
+ * `prec`: CW_PREC_F64_NATIVE, the IEEE FP64 operator (the twin cw_cg_solve uses), or CW_PREC_F64,
+ * the op's own double-float arithmetic on its float-pair metric. op: CW_PREC_F64 with
+ * CW_BC_DIRICHLET0 (else CW_ERR_ARG). The first call allocates the solver scratch and the IEEE
+ * twin, as cw_cg_solve does. Synchronises `stream`.
+ */
+cw_status cw_cg_residual(cw_op op, const double *b, const double *u, int prec, double *rel_residual, void *stream);
 
 /*
  * Batched apply (not in the paper): y_i = A_i x_i (LOCAL, unassembled) for nprob operators at
@@ -312,19 +329,24 @@ cw_status cw_apply_batched(const cw_op *ops, const void *const *x, void *const *
  * Allocation-free variant of cw_cg_solve. The paper has no counterpart; this entry point exists
  * for callers that must not allocate device memory while solving -- e.g. code that runs inside a
  * caller-managed memory pool or an allocator callback, a real-time loop whose memory is fixed at
- * start-up, or a host whose policy forbids cudaMalloc/cudaFree after initialisation. It performs
- * the same FP64 solve as cw_cg_solve for mode CW_CG_F64 or CW_CG_F64_NATIVE (arguments, outputs
- * and statuses as there) but takes every scratch vector from one fixed file-scope device array of
+ * start-up, or a host whose policy forbids cudaMalloc/cudaFree after initialisation. It solves the
+ * same system with the same operator, preconditioner and stopping measure as cw_cg_solve for mode
+ * CW_CG_F64 or CW_CG_F64_NATIVE (arguments, outputs and statuses as there), with three
+ * differences: the inner CG restarts at every outer refinement step (no search direction carried
+ * over), the outer loop stops after 50 steps, and both the native-arithmetic inner operator and the
+ * outer residual read the op's own float-pair metric (cw_cg_solve builds an IEEE-metric twin for
+ * them, which would need an allocation). Iteration counts and round-off may therefore differ
+ * slightly from cw_cg_solve. Every scratch vector comes from one fixed file-scope device array of
  * about 17 MB, which every GPU that loads this library holds until the process exits. It calls no
  * cudaMalloc, cudaFree or other allocating routine, creates no stream, event or graph, and runs on
  * `stream` directly, synchronising it. Limit: cw_op_cellwise_len(op) <= 262144 (2^18);
  * larger operators are rejected with CW_ERR_ARG and a message naming the limit, before any GPU
  * work. The op itself must have been created beforehand (cw_op_create allocates its geometry).
- * The first call on a device resolves the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture. All calls share the one
- * array and leave their data in it; each call re-initialises what it reads. Calls that overlap
- * on the GPU (from two streams or two threads) race on the array and must be serialised by the
- * caller. stats->seconds is host wall time.
+ * Every call resolves the array's device address (cudaGetSymbolAddress) with the caller's device
+ * current; the first call on a device may load the library's device code there, so make it before
+ * any stream capture. All calls share the one array and leave their data in it; each call
+ * re-initialises what it reads. Calls that overlap on the GPU (from two streams or two threads)
+ * race on the array and must be serialised by the caller. stats->seconds is host wall time.
  */
 cw_status cw_cg_solve_noalloc(cw_op op, const double *b, double *u, double rtol, int maxit, int mode,
                               cw_cg_stats *stats, void *stream);

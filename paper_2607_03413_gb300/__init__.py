@@ -35,7 +35,7 @@ EXPORTED = [
     "cw_op_get_variant", "cw_op_autotune", "cw_cg_solve_noalloc", "cw_batch_create", "cw_batch_destroy",
     "cw_batch_values", "cw_batch_launch", "cw_batch_graph_launch", "cw_batch_set_variant",
     "cw_batch_get_variant", "cw_batch_autotune", "cw_batch_set_mode", "cw_apply_batched", "cw_apply_host",
-    "cw_mesh_refine_vertices", "cw_rules_1d", "cw_basis_1d",
+    "cw_mesh_refine_vertices", "cw_rules_1d", "cw_basis_1d", "cw_cg_residual",
 ]
 
 
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
         "cw_mesh_refine_vertices": ([i32, i32, i32, vp, vp], i32),
         "cw_rules_1d": ([i32, vp, vp, vp], i32),
         "cw_basis_1d": ([i32, vp, vp, vp, vp, vp], i32),
+        "cw_cg_residual": ([vp, vp, vp, i32, ctypes.POINTER(dbl), vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -252,6 +253,14 @@ def cw_cg_solve(op, b, u, rtol=1e-10, maxit=10000, mode=CW_CG_F64, stream=None, 
     if check and rc not in (CW_OK,):
         raise CwError(rc, "cw_cg_solve")
     return rc, st
+
+
+def cw_cg_residual(op, b, u, prec=CW_PREC_F64_NATIVE, stream=None):
+    """Relative residual ||m G^T(b - A u)|| / ||m G^T b|| with A in precision ``prec``
+    (CW_PREC_F64_NATIVE: the IEEE FP64 operator; CW_PREC_F64: double-float on the float-pair metric)."""
+    r = ctypes.c_double()
+    _check(load().cw_cg_residual(op, _ptr(b), _ptr(u), prec, ctypes.byref(r), _stream(stream)), "cw_cg_residual")
+    return r.value
 
 
 def cw_cg_solve_noalloc(op, b, u, rtol=1e-10, maxit=10000, mode=CW_CG_F64, stream=None):
@@ -478,6 +487,12 @@ class Operator:
         u = torch.empty(self.L, dtype=torch.float64, device="cuda") if u is None else self._f64(u, "cg_solve: u")
         rc, st = cw_cg_solve(self.handle, b, u, rtol, maxit, mode, check=check)
         return u, st, rc
+
+    def residual(self, b, u, prec=CW_PREC_F64_NATIVE):
+        """Relative residual of the solver's measure for iterate u (see cw_cg_residual)."""
+        self._f64(b, "residual: b")
+        self._f64(u, "residual: u")
+        return cw_cg_residual(self.handle, b, u, prec)
 
     def close(self):
         if self.handle:

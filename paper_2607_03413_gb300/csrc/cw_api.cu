@@ -888,9 +888,12 @@ cw_status cw_op_create(cw_mesh mh, int degree, int kind, int geom, int prec, int
         if (e == cudaSuccess) {
             const int64_t nthr = op->E * n3;
             const unsigned blocks = (unsigned)((nthr + 255) / 256);
-            if (metric_is_f64(prec))
+            if (prec == CW_PREC_F64)  // float pairs for the double-float arithmetic
                 metric_kernel<df64s><<<blocks, 256>>>(m->d_verts, m->nx, m->ny, op->E, op->n, kind, rule,
                                                       static_cast<df64s *>(op->d_geo), d_bad);
+            else if (prec == CW_PREC_F64_NATIVE)  // IEEE doubles
+                metric_kernel<double><<<blocks, 256>>>(m->d_verts, m->nx, m->ny, op->E, op->n, kind, rule,
+                                                       static_cast<double *>(op->d_geo), d_bad);
             else if (prec == CW_PREC_F32)
                 metric_kernel<float><<<blocks, 256>>>(m->d_verts, m->nx, m->ny, op->E, op->n, kind, rule,
                                                       static_cast<float *>(op->d_geo), d_bad);
@@ -909,7 +912,7 @@ cw_status cw_op_create(cw_mesh mh, int degree, int kind, int geom, int prec, int
         }
     } else if (geom == CW_GEOM_RECOMPUTE) {
         const bool f64 = metric_is_f64(prec);
-        op->geo_bytes = op->E * kTriCoef * (int64_t)(f64 ? sizeof(df64s) : sizeof(float));
+        op->geo_bytes = op->E * kTriCoef * (int64_t)(f64 ? sizeof(double) : sizeof(float));
         e = cudaMalloc(&op->d_geo, op->geo_bytes);
         if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(d_bad, 0, sizeof(int));
@@ -918,8 +921,10 @@ cw_status cw_op_create(cw_mesh mh, int degree, int kind, int geom, int prec, int
             detj_check_kernel<<<(unsigned)((nthr + 255) / 256), 256>>>(m->d_verts, m->nx, m->ny, op->E, op->n, rule,
                                                                         d_bad);
             const unsigned cb = (unsigned)((op->E + 255) / 256);
-            if (f64)
+            if (prec == CW_PREC_F64)
                 trilinear_coef_kernel<df64s><<<cb, 256>>>(m->d_verts, m->nx, m->ny, op->E, static_cast<df64s *>(op->d_geo));
+            else if (prec == CW_PREC_F64_NATIVE)
+                trilinear_coef_kernel<double><<<cb, 256>>>(m->d_verts, m->nx, m->ny, op->E, static_cast<double *>(op->d_geo));
             else
                 trilinear_coef_kernel<float><<<cb, 256>>>(m->d_verts, m->nx, m->ny, op->E, static_cast<float *>(op->d_geo));
             e = cudaGetLastError();
@@ -958,6 +963,7 @@ cw_status cw_op_destroy(cw_op oh)
     if (!op) return fail(CW_ERR_ARG, "cw_op_destroy: NULL");
     cg_release(op);
     if (op->inner) cw_op_destroy(reinterpret_cast<cw_op>(op->inner));
+    if (op->native) cw_op_destroy(reinterpret_cast<cw_op>(op->native));
     cudaFree(op->h_dx);
     cudaFree(op->h_dy);
     for (int i = 0; i < 3; ++i)
@@ -986,7 +992,7 @@ int64_t cw_op_device_bytes(cw_op oh)
 {
     Op *op = reinterpret_cast<Op *>(oh);
     if (!op) return -1;
-    return op->owned_bytes + (op->inner ? op->inner->owned_bytes : 0);
+    return op->owned_bytes + (op->inner ? op->inner->owned_bytes : 0) + (op->native ? op->native->owned_bytes : 0);
 }
 
 cw_status cw_gather(cw_op oh, const double *ug, void *x, void *stream)

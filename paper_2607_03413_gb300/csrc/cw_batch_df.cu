@@ -64,15 +64,11 @@ static cudaError_t grouped(const Tables1D &tb, const BatchProb *d_probs, int npr
     // shared memory for the largest metric of the group (kind_max components)
     const size_t smem = metric_smem_bytes<N, CPB, typename ArDF::T, df64s>(metric_ncomp(kind_max), STAGE);
     auto kern = batch_degree_kernel<N, CPB, ArDF, double, df64s, STAGE>;
-    static size_t opted = 0;
-    static int per_sm = 0;
-    if (smem > opted) {
-        cudaError_t e = opt_in_smem(kern, smem);
-        if (e != cudaSuccess) return e;
-        opted = smem;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, N * N * CPB, smem);
-        if (e != cudaSuccess) return e;
-    }
+    static size_t opted[kMaxDevices] = {};
+    static int per_sm_dev[kMaxDevices] = {};
+    int per_sm = 0;
+    if (cudaError_t e = ensure_smem_occupancy(kern, smem, N * N * CPB, opted, per_sm_dev, &per_sm); e != cudaSuccess)
+        return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

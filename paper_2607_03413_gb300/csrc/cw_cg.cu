@@ -23,7 +23,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
-#include <mutex>
 #include <string>
 #include <type_traits>
 
@@ -570,7 +569,7 @@ enum ApplyKind : int { AK_DF = 0, AK_NATIVE = 1, AK_OP = 2 };
 
 static cudaError_t apply_by_kind(const Op &op, int ak, const void *x, void *y, cudaStream_t s)
 {
-    if (ak == AK_NATIVE) return apply_launch_f64n(op, x, y, s);  // same FP64 metric layout
+    if (ak == AK_NATIVE) return apply_launch_f64n(op, x, y, s);  // the op's own FP64 metric, native arithmetic
     return apply_local(op, x, y, s);
 }
 
@@ -779,6 +778,13 @@ static cw_status ensure_scratch(Op *op, int mode)
         CW_CUDA_TRY(cudaStreamSynchronize(c->stream));
         op->owned_bytes += c->bytes;
     }
+    if (!op->native) {  // the IEEE FP64 operator of the outer residual (and of CW_CG_F64_NATIVE)
+        cw_op nat;
+        cw_status st = cw_op_create(reinterpret_cast<cw_mesh>(op->mesh), op->p, op->kind, op->geom, CW_PREC_F64_NATIVE,
+                                    op->bc, &nat);
+        if (st != CW_OK) return st;
+        op->native = reinterpret_cast<Op *>(nat);
+    }
     const bool fp64_inner = (mode == CW_CG_F64 || mode == CW_CG_F64_NATIVE);
     if (fp64_inner && !c->d64) {
         CW_CUDA_TRY(cudaMalloc(&c->d64, L * sizeof(double)));
@@ -787,7 +793,6 @@ static cw_status ensure_scratch(Op *op, int mode)
     if (!fp64_inner) {
         const int iprec = (mode == CW_CG_IR_BF16) ? CW_PREC_F32_BF16G : CW_PREC_F32;
         if (op->inner && op->inner->prec != iprec) {  // switch inner metric precision
-            op->owned_bytes -= op->inner->owned_bytes;
             cw_op_destroy(reinterpret_cast<cw_op>(op->inner));
             op->inner = nullptr;
             if (c->lv32.graph) {
@@ -861,8 +866,9 @@ static cw_status averaged_rhs(const Op &op, const double *r, double *work, void 
 
 using namespace cw;
 
-// Every mode runs the same outer loop: r = b - A u with the native-FP64 operator (the accurate
-// residual), stop when ||m G^T r|| <= rtol ||m G^T b||, else continue the inner Jacobi-PCG on
+// Every mode runs the same outer loop: r = b - A u with the IEEE FP64 operator (native FP64
+// arithmetic on a twin of the operator whose metric is stored as doubles: the accurate residual),
+// stop when ||m G^T r|| <= rtol ||m G^T b||, else continue the inner Jacobi-PCG on
 // A d = S_bar r and set u += d. The inner solver is FP64 with the double-float operator
 // (CW_CG_F64), FP64 with the native operator (CW_CG_F64_NATIVE), or FP32 with the FP32 / BF16-metric
 // operator (CW_CG_IR_*). The inner CG is not restarted between segments: each segment replaces the
@@ -919,7 +925,8 @@ extern "C" cw_status cw_cg_solve(cw_op oh, const double *b, double *u, double rt
             const bool keep = consistent && attempt == 0;
             if (fp64_inner) {
                 if ((ist = averaged_rhs(*op, r, w, c.lv64.r, false, s)) != CW_OK) return ist;
-                ist = cg_run<double, double>(*op, ak, c.lv64, c.d64, c, itol, maxit - iters, &it, keep, &rec);
+                const Op &iop = (mode == CW_CG_F64_NATIVE) ? *op->native : *op;
+                ist = cg_run<double, double>(iop, ak, c.lv64, c.d64, c, itol, maxit - iters, &it, keep, &rec);
             } else {
                 if ((ist = averaged_rhs(*op, r, w, c.lv32.r, true, s)) != CW_OK) return ist;
                 ist = cg_run<float, float>(*op->inner, AK_OP, c.lv32, c.d32, c, itol, maxit - iters, &it, keep, &rec);
@@ -930,13 +937,14 @@ extern "C" cw_status cw_cg_solve(cw_op oh, const double *b, double *u, double rt
             iters += it;
             if (ist != CW_ERR_BREAKDOWN || !keep) break;
         }
-        if (ist == CW_ERR_BREAKDOWN) return ist;
+        // breakdown, or a CUDA error of the inner run: the correction may be partly written
+        if (ist != CW_OK && ist != CW_ERR_NOT_CONVERGED) return ist;
         if (fp64_inner) k_add_correction_f64<<<vec_grid(), 256, 0, s>>>(u, c.d64, L);
         else k_add_correction<<<vec_grid(), 256, 0, s>>>(u, c.d32, L);
         ++outer;
-        // accurate residual with the native FP64 operator
+        // accurate residual with the IEEE FP64 operator (native arithmetic, metric stored as doubles)
         const double res_prev = res;
-        CW_CUDA_TRY(apply_launch_f64n(*op, u, w, s));
+        CW_CUDA_TRY(apply_launch_f64n(*op->native, u, w, s));
         k_sub<<<vec_grid(), 256, 0, s>>>(r, b, w, L);
         if ((st = residual_norm2(*op, r, w, c, &res)) != CW_OK) return st;
         if (debug_trace()) std::fprintf(stderr, "[cwfem cg] outer %d: true rel residual %.3e\n", outer, std::sqrt(res / res0));
@@ -965,6 +973,36 @@ extern "C" cw_status cw_cg_solve(cw_op oh, const double *b, double *u, double rt
     return st;
 }
 
+// Relative residual ||m G^T (b - A u)|| / ||m G^T b|| of a cell-wise iterate, with A evaluated by the
+// IEEE FP64 twin (prec CW_PREC_F64_NATIVE) or by the operator's own double-float arithmetic on its
+// float-pair metric (CW_PREC_F64).
+extern "C" cw_status cw_cg_residual(cw_op oh, const double *b, const double *u, int prec, double *rel_residual,
+                                    void *stream)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    if (!op || !b || !u || !rel_residual) return fail(CW_ERR_ARG, "cw_cg_residual: NULL argument");
+    if (op->prec != CW_PREC_F64) return fail(CW_ERR_ARG, "cw_cg_residual: the operator must be CW_PREC_F64");
+    if (op->bc != CW_BC_DIRICHLET0) return fail(CW_ERR_ARG, "cw_cg_residual: the operator must use CW_BC_DIRICHLET0");
+    if (prec != CW_PREC_F64 && prec != CW_PREC_F64_NATIVE)
+        return fail(CW_ERR_ARG, "cw_cg_residual: prec must be CW_PREC_F64 or CW_PREC_F64_NATIVE");
+    cw_status st = ensure_scratch(op, CW_CG_F64);
+    if (st != CW_OK) return st;
+    CgScratch &c = *op->cg;
+    cudaStream_t s = c.stream;
+    CW_CUDA_TRY(cudaEventRecord(c.ev0, static_cast<cudaStream_t>(stream)));
+    CW_CUDA_TRY(cudaStreamWaitEvent(s, c.ev0, 0));
+    double *r = c.rout, *w = c.q64b;
+    double res0 = 0.0, res = 0.0;
+    if ((st = residual_norm2(*op, b, w, c, &res0)) != CW_OK) return st;
+    if (prec == CW_PREC_F64_NATIVE) CW_CUDA_TRY(apply_launch_f64n(*op->native, u, w, s));
+    else CW_CUDA_TRY(apply_local(*op, u, w, s));
+    k_sub<<<vec_grid(), 256, 0, s>>>(r, b, w, op->L);
+    CW_CUDA_TRY(cudaGetLastError());
+    if ((st = residual_norm2(*op, r, w, c, &res)) != CW_OK) return st;
+    *rel_residual = res0 > 0.0 ? std::sqrt(res / res0) : 0.0;
+    return CW_OK;
+}
+
 // ===================================================================== allocation-free solve ====
 // cw_cg_solve_noalloc: the same FP64 solve as cw_cg_solve (modes CW_CG_F64 and CW_CG_F64_NATIVE)
 // for callers that cannot allocate device memory at solve time -- code running inside a memory
@@ -982,23 +1020,17 @@ constexpr size_t kNaBytes = 8 * kNaVec + size_t(kNoAllocMaxL) + 2 * kRedBlocks *
                             S_NSCAL * sizeof(double) + F_NFLAG * sizeof(int) + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
-// Device address of g_noalloc_scratch for the current device. In host code the symbol is only a
-// host-side stand-in; its device address comes from cudaGetSymbolAddress, resolved once per device.
+// Device address of g_noalloc_scratch in the current device's context. In host code the symbol is
+// only a host-side stand-in; its device address comes from cudaGetSymbolAddress, which is resolved
+// again on every call: the address belongs to the CUDA context, so a value kept from an earlier call
+// could be stale after cudaDeviceReset or under another context on the same device. Once the module
+// is loaded on the device this lookup allocates nothing.
 static cw_status noalloc_base(unsigned char **out)
 {
-    static std::mutex mu;
-    static unsigned char *base[128] = {};
-    int dev = 0;
-    CW_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 128) return fail(CW_ERR_UNSUPPORTED, "cw_cg_solve_noalloc: device index >= 128");
-    std::lock_guard<std::mutex> lock(mu);
-    if (!base[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cw_cg_solve_noalloc: cudaGetSymbolAddress");
-        base[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = base[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cw_cg_solve_noalloc: cudaGetSymbolAddress");
+    *out = static_cast<unsigned char *>(p);
     return CW_OK;
 }
 
@@ -1109,7 +1141,7 @@ extern "C" cw_status cw_cg_solve_noalloc(cw_op oh, const double *b, double *u, d
         int it = 0;
         if ((st = averaged_rhs(*op, r, w, c.lv64.r, false, s)) != CW_OK) return st;
         cw_status ist = cg_run_eager(*op, ak, c.lv64, d, c, itol, maxit - iters, &it, s);
-        if (ist == CW_ERR_BREAKDOWN) return ist;
+        if (ist != CW_OK && ist != CW_ERR_NOT_CONVERGED) return ist;
         k_add_correction_f64<<<vec_grid(), 256, 0, s>>>(u, d, L);
         iters += it;
         ++outer;

@@ -42,11 +42,13 @@ struct Op {
     int p = 0, n = 0, kind = 0, geom = 0, prec = 0, bc = 0;
     int64_t E = 0, L = 0, NG = 0;
     Tables1D tab;
-    void *d_geo = nullptr;  // metric [E][ncomp][n^3] in the metric type (FP64 precisions: df64s pairs), or affine [E][4] doubles
+    void *d_geo = nullptr;  // metric [E][ncomp][n^3] in the metric type (CW_PREC_F64: df64s pairs; CW_PREC_F64_NATIVE:
+                            // doubles), or affine [E][4] doubles
     int64_t geo_bytes = 0;
     double *d_dinv = nullptr;  // cell-wise masked inverse diagonal (solver), lazily
     CgScratch *cg = nullptr;
-    Op *inner = nullptr;  // reduced-precision twin used by iterative refinement
+    Op *inner = nullptr;   // reduced-precision twin used by iterative refinement
+    Op *native = nullptr;  // IEEE FP64 twin (CW_PREC_F64_NATIVE, metric as doubles): the solver's outer residual
     // host-buffer apply (cw_apply_host): device staging vectors, streams and events, lazily
     void *h_dx = nullptr, *h_dy = nullptr;
     cudaStream_t h_st[3] = {nullptr, nullptr, nullptr};

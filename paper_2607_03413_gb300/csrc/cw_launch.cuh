@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <type_traits>
 
 #include "cw_apply.cuh"
@@ -117,6 +118,52 @@ static cudaError_t opt_in_smem(K kernel, size_t smem)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// Dynamic shared-memory opt-in of one kernel instantiation, done once per device and size:
+// `opted[dev]` records the largest size opted in on device dev. The lock keeps host threads that
+// create or launch operators concurrently from racing on that record.
+constexpr int kMaxDevices = 64;
+inline std::mutex &smem_opt_mutex()
+{
+    static std::mutex m;
+    return m;
+}
+template <class K>
+static cudaError_t ensure_smem(K kernel, size_t smem, size_t (&opted)[kMaxDevices])
+{
+    if (smem <= 48 * 1024) return smem > 227 * 1024 ? cudaErrorInvalidConfiguration : cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return opt_in_smem(kernel, smem);
+    std::lock_guard<std::mutex> lock(smem_opt_mutex());
+    if (smem <= opted[dev]) return cudaSuccess;
+    e = opt_in_smem(kernel, smem);
+    if (e == cudaSuccess) opted[dev] = smem;
+    return e;
+}
+
+// The same for persistent kernels, which also need their resident CTAs per SM at that size:
+// per_sm[dev] is recomputed whenever a larger size is opted in.
+template <class K>
+static cudaError_t ensure_smem_occupancy(K kernel, size_t smem, int threads, size_t (&opted)[kMaxDevices],
+                                         int (&per_sm)[kMaxDevices], int *out_per_sm)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(smem_opt_mutex());
+    if (smem > opted[dev] || per_sm[dev] == 0) {
+        e = opt_in_smem(kernel, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[dev], kernel, threads, smem);
+        if (e != cudaSuccess) return e;
+        if (smem > opted[dev]) opted[dev] = smem;
+    }
+    *out_per_sm = per_sm[dev];
+    return cudaSuccess;
+}
+
 // xfuse != nullptr: the kernel also applies the x pass of the DSS inside each tile and *xfuse
 // receives the tile size (cells), so the DSS x pass only has the interfaces between tiles left
 // the plain or the register-capped instantiation (only the one used is compiled)
@@ -134,12 +181,8 @@ cudaError_t launch_metric(const Op &op, const void *x, void *y, cudaStream_t s, 
     fill_metric_tab<N>(tab, op.tab, [](double v) { return MakeC<Ar>::from(v); });
     const size_t smem = metric_smem_bytes<N, CPB, typename Ar::T, GS>(metric_ncomp(op.kind), STAGE);
     auto kern = metric_kernel_ptr<N, CPB, Ar, VS, GS, STAGE, RC>();
-    static size_t opted = 0;  // largest size opted in so far for this instantiation
-    if (smem > opted) {
-        cudaError_t e = opt_in_smem(kern, smem);
-        if (e != cudaSuccess) return e;
-        opted = smem;
-    }
+    static size_t opted[kMaxDevices] = {};  // largest size opted in so far, per device
+    if (cudaError_t e = ensure_smem(kern, smem, opted); e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((op.E + CPB - 1) / CPB);
     if (xfuse) *xfuse = CPB;
     kern<<<grid, N * N * CPB, smem, s>>>(static_cast<const VS *>(x), static_cast<VS *>(y),
@@ -158,12 +201,8 @@ cudaError_t launch_metric_dot(const Op &op, const void *x, void *y, double *part
     fill_metric_tab<N>(tab, op.tab, [](double v) { return MakeC<Ar>::from(v); });
     const size_t smem = metric_smem_bytes<N, CPB, typename Ar::T, GS>(metric_ncomp(op.kind), ST);
     auto kern = apply_metric_dot_kernel<N, CPB, Ar, VS, GS, ST, RC>;
-    static size_t opted = 0;
-    if (smem > opted) {
-        cudaError_t e = opt_in_smem(kern, smem);
-        if (e != cudaSuccess) return e;
-        opted = smem;
-    }
+    static size_t opted[kMaxDevices] = {};  // largest size opted in so far, per device
+    if (cudaError_t e = ensure_smem(kern, smem, opted); e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((op.E + CPB - 1) / CPB);
     *nblocks = grid;
     kern<<<grid, N * N * CPB, smem, s>>>(static_cast<const VS *>(x), static_cast<VS *>(y),
@@ -205,20 +244,17 @@ cudaError_t launch_affine(const Op &op, const void *x, void *y, cudaStream_t s)
         }
     const size_t smem = 2 * CPB * Lines<N>::CS * sizeof(typename Ar::T);
     auto kern = apply_affine_kernel<N, CPB, Ar, VS>;
-    static size_t opted = 0;
-    if (smem > opted) {
-        cudaError_t e = opt_in_smem(kern, smem);
-        if (e != cudaSuccess) return e;
-        opted = smem;
-    }
+    static size_t opted[kMaxDevices] = {};  // largest size opted in so far, per device
+    if (cudaError_t e = ensure_smem(kern, smem, opted); e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((op.E + CPB - 1) / CPB);
     kern<<<grid, N * N * CPB, smem, s>>>(static_cast<const VS *>(x), static_cast<VS *>(y),
                                          static_cast<const double *>(op.d_geo), op.E, op.kind, tab);
     return cudaGetLastError();
 }
 
-// variant selection: op.cpb (0 = default, else cpb_default or cpb_alt), op.stage (0/1)
-template <int N, class Ar, class VS, class GS, bool ALL_VARIANTS>
+// variant selection: op.cpb (0 = default, else cpb_default or cpb_alt), op.stage (0/1); GC is the
+// storage type of the recomputed geometry's coefficients
+template <int N, class Ar, class VS, class GS, bool ALL_VARIANTS, class GC>
 cudaError_t launch_variant(const Op &op, const void *x, void *y, cudaStream_t s, int *xfuse)
 {
     constexpr int D = cpb_default<N>(), A = cpb_alt<N>();
@@ -228,7 +264,6 @@ cudaError_t launch_variant(const Op &op, const void *x, void *y, cudaStream_t s,
         return launch_affine<N, D, Ar, VS>(op, x, y, s);
     }
     if (op.geom == CW_GEOM_RECOMPUTE) {  // default tile; direct loads or a TMA-staged input tile
-        using GC = typename RCStore<Ar>::type;
         if constexpr (ALL_VARIANTS)
             if (op.stage != 0) return launch_metric<N, D, Ar, VS, GC, 2, true>(op, x, y, s, xfuse);
         return launch_metric<N, D, Ar, VS, GC, 0, true>(op, x, y, s, xfuse);
@@ -245,18 +280,18 @@ cudaError_t launch_variant(const Op &op, const void *x, void *y, cudaStream_t s,
     return launch_metric<N, D, Ar, VS, GS, 0>(op, x, y, s, xfuse);
 }
 
-template <class Ar, class VS, class GS, bool ALL_VARIANTS = true>
+template <class Ar, class VS, class GS, bool ALL_VARIANTS = true, class GC = typename RCStore<Ar>::type>
 cudaError_t launch_degree(const Op &op, const void *x, void *y, cudaStream_t s, int *xfuse = nullptr)
 {
     if (xfuse) *xfuse = 0;
     switch (op.n) {
-    case 2: return launch_variant<2, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s, xfuse);
-    case 3: return launch_variant<3, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s, xfuse);
-    case 4: return launch_variant<4, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s, xfuse);
-    case 5: return launch_variant<5, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s, xfuse);
-    case 6: return launch_variant<6, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s, xfuse);
-    case 7: return launch_variant<7, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s, xfuse);
-    case 8: return launch_variant<8, Ar, VS, GS, ALL_VARIANTS>(op, x, y, s, xfuse);
+    case 2: return launch_variant<2, Ar, VS, GS, ALL_VARIANTS, GC>(op, x, y, s, xfuse);
+    case 3: return launch_variant<3, Ar, VS, GS, ALL_VARIANTS, GC>(op, x, y, s, xfuse);
+    case 4: return launch_variant<4, Ar, VS, GS, ALL_VARIANTS, GC>(op, x, y, s, xfuse);
+    case 5: return launch_variant<5, Ar, VS, GS, ALL_VARIANTS, GC>(op, x, y, s, xfuse);
+    case 6: return launch_variant<6, Ar, VS, GS, ALL_VARIANTS, GC>(op, x, y, s, xfuse);
+    case 7: return launch_variant<7, Ar, VS, GS, ALL_VARIANTS, GC>(op, x, y, s, xfuse);
+    case 8: return launch_variant<8, Ar, VS, GS, ALL_VARIANTS, GC>(op, x, y, s, xfuse);
     }
     return cudaErrorInvalidValue;
 }
