@@ -326,6 +326,60 @@ cw_status cw_apply_batched(const cw_op *ops, const void *const *x, void *const *
                            int flags, void *stream);
 
 /*
+ * Geometric multigrid on a uniform mesh hierarchy (Sec. 3, Algorithm mg_vcycle; Sec. 5 for the
+ * realisation). levels[0] is the coarsest level, levels[l+1] an operator on the uniform refinement of
+ * levels[l]'s mesh (twice the cells per direction, vertices from cw_mesh_refine_vertices, so that
+ * the spaces are nested: checked on the vertices, CW_ERR_ARG otherwise). All levels share degree,
+ * kind and precision -- CW_PREC_F64 (double-float cycle), CW_PREC_F64_NATIVE (IEEE FP64 cycle) or
+ * CW_PREC_F32 (FP32 cycle, the mixed-precision preconditioner of cw_mg_pcg_solve) -- and use
+ * CW_BC_DIRICHLET0; geometry modes may differ. nu1 / nu2 pre- / post-smoothing sweeps (0..64),
+ * omega in (0, 2) the damping of the Jacobi smoother.
+ *  - Smoother: one sweep is Algorithm smoother_fused: v = A u, u += D_hat (b - v) per copy,
+ *    u = S_bar u, with D_hat = omega K_cell D_cell^-1 (valence baked in, Eq. (valence_baking), zeros
+ *    on Dirichlet DoFs: "Constraints baked into the diagonal").
+ *  - Transfers: Algorithms prolongation and restriction, the restriction fed b - A u as two operands
+ *    (fused residual restriction, Sec. 5). Cells are lexicographic on every level.
+ *  - Coarse solve A_0^-1: the interior block of level 0's assembled matrix (element matrices in FP64)
+ *    inverted once at create on the host; at most 4096 interior DoFs on level 0 (CW_ERR_UNSUPPORTED
+ *    beyond).
+ * The create call allocates the level vectors (right-hand side, iterate, operator output) and the
+ * inverse diagonals, and synchronises the device. The operators must outlive the hierarchy, and a
+ * hierarchy must not be used by two streams at once (its level vectors are shared by all calls).
+ */
+typedef struct cw_mg_s *cw_mg;
+cw_status cw_mg_create(const cw_op *levels, int nlevels, int nu1, int nu2, double omega, cw_mg *out);
+cw_status cw_mg_destroy(cw_mg mg); /* waits for the device first */
+int64_t cw_mg_device_bytes(cw_mg mg);
+/*
+ * One V-cycle on the finest level: u <- MG(b, u) (Algorithm mg_vcycle). b: raw (unassembled) dual,
+ * u: continuous primal, both cell-wise vectors of the levels' type and of the finest level's length.
+ * zero_guess != 0: u enters as zero (its content is ignored; the first smoothing sweep skips the
+ * operator). Asynchronous on `stream`, no host synchronisation (can be captured into a CUDA graph).
+ */
+cw_status cw_mg_vcycle(cw_mg mg, const void *b, void *u, int zero_guess, void *stream);
+/* uf = P uc: Algorithm prolongation from level-1 to level (1 <= level < nlevels), overwriting uf */
+cw_status cw_mg_prolong(cw_mg mg, int level, const void *uc, void *uf, void *stream);
+/* rc = R rf: Algorithm restriction from level to level-1 (additive over the children) */
+cw_status cw_mg_restrict(cw_mg mg, int level, const void *rf, void *rc, void *stream);
+/* `sweeps` smoothing sweeps (Algorithm smoother_fused) on a level: u <- S(b, u); b raw dual, u continuous */
+cw_status cw_mg_smooth(cw_mg mg, int level, const void *b, void *u, int sweeps, void *stream);
+/* u = A_0^-1 b on the coarsest level (interior DoFs; zero on the boundary), b a raw dual */
+cw_status cw_mg_coarse_solve(cw_mg mg, const void *b, void *u, void *stream);
+/*
+ * Solve A_CG u_g = G^T b with CG preconditioned by one V-cycle of `mg` from a zero initial guess
+ * (Sec. 5), in the cell-wise primal-dual form, inside the FP64 outer refinement of cw_cg_solve (same
+ * stopping measure, residual with the IEEE FP64 operator; the inner CG restarts at every outer step).
+ * op: CW_PREC_F64, CW_BC_DIRICHLET0, on the finest level's mesh with its degree and kind; its
+ * double-float operator runs the CG. The cycle is fed the averaged residual S_bar r (same assembly
+ * G^T r, every copy small; rounded to FP32 for an FP32 hierarchy, whose output is widened back to
+ * FP64). One CG iteration is captured into a CUDA graph and replayed; the host reads the device flags
+ * after each. Allocates as cw_cg_solve on first use (plus two FP32 vectors for an FP32 hierarchy).
+ * Synchronises `stream`; stats as cw_cg_solve (iterations = CG iterations = V-cycles).
+ */
+cw_status cw_mg_pcg_solve(cw_mg mg, cw_op op, const double *b, double *u, double rtol, int maxit, cw_cg_stats *stats,
+                          void *stream);
+
+/*
  * Allocation-free variant of cw_cg_solve. The paper has no counterpart; this entry point exists
  * for callers that must not allocate device memory while solving -- e.g. code that runs inside a
  * caller-managed memory pool or an allocator callback, a real-time loop whose memory is fixed at

@@ -35,7 +35,9 @@ EXPORTED = [
     "cw_op_get_variant", "cw_op_autotune", "cw_cg_solve_noalloc", "cw_batch_create", "cw_batch_destroy",
     "cw_batch_values", "cw_batch_launch", "cw_batch_graph_launch", "cw_batch_set_variant",
     "cw_batch_get_variant", "cw_batch_autotune", "cw_batch_set_mode", "cw_apply_batched", "cw_apply_host",
-    "cw_mesh_refine_vertices", "cw_rules_1d", "cw_basis_1d", "cw_cg_residual",
+    "cw_mesh_refine_vertices", "cw_rules_1d", "cw_basis_1d", "cw_cg_residual", "cw_mg_create", "cw_mg_destroy",
+    "cw_mg_device_bytes", "cw_mg_vcycle", "cw_mg_prolong", "cw_mg_restrict", "cw_mg_smooth", "cw_mg_coarse_solve",
+    "cw_mg_pcg_solve",
 ]
 
 
@@ -103,6 +105,15 @@ def load(path: str = LIB_PATH):
         "cw_rules_1d": ([i32, vp, vp, vp], i32),
         "cw_basis_1d": ([i32, vp, vp, vp, vp, vp], i32),
         "cw_cg_residual": ([vp, vp, vp, i32, ctypes.POINTER(dbl), vp], i32),
+        "cw_mg_create": ([ctypes.POINTER(vp), i32, i32, i32, dbl, ctypes.POINTER(vp)], i32),
+        "cw_mg_destroy": ([vp], i32),
+        "cw_mg_device_bytes": ([vp], i64),
+        "cw_mg_vcycle": ([vp, vp, vp, i32, vp], i32),
+        "cw_mg_prolong": ([vp, i32, vp, vp, vp], i32),
+        "cw_mg_restrict": ([vp, i32, vp, vp, vp], i32),
+        "cw_mg_smooth": ([vp, i32, vp, vp, i32, vp], i32),
+        "cw_mg_coarse_solve": ([vp, vp, vp, vp], i32),
+        "cw_mg_pcg_solve": ([vp, vp, vp, vp, dbl, i32, ctypes.POINTER(cw_cg_stats), vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -340,6 +351,50 @@ def cw_apply_batched(ops, xs, ys, nrhs, flags=CW_APPLY_LOCAL, stream=None):
                                    (ctypes.c_int * n)(*nrhs), n, flags, _stream(stream)), "cw_apply_batched")
 
 
+def cw_mg_create(ops, nu1=2, nu2=2, omega=0.7):
+    n = len(ops)
+    h = ctypes.c_void_p()
+    _check(load().cw_mg_create((ctypes.c_void_p * n)(*[o.value if isinstance(o, ctypes.c_void_p) else o for o in ops]),
+                               n, nu1, nu2, float(omega), ctypes.byref(h)), "cw_mg_create")
+    return h
+
+
+def cw_mg_destroy(mg):
+    _check(load().cw_mg_destroy(mg), "cw_mg_destroy")
+
+
+def cw_mg_device_bytes(mg):
+    return load().cw_mg_device_bytes(mg)
+
+
+def cw_mg_vcycle(mg, b, u, zero_guess=True, stream=None):
+    _check(load().cw_mg_vcycle(mg, _ptr(b), _ptr(u), int(bool(zero_guess)), _stream(stream)), "cw_mg_vcycle")
+
+
+def cw_mg_prolong(mg, level, uc, uf, stream=None):
+    _check(load().cw_mg_prolong(mg, level, _ptr(uc), _ptr(uf), _stream(stream)), "cw_mg_prolong")
+
+
+def cw_mg_restrict(mg, level, rf, rc, stream=None):
+    _check(load().cw_mg_restrict(mg, level, _ptr(rf), _ptr(rc), _stream(stream)), "cw_mg_restrict")
+
+
+def cw_mg_smooth(mg, level, b, u, sweeps=1, stream=None):
+    _check(load().cw_mg_smooth(mg, level, _ptr(b), _ptr(u), sweeps, _stream(stream)), "cw_mg_smooth")
+
+
+def cw_mg_coarse_solve(mg, b, u, stream=None):
+    _check(load().cw_mg_coarse_solve(mg, _ptr(b), _ptr(u), _stream(stream)), "cw_mg_coarse_solve")
+
+
+def cw_mg_pcg_solve(mg, op, b, u, rtol=1e-10, maxit=1000, stream=None, check=True):
+    st = cw_cg_stats()
+    rc = load().cw_mg_pcg_solve(mg, op, _ptr(b), _ptr(u), rtol, maxit, ctypes.byref(st), _stream(stream))
+    if check and rc != CW_OK:
+        raise CwError(rc, "cw_mg_pcg_solve")
+    return rc, st
+
+
 # ------------------------------------------------------------------ convenience ----
 _VEC_DTYPE = {CW_PREC_F64: "float64", CW_PREC_F64_NATIVE: "float64", CW_PREC_F32: "float32",
               CW_PREC_F32_BF16G: "float32", CW_PREC_BF16: "bfloat16"}
@@ -558,6 +613,71 @@ class Batch:
     def close(self):
         if self.handle:
             cw_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Multigrid:
+    """Owns a cw_mg handle over a list of Operators (coarsest first); keeps references to them."""
+
+    def __init__(self, ops, nu1=2, nu2=2, omega=0.7):
+        self.ops = list(ops)
+        self.nu1, self.nu2, self.omega = nu1, nu2, omega
+        self.handle = cw_mg_create([o.handle for o in self.ops], nu1, nu2, omega)
+
+    @property
+    def top(self):
+        return self.ops[-1]
+
+    def vcycle(self, b, u=None, zero_guess=True):
+        top = self.top
+        top._cw(b, "vcycle: b")
+        u = top.empty() if u is None else top._cw(u, "vcycle: u")
+        cw_mg_vcycle(self.handle, b, u, zero_guess)
+        return u
+
+    def prolong(self, level, uc, uf=None):
+        f, c = self.ops[level], self.ops[level - 1]
+        c._cw(uc, "prolong: uc")
+        uf = f.empty() if uf is None else f._cw(uf, "prolong: uf")
+        cw_mg_prolong(self.handle, level, uc, uf)
+        return uf
+
+    def restrict(self, level, rf, rc=None):
+        f, c = self.ops[level], self.ops[level - 1]
+        f._cw(rf, "restrict: rf")
+        rc = c.empty() if rc is None else c._cw(rc, "restrict: rc")
+        cw_mg_restrict(self.handle, level, rf, rc)
+        return rc
+
+    def smooth(self, level, b, u, sweeps=1):
+        o = self.ops[level]
+        cw_mg_smooth(self.handle, level, o._cw(b, "smooth: b"), o._cw(u, "smooth: u"), sweeps)
+        return u
+
+    def coarse_solve(self, b, u=None):
+        o = self.ops[0]
+        o._cw(b, "coarse_solve: b")
+        u = o.empty() if u is None else o._cw(u, "coarse_solve: u")
+        cw_mg_coarse_solve(self.handle, b, u)
+        return u
+
+    def pcg_solve(self, op, b, u=None, rtol=1e-10, maxit=1000, check=True):
+        """MG-preconditioned CG for the FP64 operator `op` on the finest level's mesh."""
+        import torch
+        op._f64(b, "pcg_solve: b")
+        u = torch.empty(op.L, dtype=torch.float64, device="cuda") if u is None else op._f64(u, "pcg_solve: u")
+        rc, st = cw_mg_pcg_solve(self.handle, op.handle, b, u, rtol, maxit, check=check)
+        return u, st, rc
+
+    def close(self):
+        if self.handle:
+            cw_mg_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -607,6 +607,58 @@ __global__ void diag_kernel(const double *__restrict__ V, int nx, int ny, int n,
     }
 }
 
+// Element matrices of the cells, A[e][i][j] = sum_q (grad phi_i)^T G_q (grad phi_j) + c_q phi_i phi_j
+// (FP64, metric from the vertices as in the diagonal): grid (E, ceil(n^6 / blockDim)), one thread per
+// (i, j). Used to assemble the small coarsest level of a multigrid hierarchy.
+__global__ void elem_matrix_kernel(const double *__restrict__ V, int nx, int ny, int n, int kind, Rule1D rule,
+                                   double *__restrict__ A)
+{
+    extern __shared__ double sm[];  // [7][n^3]
+    const int n3 = n * n * n;
+    const int64_t e = blockIdx.x;
+    for (int q = threadIdx.x; q < n3; q += blockDim.x) {
+        const int a = q % n, b = (q / n) % n, c = q / (n * n);
+        double J[3][3], X[3], m[7], det;
+        cell_jacobian(V, nx, ny, e, rule.xq[a], rule.xq[b], rule.xq[c], J, X);
+        qp_metric(J, rule.wq[a] * rule.wq[b] * rule.wq[c], m, &det);
+        for (int k = 0; k < 7; ++k) sm[k * n3 + q] = m[k];
+    }
+    __syncthreads();
+    const int64_t pair = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    if (pair >= (int64_t)n3 * n3) return;
+    const int i = (int)(pair / n3), j = (int)(pair - (int64_t)i * n3);
+    const int i1 = i % n, i2 = (i / n) % n, i3 = i / (n * n);
+    const int j1 = j % n, j2 = (j / n) % n, j3 = j / (n * n);
+    double s = 0.0;
+    for (int q = 0; q < n3; ++q) {
+        const int a = q % n, b = (q / n) % n, c = q / (n * n);
+        const double Bi1 = rule.B[a][i1], Bi2 = rule.B[b][i2], Bi3 = rule.B[c][i3];
+        const double Bj1 = rule.B[a][j1], Bj2 = rule.B[b][j2], Bj3 = rule.B[c][j3];
+        if (kind & 1) {
+            const double gi[3] = {rule.Bd[a][i1] * Bi2 * Bi3, Bi1 * rule.Bd[b][i2] * Bi3, Bi1 * Bi2 * rule.Bd[c][i3]};
+            const double gj[3] = {rule.Bd[a][j1] * Bj2 * Bj3, Bj1 * rule.Bd[b][j2] * Bj3, Bj1 * Bj2 * rule.Bd[c][j3]};
+            const double G[3][3] = {{sm[0 * n3 + q], sm[3 * n3 + q], sm[4 * n3 + q]},
+                                    {sm[3 * n3 + q], sm[1 * n3 + q], sm[5 * n3 + q]},
+                                    {sm[4 * n3 + q], sm[5 * n3 + q], sm[2 * n3 + q]}};
+            for (int r = 0; r < 3; ++r)
+                for (int t = 0; t < 3; ++t) s += gi[r] * G[r][t] * gj[t];
+        }
+        if (kind & 2) s += sm[6 * n3 + q] * (Bi1 * Bi2 * Bi3) * (Bj1 * Bj2 * Bj3);
+    }
+    A[e * (int64_t)n3 * n3 + pair] = s;
+}
+
+cudaError_t element_matrices_launch(const Op &op, double *A, cudaStream_t s)
+{
+    const int n3 = op.n * op.n * op.n;
+    const Rule1D rule = make_rule(op.tab);
+    const int bs = 256;
+    dim3 grid((unsigned)op.E, (unsigned)(((int64_t)n3 * n3 + bs - 1) / bs));
+    elem_matrix_kernel<<<grid, bs, 7 * n3 * sizeof(double), s>>>(op.mesh->d_verts, op.mesh->nx, op.mesh->ny, op.n,
+                                                                  op.kind, rule, A);
+    return cudaGetLastError();
+}
+
 __device__ __forceinline__ void exact_rhs(int which, const double X[3], double *f)
 {
     if (which == 0) {

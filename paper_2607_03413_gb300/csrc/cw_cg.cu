@@ -70,6 +70,13 @@ struct CgScratch {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int64_t bytes = 0;
+    // multigrid-preconditioned CG: FP32 copies of the cycle's input and output (FP32 hierarchy) and
+    // the graph of one iteration, keyed by the hierarchy, the correction vector and the operator
+    float *r32 = nullptr, *z32 = nullptr;
+    cudaGraphExec_t mg_graph = nullptr;
+    uint64_t mg_graph_id = 0;
+    const void *mg_graph_d = nullptr;
+    const Op *mg_graph_op = nullptr;
 };
 
 // ---------------------------------------------------------------------------- kernels ----
@@ -632,6 +639,9 @@ void cg_release(Op *op)
     cudaFree(c->scal);
     cudaFree(c->flags);
     cudaFree(c->kappa);
+    cudaFree(c->r32);
+    cudaFree(c->z32);
+    if (c->mg_graph) cudaGraphExecDestroy(c->mg_graph);
     cudaFreeHost(c->h_scal);
     cudaFreeHost(c->h_flags);
     if (c->stream) cudaStreamDestroy(c->stream);
@@ -639,6 +649,23 @@ void cg_release(Op *op)
     if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;
     op->cg = nullptr;
+}
+
+// q = A p and the <p, q> stage (alpha = rho / <p, q>, breakdown test)
+template <class V>
+static cudaError_t apply_pq(const Op &aop, int ak, const V *p, V *q, CgScratch &c, cudaStream_t s)
+{
+    cudaError_t e;
+    if (c.dotpart && apply_dot_ok(aop, ak)) {  // <p, q> from the apply epilogue
+        int64_t nb = 0;
+        if ((e = apply_dot_by_kind(aop, p, q, c.dotpart, &nb, s)) != cudaSuccess) return e;
+        const unsigned g = (unsigned)std::min<int64_t>(kRedBlocks, (nb + kRedThreads - 1) / kRedThreads);
+        k_sum_fin<<<g, kRedThreads, 0, s>>>(c.dotpart, nb, c.partials, c.scal, c.flags, STAGE_PQ);
+    } else {
+        if ((e = apply_by_kind(aop, ak, p, q, s)) != cudaSuccess) return e;
+        k_dot_fin<V><<<vec_grid(), kRedThreads, 0, s>>>(p, q, aop.L, c.partials, c.scal, c.flags, STAGE_PQ);
+    }
+    return cudaGetLastError();
 }
 
 // one CG iteration on level `lv` of operator `aop` with vector type V, iterate U* u
@@ -649,15 +676,7 @@ static cudaError_t cg_iteration(const Op &aop, int ak, CgLevel &lv, U *u, CgScra
     V *r = static_cast<V *>(lv.r), *p = static_cast<V *>(lv.p), *q = static_cast<V *>(lv.q),
       *z = static_cast<V *>(lv.z), *dinv = static_cast<V *>(lv.dinv);
     cudaError_t e;
-    if (c.dotpart && apply_dot_ok(aop, ak)) {  // <p, q> from the apply epilogue
-        int64_t nb = 0;
-        if ((e = apply_dot_by_kind(aop, p, q, c.dotpart, &nb, s)) != cudaSuccess) return e;
-        const unsigned g = (unsigned)std::min<int64_t>(kRedBlocks, (nb + kRedThreads - 1) / kRedThreads);
-        k_sum_fin<<<g, kRedThreads, 0, s>>>(c.dotpart, nb, c.partials, c.scal, c.flags, STAGE_PQ);
-    } else {
-        if ((e = apply_by_kind(aop, ak, p, q, s)) != cudaSuccess) return e;
-        k_dot_fin<V><<<vec_grid(), kRedThreads, 0, s>>>(p, q, L, c.partials, c.scal, c.flags, STAGE_PQ);
-    }
+    if ((e = apply_pq<V>(aop, ak, p, q, c, s)) != cudaSuccess) return e;
     if constexpr (std::is_same<V, float>::value) {
         if (L < ((int64_t)1 << 31)) {
             // FP32 level: z = S_x(r - alpha q), then the y and z sums gathered inside the
@@ -741,6 +760,149 @@ static cw_status cg_run(const Op &aop, int ak, CgLevel &lv, U *u, CgScratch &c, 
     case ST_CONVERGED: return CW_OK;
     case ST_BREAKDOWN: return fail(CW_ERR_BREAKDOWN, "cw_cg_solve: breakdown (<p,Ap> <= 0 or non-finite)");
     default: return fail(CW_ERR_NOT_CONVERGED, "cw_cg_solve: maxit reached");
+    }
+}
+
+// ------------------------------------------------------- multigrid-preconditioned CG ----
+// Given w = S r: r <- w / kappa (the averaged residual S_bar r: same assembly G^T r, every copy small;
+// the V-cycle reads its input only through G^T, so it sees the same right-hand side), and, for an
+// FP32 hierarchy, its FP32 copy (the cycle's input). Skipped after convergence (r is then already
+// averaged and unchanged).
+template <bool F32>
+__global__ void __launch_bounds__(256) k_mg_average(double *__restrict__ r, const double *__restrict__ w,
+                                                    const uint8_t *__restrict__ kappa, float *__restrict__ r32,
+                                                    int64_t n, const int *__restrict__ flags)
+{
+    if (flags[F_DONE]) return;
+    CW_GRID_LOOP(i, n)
+    {
+        const uint8_t k = kappa[i];
+        const double ri = w[i] * (k == 1 ? 1.0 : (k == 2 ? 0.5 : (k == 4 ? 0.25 : 0.125)));  // exact
+        r[i] = ri;
+        if constexpr (F32) r32[i] = static_cast<float>(ri);
+    }
+}
+
+// Partials of rho = <r, z> and of <m w, r> = ||m G^T r||^2 (m = dinv != 0), then the stage logic
+// (STAGE_INIT or STAGE_RHO); with an FP32 cycle the output z32 is widened into z first.
+template <bool F32>
+__global__ void __launch_bounds__(kRedThreads) k_mg_dots_fin(const double *__restrict__ r, double *__restrict__ z,
+                                                             const float *__restrict__ z32,
+                                                             const double *__restrict__ w,
+                                                             const double *__restrict__ dinv, int64_t n,
+                                                             double *__restrict__ part, double *__restrict__ scal,
+                                                             int *__restrict__ flags, int stage)
+{
+    if (stage == STAGE_RHO && flags[F_DONE]) return;  // an iteration after convergence
+    df64 a1{0.0f, 0.0f}, a2{0.0f, 0.0f};
+    CW_GRID_LOOP(i, n)
+    {
+        double zi;
+        if constexpr (F32) {
+            zi = static_cast<double>(z32[i]);
+            z[i] = zi;
+        } else {
+            zi = z[i];
+        }
+        const double ri = r[i];
+        df_mad(a1, split_f64(ri), split_f64(zi));
+        if (dinv[i] != 0.0) df_mad(a2, split_f64(w[i]), split_f64(ri));
+    }
+    block_sum_store(df_to_double(a1), part);
+    block_sum_store(df_to_double(a2), part + gridDim.x);
+    last_block_finalize(part, scal, flags, stage);
+}
+
+// one iteration: q = A p, alpha; w = S (r - alpha q); r = w / kappa; z = MG(r); rho, residual, beta;
+// d += alpha p, p = z + beta p
+static cudaError_t mgcg_iteration(const Op &aop, MgHier &h, CgLevel &lv, double *d, CgScratch &c, bool f32,
+                                  cudaStream_t s)
+{
+    const int64_t L = aop.L;
+    double *r = static_cast<double *>(lv.r), *p = static_cast<double *>(lv.p), *q = static_cast<double *>(lv.q),
+           *z = static_cast<double *>(lv.z), *dinv = static_cast<double *>(lv.dinv), *w = c.q64b;
+    cudaError_t e;
+    if ((e = apply_pq<double>(aop, AK_DF, p, q, c, s)) != cudaSuccess) return e;
+    if ((e = dss_from_axpy(aop, r, q, c.scal + S_ALPHA, c.flags + F_ACTIVE, w, s)) != cudaSuccess) return e;
+    if (f32) k_mg_average<true><<<vec_grid(), 256, 0, s>>>(r, w, c.kappa, c.r32, L, c.flags);
+    else k_mg_average<false><<<vec_grid(), 256, 0, s>>>(r, w, c.kappa, nullptr, L, c.flags);
+    if ((e = mg_vcycle_zero(h, f32 ? static_cast<void *>(c.r32) : r, f32 ? static_cast<void *>(c.z32) : z, s)) !=
+        cudaSuccess)
+        return e;
+    if (f32)
+        k_mg_dots_fin<true><<<vec_grid(), kRedThreads, 0, s>>>(r, z, c.z32, w, dinv, L, c.partials, c.scal, c.flags,
+                                                               STAGE_RHO);
+    else
+        k_mg_dots_fin<false><<<vec_grid(), kRedThreads, 0, s>>>(r, z, nullptr, w, dinv, L, c.partials, c.scal,
+                                                                c.flags, STAGE_RHO);
+    k_pupdate_u<double, double><<<vec_grid(), 256, 0, s>>>(d, p, z, L, c.scal, c.flags);
+    return cudaGetLastError();
+}
+
+// CG on A d = rhs (rhs in lv.r), d zeroed here, preconditioned by one V-cycle from a zero initial
+// guess (Sec. 5), in the primal-dual form of cg_run. One iteration per graph replay; the host reads
+// the flags after each.
+static cw_status mgcg_run(const Op &aop, MgHier &h, CgLevel &lv, double *d, CgScratch &c, double rtol, int maxit,
+                          int *iters, double *rec_reduction)
+{
+    cudaStream_t s = c.stream;
+    const int64_t L = aop.L;
+    const bool f32 = mg_top_op(h).prec == CW_PREC_F32;
+    double *r = static_cast<double *>(lv.r), *p = static_cast<double *>(lv.p), *z = static_cast<double *>(lv.z),
+           *dinv = static_cast<double *>(lv.dinv), *w = c.q64b;
+    CW_CUDA_TRY(cudaMemsetAsync(d, 0, L * sizeof(double), s));
+    c.h_scal[0] = rtol * rtol;
+    c.h_flags[0] = 0;
+    c.h_flags[1] = maxit;
+    CW_CUDA_TRY(cudaMemcpyAsync(c.scal + S_TOL2, c.h_scal, sizeof(double), cudaMemcpyHostToDevice, s));
+    CW_CUDA_TRY(cudaMemcpyAsync(c.flags + F_DONE, &c.h_flags[0], sizeof(int), cudaMemcpyHostToDevice, s));
+    CW_CUDA_TRY(cudaMemcpyAsync(c.flags + F_MAXIT, &c.h_flags[1], sizeof(int), cudaMemcpyHostToDevice, s));
+    // w = S r; r <- S_bar r; z = MG(r); rho = <r, z>, res0 = <m S r, r>; p = z
+    CW_CUDA_TRY(dss_from(aop, r, w, CW_DSS_SUM, s));
+    if (f32) k_mg_average<true><<<vec_grid(), 256, 0, s>>>(r, w, c.kappa, c.r32, L, c.flags);
+    else k_mg_average<false><<<vec_grid(), 256, 0, s>>>(r, w, c.kappa, nullptr, L, c.flags);
+    CW_CUDA_TRY(mg_vcycle_zero(h, f32 ? static_cast<void *>(c.r32) : r, f32 ? static_cast<void *>(c.z32) : z, s));
+    if (f32)
+        k_mg_dots_fin<true><<<vec_grid(), kRedThreads, 0, s>>>(r, z, c.z32, w, dinv, L, c.partials, c.scal, c.flags,
+                                                               STAGE_INIT);
+    else
+        k_mg_dots_fin<false><<<vec_grid(), kRedThreads, 0, s>>>(r, z, nullptr, w, dinv, L, c.partials, c.scal,
+                                                                c.flags, STAGE_INIT);
+    CW_CUDA_TRY(cudaMemcpyAsync(p, z, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CW_CUDA_TRY(cudaGetLastError());
+    CW_CUDA_TRY(mgcg_iteration(aop, h, lv, d, c, f32, s));  // eager: first-use initialisation
+    if (c.mg_graph && (c.mg_graph_id != mg_id(h) || c.mg_graph_d != d || c.mg_graph_op != &aop)) {
+        cudaGraphExecDestroy(c.mg_graph);
+        c.mg_graph = nullptr;
+    }
+    if (!c.mg_graph) {
+        cudaGraph_t g;
+        CW_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = mgcg_iteration(aop, h, lv, d, c, f32, s);
+        cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        if (e != cudaSuccess) return cuda_fail(e, "mg-pcg capture");
+        if (e2 != cudaSuccess) return cuda_fail(e2, "mg-pcg capture end");
+        e = cudaGraphInstantiate(&c.mg_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "mg-pcg graph instantiate");
+        c.mg_graph_id = mg_id(h);
+        c.mg_graph_d = d;
+        c.mg_graph_op = &aop;
+    }
+    for (;;) {
+        CW_CUDA_TRY(cudaMemcpyAsync(c.h_flags, c.flags, F_NFLAG * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CW_CUDA_TRY(cudaStreamSynchronize(s));
+        if (c.h_flags[F_DONE]) break;
+        CW_CUDA_TRY(cudaGraphLaunch(c.mg_graph, s));
+    }
+    *iters = c.h_flags[F_ITER];
+    CW_CUDA_TRY(cudaMemcpyAsync(c.h_scal, c.scal, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CW_CUDA_TRY(cudaStreamSynchronize(s));
+    *rec_reduction = c.h_scal[S_RES0] > 0.0 ? std::sqrt(c.h_scal[S_RES] / c.h_scal[S_RES0]) : 0.0;
+    switch (c.h_flags[F_STATUS]) {
+    case ST_CONVERGED: return CW_OK;
+    case ST_BREAKDOWN: return fail(CW_ERR_BREAKDOWN, "cw_mg_pcg_solve: breakdown (<p,Ap> <= 0 or non-finite)");
+    default: return fail(CW_ERR_NOT_CONVERGED, "cw_mg_pcg_solve: maxit reached");
     }
 }
 
@@ -876,22 +1038,22 @@ using namespace cw;
 // mixed-precision Krylov solvers). A segment ends when its recursive residual has dropped by the
 // reduction still needed (FP64 inner levels) or by a factor 10 (FP32 inner levels, whose recursive
 // residual drifts from the true one as the iteration proceeds).
-extern "C" cw_status cw_cg_solve(cw_op oh, const double *b, double *u, double rtol, int maxit, int mode,
-                                 cw_cg_stats *stats, void *stream)
+// The outer refinement loop shared by cw_cg_solve (Jacobi-preconditioned inner CG, mg == nullptr)
+// and cw_mg_pcg_solve (V-cycle-preconditioned inner CG in FP64).
+static cw_status solve_impl(Op *op, const double *b, double *u, double rtol, int maxit, int mode, MgHier *mg,
+                            cw_cg_stats *stats, void *stream)
 {
-    Op *op = reinterpret_cast<Op *>(oh);
-    if (!op || !b || !u) return fail(CW_ERR_ARG, "cw_cg_solve: NULL argument");
-    if (op->prec != CW_PREC_F64) return fail(CW_ERR_ARG, "cw_cg_solve: the operator must be CW_PREC_F64");
-    if (op->bc != CW_BC_DIRICHLET0) return fail(CW_ERR_ARG, "cw_cg_solve: the operator must use CW_BC_DIRICHLET0");
-    if (mode < CW_CG_F64 || mode > CW_CG_F64_NATIVE) return fail(CW_ERR_ARG, "cw_cg_solve: bad mode");
-    if (!(rtol > 0.0) || maxit < 1) return fail(CW_ERR_ARG, "cw_cg_solve: rtol must be > 0 and maxit >= 1");
-    if (b == u) return fail(CW_ERR_ARG, "cw_cg_solve: b and u must not alias");
     cudaStream_t us = static_cast<cudaStream_t>(stream);
     cw_status st = ensure_scratch(op, mode);
     if (st != CW_OK) return st;
     CgScratch &c = *op->cg;
     cudaStream_t s = c.stream;
     const int64_t L = op->L;
+    if (mg && mg_top_op(*mg).prec == CW_PREC_F32 && !c.r32) {
+        CW_CUDA_TRY(cudaMalloc(&c.r32, L * sizeof(float)));
+        CW_CUDA_TRY(cudaMalloc(&c.z32, L * sizeof(float)));
+        op->owned_bytes += 2 * L * (int64_t)sizeof(float);
+    }
     // order the solve after the caller's stream
     CW_CUDA_TRY(cudaEventRecord(c.ev0, us));
     CW_CUDA_TRY(cudaStreamWaitEvent(s, c.ev0, 0));
@@ -923,7 +1085,10 @@ extern "C" cw_status cw_cg_solve(cw_op oh, const double *b, double *u, double rt
             // continue the Krylov process only after a consistent segment; restart otherwise or
             // when a continued segment breaks down
             const bool keep = consistent && attempt == 0;
-            if (fp64_inner) {
+            if (mg) {  // V-cycle-preconditioned CG, restarted at every outer step
+                if ((ist = averaged_rhs(*op, r, w, c.lv64.r, false, s)) != CW_OK) return ist;
+                ist = mgcg_run(*op, *mg, c.lv64, c.d64, c, itol, maxit - iters, &it, &rec);
+            } else if (fp64_inner) {
                 if ((ist = averaged_rhs(*op, r, w, c.lv64.r, false, s)) != CW_OK) return ist;
                 const Op &iop = (mode == CW_CG_F64_NATIVE) ? *op->native : *op;
                 ist = cg_run<double, double>(iop, ak, c.lv64, c.d64, c, itol, maxit - iters, &it, keep, &rec);
@@ -935,7 +1100,7 @@ extern "C" cw_status cw_cg_solve(cw_op oh, const double *b, double *u, double rt
                 std::fprintf(stderr, "[cwfem cg] outer %d: inner status %d, %d iterations (tol %.2e, %s)\n", outer,
                              (int)ist, it, itol, keep ? "continued" : "restarted");
             iters += it;
-            if (ist != CW_ERR_BREAKDOWN || !keep) break;
+            if (ist != CW_ERR_BREAKDOWN || !keep || mg) break;
         }
         // breakdown, or a CUDA error of the inner run: the correction may be partly written
         if (ist != CW_OK && ist != CW_ERR_NOT_CONVERGED) return ist;
@@ -971,6 +1136,36 @@ extern "C" cw_status cw_cg_solve(cw_op oh, const double *b, double *u, double rt
         stats->seconds = ms * 1e-3;
     }
     return st;
+}
+
+extern "C" cw_status cw_cg_solve(cw_op oh, const double *b, double *u, double rtol, int maxit, int mode,
+                                 cw_cg_stats *stats, void *stream)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    if (!op || !b || !u) return fail(CW_ERR_ARG, "cw_cg_solve: NULL argument");
+    if (op->prec != CW_PREC_F64) return fail(CW_ERR_ARG, "cw_cg_solve: the operator must be CW_PREC_F64");
+    if (op->bc != CW_BC_DIRICHLET0) return fail(CW_ERR_ARG, "cw_cg_solve: the operator must use CW_BC_DIRICHLET0");
+    if (mode < CW_CG_F64 || mode > CW_CG_F64_NATIVE) return fail(CW_ERR_ARG, "cw_cg_solve: bad mode");
+    if (!(rtol > 0.0) || maxit < 1) return fail(CW_ERR_ARG, "cw_cg_solve: rtol must be > 0 and maxit >= 1");
+    if (b == u) return fail(CW_ERR_ARG, "cw_cg_solve: b and u must not alias");
+    return solve_impl(op, b, u, rtol, maxit, mode, nullptr, stats, stream);
+}
+
+extern "C" cw_status cw_mg_pcg_solve(cw_mg mh, cw_op oh, const double *b, double *u, double rtol, int maxit,
+                                     cw_cg_stats *stats, void *stream)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    MgHier *mg = reinterpret_cast<MgHier *>(mh);
+    if (!mg || !op || !b || !u) return fail(CW_ERR_ARG, "cw_mg_pcg_solve: NULL argument");
+    if (op->prec != CW_PREC_F64) return fail(CW_ERR_ARG, "cw_mg_pcg_solve: the operator must be CW_PREC_F64");
+    if (op->bc != CW_BC_DIRICHLET0) return fail(CW_ERR_ARG, "cw_mg_pcg_solve: the operator must use CW_BC_DIRICHLET0");
+    const Op &top = mg_top_op(*mg);
+    if (top.mesh->nx != op->mesh->nx || top.mesh->ny != op->mesh->ny || top.mesh->nz != op->mesh->nz ||
+        top.p != op->p || top.kind != op->kind)
+        return fail(CW_ERR_ARG, "cw_mg_pcg_solve: the operator and the finest level differ in mesh, degree or kind");
+    if (!(rtol > 0.0) || maxit < 1) return fail(CW_ERR_ARG, "cw_mg_pcg_solve: rtol must be > 0 and maxit >= 1");
+    if (b == u) return fail(CW_ERR_ARG, "cw_mg_pcg_solve: b and u must not alias");
+    return solve_impl(op, b, u, rtol, maxit, CW_CG_F64, mg, stats, stream);
 }
 
 // Relative residual ||m G^T (b - A u)|| / ||m G^T b|| of a cell-wise iterate, with A evaluated by the

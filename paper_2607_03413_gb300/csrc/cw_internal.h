@@ -95,6 +95,30 @@ cudaError_t dss_from_axpy(const Op &op, void *r, const void *q, const double *al
 // solver scratch release (cw_cg.cu)
 void cg_release(Op *op);
 
+// element matrices A[e][i][j] (FP64, E * (p+1)^6 doubles) of every cell of the operator's mesh
+cudaError_t element_matrices_launch(const Op &op, double *A, cudaStream_t s);
+
+// ---- multigrid (cw_mg.cu, transfers in cw_mg_tr_*.cu)
+// uf = P uc (add: uf += P uc) between the coarse level `coarse` and its refinement `fine`
+cudaError_t mg_prolong_launch(const Op &fine, const Op &coarse, const void *uc, void *uf, bool add, cudaStream_t s);
+// bc = R (bf - vf) (vf may be NULL: bc = R bf)
+cudaError_t mg_restrict_launch(const Op &fine, const Op &coarse, const void *bf, const void *vf, void *bc,
+                               cudaStream_t s);
+cudaError_t mg_prolong_launch_df(const Op &fine, const Op &coarse, const void *uc, void *uf, bool add, cudaStream_t s);
+cudaError_t mg_restrict_launch_df(const Op &fine, const Op &coarse, const void *bf, const void *vf, void *bc,
+                                  cudaStream_t s);
+cudaError_t mg_prolong_launch_f32(const Op &fine, const Op &coarse, const void *uc, void *uf, bool add, cudaStream_t s);
+cudaError_t mg_restrict_launch_f32(const Op &fine, const Op &coarse, const void *bf, const void *vf, void *bc,
+                                   cudaStream_t s);
+cudaError_t mg_prolong_launch_f64n(const Op &fine, const Op &coarse, const void *uc, void *uf, bool add, cudaStream_t s);
+cudaError_t mg_restrict_launch_f64n(const Op &fine, const Op &coarse, const void *bf, const void *vf, void *bc,
+                                    cudaStream_t s);
+struct MgHier;
+// u = MG(b): one V-cycle on the finest level from a zero initial guess (enqueue only)
+cudaError_t mg_vcycle_zero(MgHier &h, const void *b, void *u, cudaStream_t s);
+const Op &mg_top_op(const MgHier &h);
+uint64_t mg_id(const MgHier &h);
+
 // error reporting (thread-local message)
 void set_error(const std::string &msg);
 cw_status fail(cw_status st, const std::string &msg);
