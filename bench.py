@@ -8,11 +8,12 @@ flush is needed between steps.
 
 Extra measurements in the same JSON line: the same workload in FP32 / BF16-metric / BF16, a
 degree sweep p=1..7 at ~2^27 cell-wise values (FP64, FP32 and BF16 Laplace), the Poisson CG
-time-to-1e-10 (plain FP64 Jacobi-PCG vs FP64 iterative refinement around an FP32 inner CG), and
+time-to-1e-10 (plain FP64 Jacobi-PCG vs FP64 iterative refinement around an FP32 inner CG), the
+same Poisson problem solved with the V-cycle-preconditioned CG (FP64 and FP32 cycles), and
 the batched apply (16 RHS on Q5 64^3 + 48 uneven problems in one persistent launch).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-sweep] [--no-cg]
-                  [--no-batched] [--no-mixed] [--no-e2e] [--no-cpu] [--no-tune] [--variant C,S] [--cg-mode M]
+                  [--no-batched] [--no-mg] [--no-mixed] [--no-e2e] [--no-cpu] [--no-tune] [--variant C,S] [--cg-mode M]
                   [--cells N] [--prec P]
 
 --impl reference times the FP64 CPU oracle (explicit element matrices) on a bounded cell sample of
@@ -471,6 +472,8 @@ def gpu_arm(args, rank, local, world):
         out["sweep"] = degree_sweep(cw, stream, hbm, args)
     if args.cg:
         out["cg"] = cg_bench(cw, args)
+    if args.mg:
+        out["mg"] = mg_bench(cw, args, stream)
     if args.batched:
         out["batched"] = batched_bench(cw, args, stream)
     return out
@@ -614,6 +617,71 @@ def cg_bench(cw, args):
     return res
 
 
+def mg_bench(cw, args, stream):
+    """The Poisson problem of the CG leg (Q3, u = sin(pi x) sin(pi y) sin(pi z)) on a 128^3 mesh that
+    is the 5-fold uniform refinement of a curved 4^3 mesh (0.1 h sinusoidal displacement of the coarse
+    vertices; every level's mesh nested in the next, as geometric multigrid requires): CG preconditioned
+    by one V-cycle (6 levels, 2 + 2 fused Jacobi sweeps, omega 0.7, dense coarse solve on 4^3 cells)
+    with the cycle in double-float FP64 and in FP32, against the fastest Jacobi solve (FP64 refinement
+    around an FP32 inner CG) on the same mesh; time to relative residual 1e-10 (IEEE FP64 operator)."""
+    import torch
+    p, n0, nl = 3, 4, 6
+    ms = [synth.box_mesh(n0, perturb=0.1)]
+    for _ in range(nl - 1):
+        ms.append(synth.refine(ms[-1]))
+    Ms = [cw.Mesh.from_synth(m) for m in ms]
+    fine = cw.Operator(Ms[-1], p, cw.CW_LAPLACE, cw.CW_GEOM_METRIC, cw.CW_PREC_F64, cw.CW_BC_DIRICHLET0)
+    b = fine.load_vector(0)
+    u = torch.empty_like(b)
+    res = {"workload": f"Poisson Q{p}, {ms[-1].nx}^3 cells refined {nl - 1} times from a curved {n0}^3 mesh, "
+                       f"{fine.L} cell-wise values, rtol 1e-10", "unit": "s", "levels": nl}
+    for name, prec in (("mg_f64_cycle", cw.CW_PREC_F64), ("mg_f32_cycle", cw.CW_PREC_F32)):
+        ops = [cw.Operator(M, p, cw.CW_LAPLACE, cw.CW_GEOM_METRIC, prec, cw.CW_BC_DIRICHLET0) for M in Ms[:-1]]
+        ops.append(fine if prec == cw.CW_PREC_F64 else
+                   cw.Operator(Ms[-1], p, cw.CW_LAPLACE, cw.CW_GEOM_METRIC, prec, cw.CW_BC_DIRICHLET0))
+        t0 = time.perf_counter()
+        mg = cw.Multigrid(ops, nu1=2, nu2=2, omega=0.7)
+        setup_s = time.perf_counter() - t0
+        mg.pcg_solve(fine, b, u, rtol=1e-3, maxit=50, check=False)  # warm-up: solver scratch, graph capture
+        torch.cuda.synchronize()
+        _, st, rc = mg.pcg_solve(fine, b, u, rtol=1e-10, maxit=200, check=False)
+        # one V-cycle alone on the finest level (zero initial guess), CUDA events on its stream
+        xb = ops[-1].empty()
+        xb.copy_(b.to(xb.dtype))
+        zb = ops[-1].empty()
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                cw.cw_mg_vcycle(mg.handle, xb, zb, True, stream=stream.cuda_stream)
+            e0, e1 = event_pair()
+            e0.record(stream)
+            for _ in range(10):
+                cw.cw_mg_vcycle(mg.handle, xb, zb, True, stream=stream.cuda_stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = {"seconds": st.seconds, "iterations": st.iterations, "outer": st.outer_iterations,
+                     "rel_residual": st.rel_residual, "status": int(rc),
+                     "ms_per_iteration": 1e3 * st.seconds / max(1, st.iterations),
+                     "vcycle_ms": e0.elapsed_time(e1) / 10, "setup_s": round(setup_s, 3),
+                     "rel_residual_ieee_fp64_operator": fine.residual(b, u, cw.CW_PREC_F64_NATIVE),
+                     "rel_residual_doublefloat_operator": fine.residual(b, u, cw.CW_PREC_F64)}
+        del xb, zb
+        mg.close()
+        for o in ops:
+            if o is not fine:
+                o.close()
+    fine.cg_solve(b, u, rtol=1e-3, maxit=200, mode=cw.CW_CG_IR_F32, check=False)
+    torch.cuda.synchronize()
+    _, st, rc = fine.cg_solve(b, u, rtol=1e-10, maxit=20000, mode=cw.CW_CG_IR_F32, check=False)
+    res["jacobi_ir_f32"] = {"seconds": st.seconds, "iterations": st.iterations, "outer": st.outer_iterations,
+                            "rel_residual": st.rel_residual, "status": int(rc)}
+    best = min(res["mg_f64_cycle"]["seconds"], res["mg_f32_cycle"]["seconds"])
+    res["speedup_mg_vs_jacobi_ir_f32"] = res["jacobi_ir_f32"]["seconds"] / best
+    fine.close()
+    for M in Ms:
+        M.close()
+    return res
+
+
 # ------------------------------------------------------------------------- CPU oracle ----
 def oracle_sample_rate(target_s, seed=0):
     """Times the oracle apply (explicit element matrices, K+M, p=4) on a cell sample of the 64^3
@@ -696,6 +764,7 @@ def main():
     ap.add_argument("--no-sweep", dest="sweep", action="store_false")
     ap.add_argument("--no-cg", dest="cg", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--no-mg", dest="mg", action="store_false")
     ap.add_argument("--no-mixed", dest="mixed", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")

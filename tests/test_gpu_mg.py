@@ -193,8 +193,8 @@ def test_mg_pcg_converges_to_direct_solve(cw, orc, omg, p, nl, prec):
 def test_mg_argument_errors(cw):
     import torch
     p = 2
-    m0 = synth.box_mesh(2, perturb=0.1)
-    m1 = synth.box_mesh(4, perturb=0.1)  # not the refinement of m0: vertices differ
+    m0 = synth.box_mesh(3, perturb=0.1)
+    m1 = synth.box_mesh(6, perturb=0.1)  # not the refinement of m0: the displacement scales with h
     M0, M1 = cw.Mesh.from_synth(m0), cw.Mesh.from_synth(m1)
     o0 = cw.Operator(M0, p, 1, cw.CW_GEOM_METRIC, cw.CW_PREC_F64, cw.CW_BC_DIRICHLET0)
     o1 = cw.Operator(M1, p, 1, cw.CW_GEOM_METRIC, cw.CW_PREC_F64, cw.CW_BC_DIRICHLET0)
