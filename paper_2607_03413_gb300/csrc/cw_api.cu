@@ -261,6 +261,23 @@ __global__ void gather_kernel(const double *__restrict__ ug, VS *__restrict__ x,
 }
 
 // ------------------------------------------------------------------------------- DSS ----
+// v * s with s a power of two (exact): valence scaling and the halving of the averaging passes
+template <class VS>
+struct MulOp {
+    static __device__ __forceinline__ VS mul(VS a, double s) { return static_cast<VS>(a * s); }
+};
+template <>
+struct MulOp<float> {
+    static __device__ __forceinline__ float mul(float a, double s) { return a * static_cast<float>(s); }
+};
+template <>
+struct MulOp<__nv_bfloat16> {
+    static __device__ __forceinline__ __nv_bfloat16 mul(__nv_bfloat16 a, double s)
+    {
+        return __float2bfloat16_rn(__bfloat162float(a) * static_cast<float>(s));
+    }
+};
+
 // One pass of Algorithm struct_dss along axis `ax`: for every interior interface normal to ax
 // between cells K_L and K_R = K_L + stride, s = v[K_L, face = p] + v[K_R, face = 0] is written to
 // both copies. One thread per (interface, face node); no atomics; exchange partners at static
@@ -268,7 +285,10 @@ __global__ void gather_kernel(const double *__restrict__ ug, VS *__restrict__ x,
 
 // grid: x covers (face node, first in-face cell coordinate, interface coordinate along ax),
 // y the remaining cell coordinate. All index arithmetic is 32-bit.
-template <class VS>
+// HALF: the averaging variant (S_bar): both copies receive (left + right) / 2, so that after the three
+// passes every copy holds the sum over the DoF's kappa copies divided by kappa (halving is exact; the
+// result equals the summing passes followed by the division by the valence, bit for bit).
+template <class VS, bool HALF = false>
 __global__ void dss_axis_kernel(VS *__restrict__ v, int nx, int ny, int nz, int p, int ax, uint32_t nx_thr,
                                 FastDiv fd_n2, FastDiv fd_e0)
 {
@@ -312,7 +332,8 @@ __global__ void dss_axis_kernel(VS *__restrict__ v, int nx, int ny, int nz, int 
         ir = fa + n * fb;
     }
     VS *pl = v + KL * n3 + il, *pr = v + KR * n3 + ir;
-    const VS s = AddOp<VS>::add(*pl, *pr);
+    VS s = AddOp<VS>::add(*pl, *pr);
+    if constexpr (HALF) s = MulOp<VS>::mul(s, 0.5);
     *pl = s;
     *pr = s;
     (void)nz;
@@ -321,7 +342,7 @@ __global__ void dss_axis_kernel(VS *__restrict__ v, int nx, int ny, int nz, int 
 // The x pass of Algorithm struct_dss restricted to the interfaces between tiles of `xtile`
 // consecutive cells (K_L = (b+1) xtile - 1 with K_L + 1 < E and K_L not the last cell of its x-row);
 // the interfaces inside tiles were summed by the operator kernel. One thread per (interface, face node).
-template <class VS>
+template <class VS, bool HALF = false>
 __global__ void dss_xtile_kernel(VS *__restrict__ v, int nx, int p, int xtile, int64_t E, uint32_t nthr,
                                  FastDiv fd_n2)
 {
@@ -334,51 +355,17 @@ __global__ void dss_xtile_kernel(VS *__restrict__ v, int nx, int p, int xtile, i
     if (KL + 1 >= E || KL % nx == nx - 1) return;
     const uint32_t fa = f % n, fb = f / n;
     VS *pl = v + KL * n3 + p + n * fa + n2 * fb, *pr = v + (KL + 1) * n3 + n * fa + n2 * fb;
-    const VS sum = AddOp<VS>::add(*pl, *pr);
+    VS sum = AddOp<VS>::add(*pl, *pr);
+    if constexpr (HALF) sum = MulOp<VS>::mul(sum, 0.5);
     *pl = sum;
     *pr = sum;
 }
 
-template <class VS>
-struct MulOp {
-    static __device__ __forceinline__ VS mul(VS a, double s) { return static_cast<VS>(a * s); }
-};
-template <>
-struct MulOp<__nv_bfloat16> {
-    static __device__ __forceinline__ __nv_bfloat16 mul(__nv_bfloat16 a, double s)
-    {
-        return __float2bfloat16_rn(__bfloat162float(a) * static_cast<float>(s));
-    }
-};
-
-// valence of local node (i,j,k) of cell (cx,cy,cz): product over axes of 2 on interior faces
-__device__ __forceinline__ int node_valence(int64_t cx, int64_t cy, int64_t cz, int i, int j, int k, int p, int nx,
-                                            int ny, int nz)
-{
-    int v = 1;
-    if ((i == 0 && cx > 0) || (i == p && cx < nx - 1)) v *= 2;
-    if ((j == 0 && cy > 0) || (j == p && cy < ny - 1)) v *= 2;
-    if ((k == 0 && cz > 0) || (k == p && cz < nz - 1)) v *= 2;
-    return v;
-}
-
-template <class VS>
-__global__ void scale_by_valence_kernel(VS *__restrict__ v, int nx, int ny, int nz, int p, int64_t L)
-{
-    const int n = p + 1, n3 = n * n * n;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= L) return;
-    const int64_t e = t / n3;
-    const int loc = (int)(t - e * n3), i = loc % n, j = (loc / n) % n, k = loc / (n * n);
-    const int64_t cx = e % nx, cy = (e / nx) % ny, cz = e / ((int64_t)nx * ny);
-    const int val = node_valence(cx, cy, cz, i, j, k, p, nx, ny, nz);
-    if (val > 1) v[t] = MulOp<VS>::mul(v[t], val == 2 ? 0.5 : (val == 4 ? 0.25 : 0.125));  // exact 1/val
-}
 
 // dst = src with the x pass of Algorithm struct_dss applied: an entry on an interior x-face adds its
 // partner copy in the neighbouring cell, every other entry is copied (out of place, so the read of
 // a partner never sees an updated value). Replaces a copy and an in-place x pass with one pass.
-template <class VS>
+template <class VS, bool HALF = false>
 __global__ void dss_x_from_kernel(const VS *__restrict__ src, VS *__restrict__ dst, int nx, int p, uint32_t nlines,
                                   FastDiv fd_n2, FastDiv fd_nx)
 {
@@ -394,8 +381,14 @@ __global__ void dss_x_from_kernel(const VS *__restrict__ src, VS *__restrict__ d
 #pragma unroll
     for (int i = 0; i < 8; ++i)
         if (i < n) v[i] = src[b + i];
-    if (cx > 0) v[0] = AddOp<VS>::add(src[b - n3 + p], v[0]);
-    if (cx + 1 < static_cast<uint32_t>(nx)) v[p] = AddOp<VS>::add(v[p], src[b + n3]);
+    if (cx > 0) {
+        v[0] = AddOp<VS>::add(src[b - n3 + p], v[0]);
+        if constexpr (HALF) v[0] = MulOp<VS>::mul(v[0], 0.5);
+    }
+    if (cx + 1 < static_cast<uint32_t>(nx)) {
+        v[p] = AddOp<VS>::add(v[p], src[b + n3]);
+        if constexpr (HALF) v[p] = MulOp<VS>::mul(v[p], 0.5);
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i)
         if (i < n) dst[b + i] = v[i];
@@ -458,8 +451,12 @@ static cudaError_t dss_from_typed(const Op &op, const VS *src, VS *dst, int flag
         return dss_typed(op, dst, flags, s, 0);
     }
     const uint32_t nlines = (uint32_t)(op.L / op.n);
-    dss_x_from_kernel<VS><<<(nlines + 255) / 256, 256, 0, s>>>(src, dst, m.nx, op.p, nlines, FastDiv::make(op.n * op.n),
-                                                                 FastDiv::make(m.nx));
+    if (flags == CW_DSS_AVERAGE)
+        dss_x_from_kernel<VS, true><<<(nlines + 255) / 256, 256, 0, s>>>(src, dst, m.nx, op.p, nlines,
+                                                                         FastDiv::make(op.n * op.n), FastDiv::make(m.nx));
+    else
+        dss_x_from_kernel<VS, false><<<(nlines + 255) / 256, 256, 0, s>>>(src, dst, m.nx, op.p, nlines,
+                                                                          FastDiv::make(op.n * op.n), FastDiv::make(m.nx));
     return dss_typed(op, dst, flags, s, 1);
 }
 
@@ -522,22 +519,36 @@ static cudaError_t dss_typed(const Op &op, VS *v, int flags, cudaStream_t s, int
         const uint32_t nthr = (uint32_t)n2 * e0 * (uint32_t)(dims[ax] - 1);
         const int bs = 256;
         dim3 grid((nthr + bs - 1) / bs, dims[b]);
+        const bool half = flags == CW_DSS_AVERAGE;  // averaging passes: (left + right) / 2 to both copies
         if (ax == 0 && xtile > 1) {  // only the x-interfaces between tiles are left
             const int64_t nb = (op.E / xtile) * n2;  // interface K_L = (b+1) xtile - 1, b < E/xtile
             if (nb >= ((int64_t)1 << 32)) return cudaErrorInvalidValue;  // callers fuse only below this
-            if (nb > 0)
-                dss_xtile_kernel<VS><<<(unsigned)((nb + bs - 1) / bs), bs, 0, s>>>(
-                    v, m.nx, op.p, xtile, op.E, (uint32_t)nb, FastDiv::make(n2));
+            if (nb > 0) {
+                const unsigned g = (unsigned)((nb + bs - 1) / bs);
+                if (half)
+                    dss_xtile_kernel<VS, true><<<g, bs, 0, s>>>(v, m.nx, op.p, xtile, op.E, (uint32_t)nb, FastDiv::make(n2));
+                else
+                    dss_xtile_kernel<VS, false><<<g, bs, 0, s>>>(v, m.nx, op.p, xtile, op.E, (uint32_t)nb, FastDiv::make(n2));
+            }
             continue;
         }
-        dss_axis_kernel<VS><<<grid, bs, 0, s>>>(v, m.nx, m.ny, m.nz, op.p, ax, nthr, FastDiv::make(n2),
-                                                FastDiv::make(e0));
-    }
-    if (flags == CW_DSS_AVERAGE) {
-        const int bs = 256;
-        scale_by_valence_kernel<VS><<<(unsigned)((op.L + bs - 1) / bs), bs, 0, s>>>(v, m.nx, m.ny, m.nz, op.p, op.L);
+        if (half)
+            dss_axis_kernel<VS, true><<<grid, bs, 0, s>>>(v, m.nx, m.ny, m.nz, op.p, ax, nthr, FastDiv::make(n2),
+                                                          FastDiv::make(e0));
+        else
+            dss_axis_kernel<VS, false><<<grid, bs, 0, s>>>(v, m.nx, m.ny, m.nz, op.p, ax, nthr, FastDiv::make(n2),
+                                                           FastDiv::make(e0));
     }
     return cudaGetLastError();
+}
+
+cudaError_t dss_average_launch(const Op &op, void *v, cudaStream_t s, int xtile)
+{
+    switch (vec_elem_size(op.prec)) {
+    case 8: return dss_typed(op, static_cast<double *>(v), CW_DSS_AVERAGE, s, 0, 3, xtile);
+    case 4: return dss_typed(op, static_cast<float *>(v), CW_DSS_AVERAGE, s, 0, 3, xtile);
+    default: return dss_typed(op, static_cast<__nv_bfloat16 *>(v), CW_DSS_AVERAGE, s, 0, 3, xtile);
+    }
 }
 
 cudaError_t dss_launch(const Op &op, void *v, int flags, cudaStream_t s, int xtile)

@@ -275,11 +275,18 @@ __host__ __device__ constexpr size_t metric_smem_bytes(int nc, int stage)
 // point is recomputed from them (Sec. 6: J, det J, J^-1 at the point): G = (w / det J) [c_a . c_b]
 // with c_0 = J_eta x J_zeta, c_1 = J_zeta x J_xi, c_2 = J_xi x J_eta (the rows of det J J^-1), and
 // the mass coefficient w det J.
-template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool DOT = false, bool RC = false>
-__device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__restrict__ y, const GS *__restrict__ geo,
+// SMOOTH (Algorithm smoother_fused in one pass over the operator's output): y aliases x (= u, updated
+// in place), and the stored value is u + D_hat (b - A u) (sb = b, sd = D_hat, cell-wise in the vector
+// type), with the x-interfaces inside the tile averaged (the x pass of the averaging DSS:
+// (left + right) / 2 to both copies; asm_nx must be the mesh's cells per x-row). Each thread re-reads
+// u, b and D_hat on the x-line it stores, with plain loads (y aliases x). The operator output never
+// reaches memory.
+template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool DOT = false, bool RC = false,
+          bool SMOOTH = false>
+__device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__restrict__ geo,
                                             int64_t ncells, int kind, const TabMetric<N, typename Ar::C> &tab,
                                             int64_t tile, int cpt, unsigned char *smem_raw, df64 *dot = nullptr,
-                                            int asm_nx = 0)
+                                            int asm_nx = 0, const VS *sb = nullptr, const VS *sd = nullptr)
 {
     static_assert(!(RC && STAGE == 1), "recomputed geometry has no metric tile to stage");
     // Double-float renormalisation of the intermediate values: kept where the operator serves the
@@ -571,7 +578,28 @@ __device__ __forceinline__ void metric_tile(const VS *__restrict__ x, VS *__rest
         {
             CW_LDX(s0, v);
             sweep<N, Ar, 1, NRM>(tab, v, w);
-            if (asm_nx > 0) {  // kernel-uniform
+            if constexpr (SMOOTH) {
+                VS nv[N];
+                const int64_t o = (act ? cell : 0) * N3 + N * r;
+#pragma unroll
+                for (int m = 0; m < N; ++m) {
+                    VS av;
+                    Ar::to(av, w[m]);
+                    nv[m] = act ? y[o + m] + sd[o + m] * (sb[o + m] - av) : VS(0);
+                }
+                VS *exl = reinterpret_cast<VS *>(S0 + CPB * CS), *exr = exl + CPB * N2;  // S1 is free
+                exl[c * N2 + r] = nv[0];
+                exr[c * N2 + r] = nv[N - 1];
+                __syncthreads();
+                if (act) {
+                    const int64_t cx = cell % asm_nx;
+                    if (c + 1 < cpt && cell + 1 < ncells && cx + 1 < asm_nx)
+                        nv[N - 1] = AddOp<VS>::add(nv[N - 1], exl[(c + 1) * N2 + r]) * VS(0.5);
+                    if (c > 0 && cx > 0) nv[0] = AddOp<VS>::add(exr[(c - 1) * N2 + r], nv[0]) * VS(0.5);
+#pragma unroll
+                    for (int m = 0; m < N; ++m) y[o + m] = nv[m];
+                }
+            } else if (asm_nx > 0) {  // kernel-uniform
                 VS o0, o1;
                 Ar::to(o0, w[0]);
                 Ar::to(o1, w[N - 1]);
@@ -673,6 +701,20 @@ __global__ void __launch_bounds__(N *N *CPB) apply_metric_dot_kernel(const VS *_
         for (int i = 0; i < (N * N * CPB + 31) / 32; ++i) t += s_red[i];
         part[blockIdx.x] = t;
     }
+}
+
+// One fused smoothing sweep on a tile (see SMOOTH in metric_tile): u <- x-average(u + D_hat (b - A u)),
+// in place; the x pass between tiles and the y and z passes of the averaging DSS follow.
+template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool RC = false>
+__global__ void __launch_bounds__(N *N *CPB) smooth_metric_kernel(VS *u, const VS *__restrict__ b,
+                                                                   const VS *__restrict__ dhat,
+                                                                   const GS *__restrict__ geo, int64_t ncells,
+                                                                   int kind, TabMetric<N, typename Ar::C> tab,
+                                                                   int asm_nx)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    metric_tile<N, CPB, Ar, VS, GS, STAGE, false, RC, true>(u, u, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw,
+                                                            nullptr, asm_nx, b, dhat);
 }
 
 // ---------------------------------------------------------------------- Cartesian kernel ----

@@ -113,6 +113,13 @@ cudaError_t mg_restrict_launch_f32(const Op &fine, const Op &coarse, const void 
 cudaError_t mg_prolong_launch_f64n(const Op &fine, const Op &coarse, const void *uc, void *uf, bool add, cudaStream_t s);
 cudaError_t mg_restrict_launch_f64n(const Op &fine, const Op &coarse, const void *bf, const void *vf, void *bc,
                                     cudaStream_t s);
+// one fused smoothing sweep on curved cells (metric stored or recomputed), in place on u: the operator
+// epilogue forms u + D_hat (b - A u) and averages the x-interfaces inside each tile of *xfuse cells
+cudaError_t mg_smooth_launch_df(const Op &op, void *u, const void *b, const void *dhat, cudaStream_t s, int *xfuse);
+cudaError_t mg_smooth_launch_f32(const Op &op, void *u, const void *b, const void *dhat, cudaStream_t s, int *xfuse);
+// the averaging DSS (every pass halves its pair sums, so no separate division by the valence) with the
+// x pass restricted to the interfaces between tiles of xtile cells (0: all)
+cudaError_t dss_average_launch(const Op &op, void *v, cudaStream_t s, int xtile);
 struct MgHier;
 // u = MG(b): one V-cycle on the finest level from a zero initial guess (enqueue only)
 cudaError_t mg_vcycle_zero(MgHier &h, const void *b, void *u, cudaStream_t s);

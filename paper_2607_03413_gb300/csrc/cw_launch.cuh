@@ -191,6 +191,48 @@ cudaError_t launch_metric(const Op &op, const void *x, void *y, cudaStream_t s, 
     return cudaGetLastError();
 }
 
+// One fused smoothing sweep (smooth_metric_kernel): default tile, input tile staged by TMA and the
+// metric prefetched into L2 (stage 2); the x-interfaces inside tiles are averaged, *xfuse receives the
+// tile size for the x pass between tiles.
+template <int N, class Ar, class VS, class GS, bool RC>
+cudaError_t launch_smooth(const Op &op, void *u, const void *b, const void *dhat, cudaStream_t s, int *xfuse)
+{
+    constexpr int CPB = cpb_default<N>();
+    TabMetric<N, typename Ar::C> tab;
+    fill_metric_tab<N>(tab, op.tab, [](double v) { return MakeC<Ar>::from(v); });
+    const size_t smem = metric_smem_bytes<N, CPB, typename Ar::T, GS>(metric_ncomp(op.kind), 2);
+    auto kern = smooth_metric_kernel<N, CPB, Ar, VS, GS, 2, RC>;
+    static size_t opted[kMaxDevices] = {};
+    if (cudaError_t e = ensure_smem(kern, smem, opted); e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((op.E + CPB - 1) / CPB);
+    *xfuse = CPB;
+    kern<<<grid, N * N * CPB, smem, s>>>(static_cast<VS *>(u), static_cast<const VS *>(b),
+                                         static_cast<const VS *>(dhat), static_cast<const GS *>(op.d_geo), op.E,
+                                         op.kind, tab, op.mesh->nx);
+    return cudaGetLastError();
+}
+
+template <class Ar, class VS, class GS>
+cudaError_t launch_smooth_degree(const Op &op, void *u, const void *b, const void *dhat, cudaStream_t s, int *xfuse)
+{
+    using GC = typename RCStore<Ar>::type;
+    const bool rc = op.geom == CW_GEOM_RECOMPUTE;
+#define CW_SM(NN) \
+    return rc ? launch_smooth<NN, Ar, VS, GC, true>(op, u, b, dhat, s, xfuse) \
+              : launch_smooth<NN, Ar, VS, GS, false>(op, u, b, dhat, s, xfuse)
+    switch (op.n) {
+    case 2: CW_SM(2);
+    case 3: CW_SM(3);
+    case 4: CW_SM(4);
+    case 5: CW_SM(5);
+    case 6: CW_SM(6);
+    case 7: CW_SM(7);
+    case 8: CW_SM(8);
+    }
+#undef CW_SM
+    return cudaErrorInvalidValue;
+}
+
 // y = A x with the CTA partials of <x, y> written to part (default tile size, TMA staging);
 // *nblocks receives the number of partials
 template <int N, class Ar, class VS, class GS, bool RC = false>

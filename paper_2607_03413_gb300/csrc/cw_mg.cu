@@ -150,6 +150,19 @@ static cudaError_t restrict_(const MgHier &h, int l, const void *bf, const void 
     }
 }
 
+// Whether a sweep can run as one operator launch with the Jacobi update and the in-tile x averages in
+// its epilogue (curved cells in double-float or FP32 arithmetic; the x pass between tiles then indexes
+// its interfaces with 32 bits)
+static bool fused_sweep(const MgHier &h, const Op &op)
+{
+    return (h.prec == CW_PREC_F64 || h.prec == CW_PREC_F32) && op.geom != CW_GEOM_AFFINE &&
+           op.E * (int64_t)(op.n * op.n) < ((int64_t)1 << 32);
+}
+
+// `sweeps` sweeps of Algorithm smoother_fused: u <- S_bar (u + D_hat (b - A u)). The first sweep from
+// u = 0 (zero) is u = S_bar D_hat b. A fused sweep is one operator launch whose epilogue applies the
+// update and the x averages inside its tiles, then the x pass between tiles and the y and z passes of
+// the averaging DSS; otherwise operator, update kernel and the three averaging passes.
 template <class VS>
 static cudaError_t smooth_t(const MgHier &h, int l, const VS *b, VS *u, int sweeps, bool zero, cudaStream_t s)
 {
@@ -157,16 +170,21 @@ static cudaError_t smooth_t(const MgHier &h, int l, const VS *b, VS *u, int swee
     const Op &op = *L.op;
     const VS *dh = static_cast<const VS *>(L.dhat);
     VS *v = static_cast<VS *>(L.v);
+    const bool fused = fused_sweep(h, op);
     for (int k = 0; k < sweeps; ++k) {
+        cudaError_t e;
+        int xtile = 0;
         if (zero && k == 0) {
             k_jacobi_zero<VS><<<vgrid(op.L), 256, 0, s>>>(u, b, dh, op.L);
-        } else {
-            cudaError_t e = apply_local(op, u, v, s);
+        } else if (fused) {
+            e = h.prec == CW_PREC_F64 ? mg_smooth_launch_df(op, u, b, dh, s, &xtile)
+                                      : mg_smooth_launch_f32(op, u, b, dh, s, &xtile);
             if (e != cudaSuccess) return e;
+        } else {
+            if ((e = apply_local(op, u, v, s)) != cudaSuccess) return e;
             k_jacobi<VS><<<vgrid(op.L), 256, 0, s>>>(u, b, v, dh, op.L);
         }
-        cudaError_t e = dss_launch(op, u, CW_DSS_AVERAGE, s);
-        if (e != cudaSuccess) return e;
+        if ((e = dss_average_launch(op, u, s, xtile)) != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }

@@ -110,12 +110,16 @@ def test_coarse_solve_and_smoother_match_oracle(cw, orc, omg, p, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["doublefloat", "ieee_f64"])
-@pytest.mark.parametrize("p,perturb", [(1, 0.3), (2, 0.3), (3, 0.0), (3, 0.2)])
-def test_vcycle_matches_oracle(cw, orc, omg, p, perturb, prec):
+@pytest.mark.parametrize("p,perturb,geom", [(1, 0.3, 1), (2, 0.3, 1), (3, 0.0, 1), (3, 0.2, 1), (2, 0.3, 2),
+                                            (3, 0.0, 0)], ids=["p1", "p2", "p3cart", "p3", "p2recomputed",
+                                                               "p3affine"])
+def test_vcycle_matches_oracle(cw, orc, omg, p, perturb, geom, prec):
     """One V-cycle on three levels, from zero and from a continuous initial guess, against the
-    oracle's cell-wise V-cycle in the fused form."""
+    oracle's cell-wise V-cycle in the fused form (stored and recomputed metric: sweeps fused into the
+    operator launch in double-float; Cartesian cells and IEEE FP64: operator, update and averaging
+    passes as separate launches)."""
     ms = meshes(synth.box_mesh(2, 3, 2, perturb=perturb), 3)
-    Ms, ops, mg = gpu_hierarchy(cw, ms, p, prec)
+    Ms, ops, mg = gpu_hierarchy(cw, ms, p, prec, geom=geom)
     lv = omg.hierarchy(ms, p, 1)
     m = ms[2]
     b = synth.cellwise_random(m, p, seed=5)
@@ -128,7 +132,7 @@ def test_vcycle_matches_oracle(cw, orc, omg, p, perturb, prec):
     assert rel_err(to_np(ud), omg.vcycle(lv, 2, b, u0, fused=True)) <= 1e-11
 
 
-@pytest.mark.parametrize("p", [2, 3])
+@pytest.mark.parametrize("p", [2, 3, 5])
 def test_fp32_vcycle_matches_oracle_fp32_cycle(cw, orc, omg, p):
     """The FP32 cycle against the oracle's FP32-storage cycle (every vector rounded to FP32 after each
     step, FP64 arithmetic within a step): agreement to FP32 rounding, far from the FP64 result's
