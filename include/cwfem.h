@@ -202,6 +202,26 @@ cw_status cw_op_get_variant(cw_op op, int *cells_per_cta, int *stage, int *choic
  */
 cw_status cw_op_autotune(cw_op op, const void *x, void *y, int reps, void *stream, float *best_ms);
 
+/*
+ * Device-side failure report. The operator kernels move tiles into shared memory with bulk copies
+ * (TMA) completed on mbarriers, and every wait for such a copy is bounded. If a wait expires, the CTA
+ * abandons its tile (no output written for it; no staged data that was not seen to arrive is ever
+ * read), waits (bounded) for the copies it issued, and records the event in the operator's device
+ * status word. cw_op_check synchronises `stream` and returns CW_ERR_TIMEOUT (clearing the word) if
+ * that happened since the last check, else CW_OK; the calls that synchronise anyway (cw_cg_solve,
+ * cw_cg_residual, cw_mg_pcg_solve, cw_cg_solve_noalloc, cw_op_autotune, cw_batch_autotune,
+ * cw_apply_batched) check their operators' words themselves. The CUDA context stays usable.
+ */
+cw_status cw_op_check(cw_op op, void *stream);
+/*
+ * Fault-injection hook for tests of the failure report (on != 0 arms it, 0 disarms it): the
+ * operator's kernels then arm the barrier of each staged input tile with 16 bytes more than the copy
+ * delivers, so the copy lands but the barrier phase can never complete, the (shortened) bounded wait
+ * runs out and the tile is abandoned and reported as above. Tiles read without staging (stage 0, a
+ * ragged last tile) are not affected. Not for production use.
+ */
+cw_status cw_op_inject_stall(cw_op op, int on);
+
 /* x = G u: replicate a device global FP64 vector into cell-wise storage of the op's precision. */
 cw_status cw_gather(cw_op op, const double *u_global, void *x, void *stream);
 

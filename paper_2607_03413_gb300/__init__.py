@@ -37,7 +37,7 @@ EXPORTED = [
     "cw_batch_get_variant", "cw_batch_autotune", "cw_batch_set_mode", "cw_apply_batched", "cw_apply_host",
     "cw_mesh_refine_vertices", "cw_rules_1d", "cw_basis_1d", "cw_cg_residual", "cw_mg_create", "cw_mg_destroy",
     "cw_mg_device_bytes", "cw_mg_vcycle", "cw_mg_prolong", "cw_mg_restrict", "cw_mg_smooth", "cw_mg_coarse_solve",
-    "cw_mg_pcg_solve",
+    "cw_mg_pcg_solve", "cw_op_check", "cw_op_inject_stall",
 ]
 
 
@@ -105,6 +105,8 @@ def load(path: str = LIB_PATH):
         "cw_rules_1d": ([i32, vp, vp, vp], i32),
         "cw_basis_1d": ([i32, vp, vp, vp, vp, vp], i32),
         "cw_cg_residual": ([vp, vp, vp, i32, ctypes.POINTER(dbl), vp], i32),
+        "cw_op_check": ([vp, vp], i32),
+        "cw_op_inject_stall": ([vp, i32], i32),
         "cw_mg_create": ([ctypes.POINTER(vp), i32, i32, i32, dbl, ctypes.POINTER(vp)], i32),
         "cw_mg_destroy": ([vp], i32),
         "cw_mg_device_bytes": ([vp], i64),
@@ -279,6 +281,15 @@ def cw_cg_solve_noalloc(op, b, u, rtol=1e-10, maxit=10000, mode=CW_CG_F64, strea
     st = cw_cg_stats()
     rc = load().cw_cg_solve_noalloc(op, _ptr(b), _ptr(u), rtol, maxit, mode, ctypes.byref(st), _stream(stream))
     return rc, st
+
+
+def cw_op_check(op, stream=None):
+    """CW_OK, or CW_ERR_TIMEOUT if a bounded wait of the operator's kernels expired since the last check."""
+    return load().cw_op_check(op, _stream(stream))
+
+
+def cw_op_inject_stall(op, on=True):
+    _check(load().cw_op_inject_stall(op, int(bool(on))), "cw_op_inject_stall")
 
 
 def cw_op_set_variant(op, cells_per_cta, stage):

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -36,6 +37,10 @@ cw_status cuda_fail(cudaError_t e, const char *where)
     }
     return CW_ERR_CUDA;
 }
+
+static std::atomic<uint64_t> g_op_generation{0};
+uint64_t op_generation() { return g_op_generation.load(); }
+void op_generation_bump() { g_op_generation.fetch_add(1); }
 
 size_t vec_elem_size(int prec)
 {
@@ -1015,7 +1020,15 @@ cw_status cw_op_create(cw_mesh mh, int degree, int kind, int geom, int prec, int
         delete op;
         return cuda_fail(e, "cw_op_create");
     }
-    op->owned_bytes = op->geo_bytes;
+    e = cudaMalloc(&op->d_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(op->d_status, 0, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        cudaFree(op->d_status);
+        cudaFree(op->d_geo);
+        delete op;
+        return cuda_fail(e, "cw_op_create");
+    }
+    op->owned_bytes = op->geo_bytes + (int64_t)sizeof(unsigned);
     *out = reinterpret_cast<cw_op>(op);
     return CW_OK;
 }
@@ -1037,6 +1050,7 @@ cw_status cw_op_destroy(cw_op oh)
     if (op->h_done) cudaEventDestroy(op->h_done);
     cudaFree(op->d_geo);
     cudaFree(op->d_dinv);
+    cudaFree(op->d_status);
     delete op;
     return CW_OK;
 }
@@ -1133,7 +1147,38 @@ cw_status cw_load_vector(cw_op oh, int which, double *b, void *stream)
 
 }  // extern "C"
 
+namespace cw {
+cw_status op_status_take(Op *op, cudaStream_t s, const char *where)
+{
+    if (!op || !op->d_status) return CW_OK;
+    unsigned w = 0;
+    CW_CUDA_TRY(cudaMemcpyAsync(&w, op->d_status, sizeof w, cudaMemcpyDeviceToHost, s));
+    CW_CUDA_TRY(cudaStreamSynchronize(s));
+    if (w == 0) return CW_OK;
+    CW_CUDA_TRY(cudaMemsetAsync(op->d_status, 0, sizeof(unsigned), s));
+    CW_CUDA_TRY(cudaStreamSynchronize(s));
+    return fail(CW_ERR_TIMEOUT, std::string(where) +
+                                    ": a bounded wait for a staged tile expired (the tile was left without output)");
+}
+}  // namespace cw
+
 extern "C" {
+
+cw_status cw_op_check(cw_op oh, void *stream)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    if (!op) return fail(CW_ERR_ARG, "cw_op_check: NULL handle");
+    return op_status_take(op, static_cast<cudaStream_t>(stream), "cw_op_check");
+}
+
+cw_status cw_op_inject_stall(cw_op oh, int on)
+{
+    Op *op = reinterpret_cast<Op *>(oh);
+    if (!op) return fail(CW_ERR_ARG, "cw_op_inject_stall: NULL handle");
+    op->dbg_tma_extra = on ? 16u : 0u;
+    op_generation_bump();
+    return CW_OK;
+}
 
 cw_status cw_op_set_variant(cw_op oh, int cells_per_cta, int stage)
 {
@@ -1150,6 +1195,7 @@ cw_status cw_op_set_variant(cw_op oh, int cells_per_cta, int stage)
         return fail(CW_ERR_UNSUPPORTED, "cw_op_set_variant: CW_GEOM_RECOMPUTE uses the default cells per CTA");
     op->cpb = cells_per_cta == ch[0] ? 0 : cells_per_cta;
     op->stage = stage;
+    op_generation_bump();
     return CW_OK;
 }
 
@@ -1224,8 +1270,9 @@ cw_status cw_op_autotune(cw_op oh, const void *x, void *y, int reps, void *strea
     cudaEventDestroy(e1);
     op->cpb = bc;
     op->stage = bs;
+    op_generation_bump();
     if (best_ms) *best_ms = best;
-    return CW_OK;
+    return op_status_take(op, s, "cw_op_autotune");
 }
 
 }  // extern "C"

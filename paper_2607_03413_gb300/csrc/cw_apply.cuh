@@ -281,12 +281,21 @@ __host__ __device__ constexpr size_t metric_smem_bytes(int nc, int stage)
 // (left + right) / 2 to both copies; asm_nx must be the mesh's cells per x-row). Each thread re-reads
 // u, b and D_hat on the x-line it stores, with plain loads (y aliases x). The operator output never
 // reaches memory.
+// Staged tiles and their waits: every wait is bounded and its outcome is made block-uniform
+// (__syncthreads_and). If a copy did not complete within the bound, the CTA abandons the tile: it
+// writes no output, thread 0 records kDevStatusTimeout in *status (the operator's device status word,
+// reported as CW_ERR_TIMEOUT by the next checking call), waits (bounded) for the copies it issued so
+// that none lands after the tile is left, and the function returns false. No path reads a staged
+// tile whose copy has not been seen to complete. dbg_extra > 0 (fault injection for tests) arms the
+// input tile's barrier with dbg_extra bytes more than the copy delivers, so that its phase can never
+// complete and the (then short) bounded wait runs out.
 template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool DOT = false, bool RC = false,
           bool SMOOTH = false>
-__device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__restrict__ geo,
+__device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__restrict__ geo,
                                             int64_t ncells, int kind, const TabMetric<N, typename Ar::C> &tab,
                                             int64_t tile, int cpt, unsigned char *smem_raw, df64 *dot = nullptr,
-                                            int asm_nx = 0, const VS *sb = nullptr, const VS *sd = nullptr)
+                                            int asm_nx = 0, const VS *sb = nullptr, const VS *sd = nullptr,
+                                            unsigned *status = nullptr, uint32_t dbg_extra = 0)
 {
     static_assert(!(RC && STAGE == 1), "recomputed geometry has no metric tile to stage");
     // Double-float renormalisation of the intermediate values: kept where the operator serves the
@@ -314,6 +323,15 @@ __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__rest
     const VS *xs = nullptr;
     const GS *gs = nullptr;
     uint64_t *bar = nullptr;
+    const uint32_t lim = dbg_extra ? kWaitLimitInjected : kWaitLimit;
+    // expired wait: report, drain the issued copies (bounded), leave the tile without output
+    auto abandon = [&](int b0, int b1) {  // barriers [b0, b1) still owe their copies
+        if (t == 0) {
+            if (status) atomicOr(status, kDevStatusTimeout);
+            for (int b = b0; b < b1; ++b) mbar_wait_bounded(bar + b, 0, lim);
+        }
+        __syncthreads();
+    };
     if constexpr (STAGE == 1) {
         const size_t offg = (3 * CPB * CS * sizeof(T) + 15) / 16 * 16;
         GS *sG = reinterpret_cast<GS *>(smem_raw + offg);
@@ -331,15 +349,19 @@ __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__rest
             }
             __syncthreads();
             if (t == 0) {
-                mbar_expect_tx(bar, xb);
+                mbar_expect_tx(bar, xb + dbg_extra);
                 bulk_g2s(sX, xsrc, xb, bar);
                 mbar_expect_tx(bar + 1, gb);
                 bulk_g2s(sG, gsrc, gb, bar + 1);
             }
-            x_smem = mbar_wait_bounded(bar, 0);
+            if (!__syncthreads_and(mbar_wait_bounded(bar, 0, lim))) {
+                abandon(0, 2);
+                return false;
+            }
+            x_smem = true;
             xs = sX + c * N3;
             gs = sG + c * NC * N3;
-            g_smem = true;  // decided at the physics step
+            g_smem = true;  // its wait comes at the physics step
         }
     } else if constexpr (STAGE == 2) {
         bar = reinterpret_cast<uint64_t *>(smem_raw + (3 * CPB * CS * sizeof(T) + 15) / 16 * 16);
@@ -356,10 +378,14 @@ __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__rest
             if (t == 0) mbar_init(bar, 1);
             __syncthreads();
             if (t == 0) {
-                mbar_expect_tx(bar, xb);
+                mbar_expect_tx(bar, xb + dbg_extra);
                 bulk_g2s(sX, xsrc, xb, bar);
             }
-            x_smem = mbar_wait_bounded(bar, 0);
+            if (!__syncthreads_and(mbar_wait_bounded(bar, 0, lim))) {
+                abandon(0, 1);
+                return false;
+            }
+            x_smem = true;
             xs = sX + c * N3;
         }
     }
@@ -417,7 +443,10 @@ __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__rest
         }
         // (4) quadrature-point physics on the owned pencil, qp = (ra, rb, k)
         if constexpr (STAGE == 1) {
-            if (g_smem) g_smem = mbar_wait_bounded(bar + 1, 0);
+            if (g_smem && !__syncthreads_and(mbar_wait_bounded(bar + 1, 0, lim))) {  // g_smem is block-uniform
+                abandon(1, 2);
+                return false;
+            }
         }
         {
             const GS *gc = g_smem ? gs + r : geo + (act ? cell : 0) * (RC ? kTriCoef : NC * N3) + (RC ? 0 : r);
@@ -626,13 +655,7 @@ __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__rest
             }
         }
     }
-    if constexpr (STAGE == 1) {
-        // a copy that missed its wait bound must not land in shared memory after exit
-        if (xs != nullptr && (!x_smem || !g_smem)) {
-            mbar_wait_bounded(bar, 0);
-            mbar_wait_bounded(bar + 1, 0);
-        }
-    }
+    return true;
 }
 
 // Register caps for the double-float kernels (as CTAs per SM for the launch bounds): stored metric
@@ -657,21 +680,22 @@ template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool RC = fal
 __global__ void __launch_bounds__(N *N *CPB) apply_metric_kernel(const VS *__restrict__ x, VS *__restrict__ y,
                                                                   const GS *__restrict__ geo, int64_t ncells,
                                                                   int kind, TabMetric<N, typename Ar::C> tab,
-                                                                  int asm_nx)
+                                                                  int asm_nx, unsigned *status, uint32_t dbg_extra)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     metric_tile<N, CPB, Ar, VS, GS, STAGE, false, RC>(x, y, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw, nullptr,
-                                                      asm_nx);
+                                                      asm_nx, nullptr, nullptr, status, dbg_extra);
 }
 
 template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool RC = false>
 __global__ void __launch_bounds__(N *N *CPB, (df_min_blocks<N * N * CPB, RC>()))
     apply_metric_kernel_capped(const VS *__restrict__ x, VS *__restrict__ y, const GS *__restrict__ geo,
-                               int64_t ncells, int kind, TabMetric<N, typename Ar::C> tab, int asm_nx)
+                               int64_t ncells, int kind, TabMetric<N, typename Ar::C> tab, int asm_nx,
+                               unsigned *status, uint32_t dbg_extra)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     metric_tile<N, CPB, Ar, VS, GS, STAGE, false, RC>(x, y, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw, nullptr,
-                                                      asm_nx);
+                                                      asm_nx, nullptr, nullptr, status, dbg_extra);
 }
 
 // y = A x and the CTA's partial of <x, A x> in part[blockIdx.x] (deterministic: fixed order in a CTA)
@@ -679,12 +703,14 @@ template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool RC = fal
 __global__ void __launch_bounds__(N *N *CPB) apply_metric_dot_kernel(const VS *__restrict__ x, VS *__restrict__ y,
                                                                       const GS *__restrict__ geo, int64_t ncells,
                                                                       int kind, TabMetric<N, typename Ar::C> tab,
-                                                                      double *__restrict__ part)
+                                                                      double *__restrict__ part, unsigned *status,
+                                                                      uint32_t dbg_extra)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double s_red[(N * N * CPB + 31) / 32];
     df64 acc{0.0f, 0.0f};
-    metric_tile<N, CPB, Ar, VS, GS, STAGE, true, RC>(x, y, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw, &acc);
+    metric_tile<N, CPB, Ar, VS, GS, STAGE, true, RC>(x, y, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw, &acc, 0,
+                                                     nullptr, nullptr, status, dbg_extra);
     double v = df_to_double(acc);
     // N^2 * CPB is not always a multiple of 32: the last warp may hold only nw lanes
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -710,11 +736,11 @@ __global__ void __launch_bounds__(N *N *CPB) smooth_metric_kernel(VS *u, const V
                                                                    const VS *__restrict__ dhat,
                                                                    const GS *__restrict__ geo, int64_t ncells,
                                                                    int kind, TabMetric<N, typename Ar::C> tab,
-                                                                   int asm_nx)
+                                                                   int asm_nx, unsigned *status, uint32_t dbg_extra)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     metric_tile<N, CPB, Ar, VS, GS, STAGE, false, RC, true>(u, u, geo, ncells, kind, tab, blockIdx.x, CPB, smem_raw,
-                                                            nullptr, asm_nx, b, dhat);
+                                                            nullptr, asm_nx, b, dhat, status, dbg_extra);
 }
 
 // ---------------------------------------------------------------------- Cartesian kernel ----

@@ -72,6 +72,7 @@ static cw_status batch_rebuild(Batch &b)
         P.x = b.x[i];
         P.y = b.y[i];
         P.geo = o.d_geo;
+        P.status = o.d_status;
         P.ncells = o.E;
         P.stride = o.L;
         P.n = o.n;
@@ -327,7 +328,10 @@ cw_status cw_batch_autotune(cw_batch bh, int reps, void *stream, float *best_ms)
     }
     cw_status st = batch_rebuild(*b);
     if (best_ms) *best_ms = best_all;
-    return st;
+    if (st != CW_OK) return st;
+    for (Op *o : b->ops)
+        if ((st = op_status_take(o, static_cast<cudaStream_t>(stream), "cw_batch_autotune")) != CW_OK) return st;
+    return CW_OK;
 }
 
 cw_status cw_apply_batched(const cw_op *ops, const void *const *x, void *const *y, const int *nrhs, int nprob,
@@ -350,6 +354,8 @@ cw_status cw_apply_batched(const cw_op *ops, const void *const *x, void *const *
     cw_batch_destroy(b);
     if (st != CW_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "cw_apply_batched");
+    for (int i = 0; i < nprob; ++i)  // an expired bounded wait left a tile without output
+        if ((st = op_status_take(reinterpret_cast<Op *>(ops[i]), s, "cw_apply_batched")) != CW_OK) return st;
     return CW_OK;
 }
 

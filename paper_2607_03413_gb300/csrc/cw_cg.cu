@@ -52,6 +52,7 @@ struct CgLevel {  // vectors of one precision level
     const void *graph_u = nullptr;    // iterate pointer the graph was captured with
     const Op *graph_op = nullptr;     // operator the graph was captured with
     int graph_ak = -1;                // operator evaluation the graph was captured with
+    uint64_t graph_gen = 0;           // operator generation (kernel choices) at capture
 };
 
 struct CgScratch {
@@ -77,6 +78,7 @@ struct CgScratch {
     uint64_t mg_graph_id = 0;
     const void *mg_graph_d = nullptr;
     const Op *mg_graph_op = nullptr;
+    uint64_t mg_graph_gen = 0;
 };
 
 // ---------------------------------------------------------------------------- kernels ----
@@ -725,7 +727,7 @@ static cw_status cg_run(const Op &aop, int ak, CgLevel &lv, U *u, CgScratch &c, 
     CW_CUDA_TRY(cudaGetLastError());
     // one eager iteration (first-use initialisation of the kernels), then graph batches
     CW_CUDA_TRY((cg_iteration<V, U>(aop, ak, lv, u, c, s)));
-    if (lv.graph && (lv.graph_u != u || lv.graph_op != &aop || lv.graph_ak != ak)) {
+    if (lv.graph && (lv.graph_u != u || lv.graph_op != &aop || lv.graph_ak != ak || lv.graph_gen != op_generation())) {
         cudaGraphExecDestroy(lv.graph);
         lv.graph = nullptr;
     }
@@ -743,6 +745,7 @@ static cw_status cg_run(const Op &aop, int ak, CgLevel &lv, U *u, CgScratch &c, 
         lv.graph_u = u;
         lv.graph_op = &aop;
         lv.graph_ak = ak;
+        lv.graph_gen = op_generation();
     }
     for (;;) {
         CW_CUDA_TRY(cudaMemcpyAsync(c.h_flags, c.flags, F_NFLAG * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -871,7 +874,8 @@ static cw_status mgcg_run(const Op &aop, MgHier &h, CgLevel &lv, double *d, CgSc
     CW_CUDA_TRY(cudaMemcpyAsync(p, z, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CW_CUDA_TRY(cudaGetLastError());
     CW_CUDA_TRY(mgcg_iteration(aop, h, lv, d, c, f32, s));  // eager: first-use initialisation
-    if (c.mg_graph && (c.mg_graph_id != mg_id(h) || c.mg_graph_d != d || c.mg_graph_op != &aop)) {
+    if (c.mg_graph && (c.mg_graph_id != mg_id(h) || c.mg_graph_d != d || c.mg_graph_op != &aop ||
+                       c.mg_graph_gen != op_generation())) {
         cudaGraphExecDestroy(c.mg_graph);
         c.mg_graph = nullptr;
     }
@@ -888,6 +892,7 @@ static cw_status mgcg_run(const Op &aop, MgHier &h, CgLevel &lv, double *d, CgSc
         c.mg_graph_id = mg_id(h);
         c.mg_graph_d = d;
         c.mg_graph_op = &aop;
+        c.mg_graph_gen = op_generation();
     }
     for (;;) {
         CW_CUDA_TRY(cudaMemcpyAsync(c.h_flags, c.flags, F_NFLAG * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1048,6 +1053,14 @@ static cw_status solve_impl(Op *op, const double *b, double *u, double rtol, int
     if (st != CW_OK) return st;
     CgScratch &c = *op->cg;
     cudaStream_t s = c.stream;
+    // a failed solve first asks the operators' device status words: an expired bounded wait (a tile
+    // left without output) explains a breakdown or a non-finite residual and is reported instead
+    auto failed = [&](cw_status why) {
+        for (Op *o : {op, op->inner, op->native})
+            if (op_status_take(o, s, "cw_cg_solve") == CW_ERR_TIMEOUT) return CW_ERR_TIMEOUT;
+        if (mg && mg_status_take(*mg, s) == CW_ERR_TIMEOUT) return CW_ERR_TIMEOUT;
+        return why;
+    };
     const int64_t L = op->L;
     if (mg && mg_top_op(*mg).prec == CW_PREC_F32 && !c.r32) {
         CW_CUDA_TRY(cudaMalloc(&c.r32, L * sizeof(float)));
@@ -1103,7 +1116,7 @@ static cw_status solve_impl(Op *op, const double *b, double *u, double rtol, int
             if (ist != CW_ERR_BREAKDOWN || !keep || mg) break;
         }
         // breakdown, or a CUDA error of the inner run: the correction may be partly written
-        if (ist != CW_OK && ist != CW_ERR_NOT_CONVERGED) return ist;
+        if (ist != CW_OK && ist != CW_ERR_NOT_CONVERGED) return failed(ist);
         if (fp64_inner) k_add_correction_f64<<<vec_grid(), 256, 0, s>>>(u, c.d64, L);
         else k_add_correction<<<vec_grid(), 256, 0, s>>>(u, c.d32, L);
         ++outer;
@@ -1113,7 +1126,7 @@ static cw_status solve_impl(Op *op, const double *b, double *u, double rtol, int
         k_sub<<<vec_grid(), 256, 0, s>>>(r, b, w, L);
         if ((st = residual_norm2(*op, r, w, c, &res)) != CW_OK) return st;
         if (debug_trace()) std::fprintf(stderr, "[cwfem cg] outer %d: true rel residual %.3e\n", outer, std::sqrt(res / res0));
-        if (!std::isfinite(res)) return fail(CW_ERR_BREAKDOWN, "cw_cg_solve: non-finite residual");
+        if (!std::isfinite(res)) return failed(fail(CW_ERR_BREAKDOWN, "cw_cg_solve: non-finite residual"));
         consistent = std::sqrt(res / res_prev) <= 1.25 * rec;
         st = CW_ERR_NOT_CONVERGED;
     }
@@ -1126,6 +1139,11 @@ static cw_status solve_impl(Op *op, const double *b, double *u, double rtol, int
     double eta = 0.0;
     cw_status s3 = energy(*op, r, u, c, &eta);  // r = b - A u of the returned u
     if (s3 != CW_OK) return s3;
+    // an expired bounded wait in any operator kernel of the solve invalidates it
+    for (Op *o : {op, op->inner, op->native})
+        if ((s3 = op_status_take(o, s, "cw_cg_solve")) != CW_OK) return s3;
+    if (mg)
+        if ((s3 = mg_status_take(*mg, s)) != CW_OK) return s3;
     CW_CUDA_TRY(cudaEventRecord(c.ev0, s));
     CW_CUDA_TRY(cudaStreamWaitEvent(us, c.ev0, 0));
     if (stats) {
@@ -1194,6 +1212,8 @@ extern "C" cw_status cw_cg_residual(cw_op oh, const double *b, const double *u, 
     k_sub<<<vec_grid(), 256, 0, s>>>(r, b, w, op->L);
     CW_CUDA_TRY(cudaGetLastError());
     if ((st = residual_norm2(*op, r, w, c, &res)) != CW_OK) return st;
+    for (Op *o : {op, op->native})
+        if ((st = op_status_take(o, s, "cw_cg_residual")) != CW_OK) return st;
     *rel_residual = res0 > 0.0 ? std::sqrt(res / res0) : 0.0;
     return CW_OK;
 }
@@ -1351,6 +1371,7 @@ extern "C" cw_status cw_cg_solve_noalloc(cw_op oh, const double *b, double *u, d
     double eta = 0.0;
     cw_status s3 = energy(*op, r, u, c, &eta);
     if (s3 != CW_OK) return s3;
+    if ((s3 = op_status_take(op, s, "cw_cg_solve_noalloc")) != CW_OK) return s3;
     if (stats) {
         stats->iterations = iters;
         stats->outer_iterations = outer;

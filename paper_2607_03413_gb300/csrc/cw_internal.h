@@ -57,10 +57,17 @@ struct Op {
     static constexpr int kMaxSlabs = 16;  // 32 measured slower (more, smaller copies)
     cudaEvent_t h_ev[2][kMaxSlabs] = {};
     cudaEvent_t h_done = nullptr;
+    unsigned *d_status = nullptr;  // device status word: kDevStatusTimeout when a bounded wait expired
+    uint32_t dbg_tma_extra = 0;    // fault injection for tests: extra bytes armed on the staged input tile
     int cpb = 0;          // apply kernel variant: cells per CTA (0 = default for the degree)
     int stage = 1;        // apply kernel variant: TMA staging of the input and metric tiles
     int64_t owned_bytes = 0;
 };
+
+// bumped whenever an operator's kernel choice or fault-injection setting changes: CUDA graphs captured
+// before (the solvers' iteration graphs bake kernels and their arguments in) are re-captured
+uint64_t op_generation();
+void op_generation_bump();
 
 size_t vec_elem_size(int prec);
 bool metric_is_f64(int prec);
@@ -124,7 +131,13 @@ struct MgHier;
 // u = MG(b): one V-cycle on the finest level from a zero initial guess (enqueue only)
 cudaError_t mg_vcycle_zero(MgHier &h, const void *b, void *u, cudaStream_t s);
 const Op &mg_top_op(const MgHier &h);
+// op_status_take over the hierarchy's level operators
+cw_status mg_status_take(MgHier &h, cudaStream_t s);
 uint64_t mg_id(const MgHier &h);
+
+// device status words: CW_ERR_TIMEOUT (and the word cleared) if a bounded wait of the operator's
+// kernels expired since the last check, else CW_OK; reads the word on stream s (synchronising it)
+cw_status op_status_take(Op *op, cudaStream_t s, const char *where);
 
 // error reporting (thread-local message)
 void set_error(const std::string &msg);

@@ -187,7 +187,7 @@ cudaError_t launch_metric(const Op &op, const void *x, void *y, cudaStream_t s, 
     if (xfuse) *xfuse = CPB;
     kern<<<grid, N * N * CPB, smem, s>>>(static_cast<const VS *>(x), static_cast<VS *>(y),
                                          static_cast<const GS *>(op.d_geo), op.E, op.kind, tab,
-                                         xfuse ? op.mesh->nx : 0);
+                                         xfuse ? op.mesh->nx : 0, op.d_status, op.dbg_tma_extra);
     return cudaGetLastError();
 }
 
@@ -208,7 +208,7 @@ cudaError_t launch_smooth(const Op &op, void *u, const void *b, const void *dhat
     *xfuse = CPB;
     kern<<<grid, N * N * CPB, smem, s>>>(static_cast<VS *>(u), static_cast<const VS *>(b),
                                          static_cast<const VS *>(dhat), static_cast<const GS *>(op.d_geo), op.E,
-                                         op.kind, tab, op.mesh->nx);
+                                         op.kind, tab, op.mesh->nx, op.d_status, op.dbg_tma_extra);
     return cudaGetLastError();
 }
 
@@ -248,7 +248,8 @@ cudaError_t launch_metric_dot(const Op &op, const void *x, void *y, double *part
     const unsigned grid = (unsigned)((op.E + CPB - 1) / CPB);
     *nblocks = grid;
     kern<<<grid, N * N * CPB, smem, s>>>(static_cast<const VS *>(x), static_cast<VS *>(y),
-                                         static_cast<const GS *>(op.d_geo), op.E, op.kind, tab, part);
+                                         static_cast<const GS *>(op.d_geo), op.E, op.kind, tab, part, op.d_status,
+                                         op.dbg_tma_extra);
     return cudaGetLastError();
 }
 

@@ -126,6 +126,14 @@ struct MgHier {
 };
 
 const Op &mg_top_op(const MgHier &h) { return *h.lv.back().op; }
+cw_status mg_status_take(MgHier &h, cudaStream_t s)
+{
+    for (MgLevel &L : h.lv) {
+        cw_status st = op_status_take(L.op, s, "multigrid cycle");
+        if (st != CW_OK) return st;
+    }
+    return CW_OK;
+}
 uint64_t mg_id(const MgHier &h) { return h.id; }
 
 static unsigned vgrid(int64_t n) { return (unsigned)std::min<int64_t>(1216, std::max<int64_t>(1, (n + 255) / 256)); }

@@ -65,4 +65,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 __device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Poll limits of the staged tiles' waits: the normal bound (far above any real copy time), and the
+// short bound used when a test arms a barrier that cannot complete (see the fault-injection hook).
+constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint32_t kWaitLimitInjected = 1u << 10;
+// bit set in an operator's device status word when a bounded wait expired
+constexpr unsigned kDevStatusTimeout = 1u;
+
 }  // namespace cw
