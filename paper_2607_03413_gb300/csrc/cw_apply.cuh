@@ -319,7 +319,7 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
     T *s2 = S0 + (2 * CPB + c) * CS;
 
     // ---- tile staging (single right-hand side)
-    bool x_smem = false, g_smem = false;
+    bool x_smem = false, g_smem = false, x_ok = true;
     const VS *xs = nullptr;
     const GS *gs = nullptr;
     uint64_t *bar = nullptr;
@@ -354,14 +354,11 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
                 mbar_expect_tx(bar + 1, gb);
                 bulk_g2s(sG, gsrc, gb, bar + 1);
             }
-            if (!__syncthreads_and(mbar_wait_bounded(bar, 0, lim))) {
-                abandon(0, 2);
-                return false;
-            }
+            x_ok = mbar_wait_bounded(bar, 0, lim);  // voted on at the barrier that ends step (1)
             x_smem = true;
             xs = sX + c * N3;
             gs = sG + c * NC * N3;
-            g_smem = true;  // its wait comes at the physics step
+            g_smem = true;  // its wait comes before the physics step
         }
     } else if constexpr (STAGE == 2) {
         bar = reinterpret_cast<uint64_t *>(smem_raw + (3 * CPB * CS * sizeof(T) + 15) / 16 * 16);
@@ -381,10 +378,7 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
                 mbar_expect_tx(bar, xb + dbg_extra);
                 bulk_g2s(sX, xsrc, xb, bar);
             }
-            if (!__syncthreads_and(mbar_wait_bounded(bar, 0, lim))) {
-                abandon(0, 1);
-                return false;
-            }
+            x_ok = mbar_wait_bounded(bar, 0, lim);
             x_smem = true;
             xs = sX + c * N3;
         }
@@ -396,9 +390,9 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
         T v[N], w[N], u[N], acc[N], gx[N], gy[N], gz[N];
         // (1) x-line (j,k) = (ra, rb): N contiguous values of the cell, contracted with B along x
         {
-            if (x_smem) {
+            if (x_smem) {  // a thread whose wait expired reads nothing staged (the tile is abandoned below)
 #pragma unroll
-                for (int m = 0; m < N; ++m) v[m] = Ar::from(xs[N * r + m]);
+                for (int m = 0; m < N; ++m) v[m] = x_ok ? Ar::from(xs[N * r + m]) : Ar::zero();
             } else {
                 const VS *xc = xr + (act ? cell : 0) * N3 + N * r;
 #pragma unroll
@@ -407,7 +401,10 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
             sweep<N, Ar, 0, NRM>(tab, v, w);
             CW_STX(s0, w);
         }
-        __syncthreads();
+        if (!__syncthreads_and(x_ok)) {  // block-uniform outcome of the input tile's wait
+            abandon(0, STAGE == 1 ? 2 : 1);
+            return false;
+        }
         // (2) y-line (i,k): contract with B along y, in place
         {
             CW_LDY(s0, v);
@@ -435,19 +432,23 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
                 sweep<N, Ar, 2, NRM>(tab, v, w);
                 CW_STY(s2, w);
             }
-            __syncthreads();
+            // the metric tile's wait, voted on at the barrier this step needs anyway
+            const bool g_ok = (STAGE == 1 && g_smem) ? mbar_wait_bounded(bar + 1, 0, lim) : true;
+            if (!__syncthreads_and(g_ok)) {
+                abandon(1, 2);
+                return false;
+            }
             {
                 CW_LDZ(s1, gx);
                 CW_LDZ(s2, gy);
             }
-        }
-        // (4) quadrature-point physics on the owned pencil, qp = (ra, rb, k)
-        if constexpr (STAGE == 1) {
-            if (g_smem && !__syncthreads_and(mbar_wait_bounded(bar + 1, 0, lim))) {  // g_smem is block-uniform
+        } else if (STAGE == 1 && g_smem) {  // block-uniform
+            if (!__syncthreads_and(mbar_wait_bounded(bar + 1, 0, lim))) {
                 abandon(1, 2);
                 return false;
             }
         }
+        // (4) quadrature-point physics on the owned pencil, qp = (ra, rb, k)
         {
             const GS *gc = g_smem ? gs + r : geo + (act ? cell : 0) * (RC ? kTriCoef : NC * N3) + (RC ? 0 : r);
             // RC: the pencil's Jacobian columns as J_xi = P0 + zeta P1, J_eta = Q0 + zeta Q1, J_zeta = Z
