@@ -320,6 +320,9 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
 
     // ---- tile staging (single right-hand side)
     bool x_smem = false, g_smem = false, x_ok = true;
+    // set by any thread whose wait for a staged copy expired; read after the next barrier, so the
+    // decision to abandon the tile is block-uniform at no extra barrier on the common path
+    __shared__ int s_expired;
     const VS *xs = nullptr;
     const GS *gs = nullptr;
     uint64_t *bar = nullptr;
@@ -346,6 +349,7 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
             if (t == 0) {
                 mbar_init(bar, 1);
                 mbar_init(bar + 1, 1);
+                s_expired = 0;
             }
             __syncthreads();
             if (t == 0) {
@@ -354,7 +358,8 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
                 mbar_expect_tx(bar + 1, gb);
                 bulk_g2s(sG, gsrc, gb, bar + 1);
             }
-            x_ok = mbar_wait_bounded(bar, 0, lim);  // voted on at the barrier that ends step (1)
+            x_ok = mbar_wait_bounded(bar, 0, lim);  // outcome shared at the barrier that ends step (1)
+            if (!x_ok) s_expired = 1;
             x_smem = true;
             xs = sX + c * N3;
             gs = sG + c * NC * N3;
@@ -372,13 +377,17 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
         const bool ok = full && aligned16(xsrc) && aligned16(sX) && (xb % 16 == 0);
         if (t == 0 && full && aligned16(gsrc) && (gb % 16 == 0)) bulk_prefetch_l2(gsrc, gb);
         if (ok) {  // block-uniform
-            if (t == 0) mbar_init(bar, 1);
+            if (t == 0) {
+                mbar_init(bar, 1);
+                s_expired = 0;
+            }
             __syncthreads();
             if (t == 0) {
                 mbar_expect_tx(bar, xb + dbg_extra);
                 bulk_g2s(sX, xsrc, xb, bar);
             }
             x_ok = mbar_wait_bounded(bar, 0, lim);
+            if (!x_ok) s_expired = 1;
             x_smem = true;
             xs = sX + c * N3;
         }
@@ -401,7 +410,8 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
             sweep<N, Ar, 0, NRM>(tab, v, w);
             CW_STX(s0, w);
         }
-        if (!__syncthreads_and(x_ok)) {  // block-uniform outcome of the input tile's wait
+        __syncthreads();
+        if (x_smem && s_expired) {  // block-uniform outcome of the input tile's wait
             abandon(0, STAGE == 1 ? 2 : 1);
             return false;
         }
@@ -432,9 +442,11 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
                 sweep<N, Ar, 2, NRM>(tab, v, w);
                 CW_STY(s2, w);
             }
-            // the metric tile's wait, voted on at the barrier this step needs anyway
-            const bool g_ok = (STAGE == 1 && g_smem) ? mbar_wait_bounded(bar + 1, 0, lim) : true;
-            if (!__syncthreads_and(g_ok)) {
+            // the metric tile's wait, its outcome shared at the barrier this step needs anyway
+            if constexpr (STAGE == 1)
+                if (g_smem && !mbar_wait_bounded(bar + 1, 0, lim)) s_expired = 1;
+            __syncthreads();
+            if (STAGE == 1 && g_smem && s_expired) {
                 abandon(1, 2);
                 return false;
             }
