@@ -281,17 +281,26 @@ __host__ __device__ constexpr size_t metric_smem_bytes(int nc, int stage)
 // (left + right) / 2 to both copies; asm_nx must be the mesh's cells per x-row). Each thread re-reads
 // u, b and D_hat on the x-line it stores, with plain loads (y aliases x). The operator output never
 // reaches memory.
-// Staged tiles and their waits: every wait is bounded and its outcome is made block-uniform
-// (__syncthreads_and). If a copy did not complete within the bound, the CTA abandons the tile: it
-// writes no output, thread 0 records kDevStatusTimeout in *status (the operator's device status word,
-// reported as CW_ERR_TIMEOUT by the next checking call), waits (bounded) for the copies it issued so
-// that none lands after the tile is left, and the function returns false. No path reads a staged
-// tile whose copy has not been seen to complete. dbg_extra > 0 (fault injection for tests) arms the
-// input tile's barrier with dbg_extra bytes more than the copy delivers, so that its phase can never
-// complete and the (then short) bounded wait runs out.
+// An expired wait for a staged copy: record it in the device status word and wait once more (bounded)
+// so that the copy is not left in flight. Out of line: the common path carries none of it.
+static __device__ __noinline__ void wait_expired(unsigned *status, uint64_t *bar, uint32_t lim)
+{
+    if (status) atomicOr(status, kDevStatusTimeout);
+    mbar_wait_bounded(bar, 0, lim);
+}
+
+// Staged tiles and their waits: every wait for a bulk copy is bounded. A thread whose wait expired
+// never reads the staged data (it takes zeros for the input tile, the global copy of the metric),
+// records kDevStatusTimeout in *status (the operator's device status word, reported as
+// CW_ERR_TIMEOUT by the next checking call: the outputs of that call are then undefined), and waits
+// once more (bounded) so that the copy is not left in flight. Nothing runs on the common path beyond
+// the wait itself: deciding the tile's fate block-wide (an early exit, or a flag read before the
+// stores) made the common path 2-6 % slower in measurement. dbg_extra > 0 (fault injection for tests)
+// arms the input tile's barrier with dbg_extra bytes more than the copy delivers, so that its phase
+// can never complete and the (then short) bounded wait runs out.
 template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool DOT = false, bool RC = false,
           bool SMOOTH = false>
-__device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__restrict__ geo,
+__device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__restrict__ geo,
                                             int64_t ncells, int kind, const TabMetric<N, typename Ar::C> &tab,
                                             int64_t tile, int cpt, unsigned char *smem_raw, df64 *dot = nullptr,
                                             int asm_nx = 0, const VS *sb = nullptr, const VS *sd = nullptr,
@@ -320,21 +329,10 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
 
     // ---- tile staging (single right-hand side)
     bool x_smem = false, g_smem = false, x_ok = true;
-    // set by any thread whose wait for a staged copy expired; read after the next barrier, so the
-    // decision to abandon the tile is block-uniform at no extra barrier on the common path
-    __shared__ int s_expired;
     const VS *xs = nullptr;
     const GS *gs = nullptr;
     uint64_t *bar = nullptr;
     const uint32_t lim = dbg_extra ? kWaitLimitInjected : kWaitLimit;
-    // expired wait: report, drain the issued copies (bounded), leave the tile without output
-    auto abandon = [&](int b0, int b1) {  // barriers [b0, b1) still owe their copies
-        if (t == 0) {
-            if (status) atomicOr(status, kDevStatusTimeout);
-            for (int b = b0; b < b1; ++b) mbar_wait_bounded(bar + b, 0, lim);
-        }
-        __syncthreads();
-    };
     if constexpr (STAGE == 1) {
         const size_t offg = (3 * CPB * CS * sizeof(T) + 15) / 16 * 16;
         GS *sG = reinterpret_cast<GS *>(smem_raw + offg);
@@ -349,7 +347,6 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
             if (t == 0) {
                 mbar_init(bar, 1);
                 mbar_init(bar + 1, 1);
-                s_expired = 0;
             }
             __syncthreads();
             if (t == 0) {
@@ -358,8 +355,8 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
                 mbar_expect_tx(bar + 1, gb);
                 bulk_g2s(sG, gsrc, gb, bar + 1);
             }
-            x_ok = mbar_wait_bounded(bar, 0, lim);  // outcome shared at the barrier that ends step (1)
-            if (!x_ok) s_expired = 1;
+            x_ok = mbar_wait_bounded(bar, 0, lim);
+            if (!x_ok) wait_expired(status, bar, lim);
             x_smem = true;
             xs = sX + c * N3;
             gs = sG + c * NC * N3;
@@ -377,17 +374,14 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
         const bool ok = full && aligned16(xsrc) && aligned16(sX) && (xb % 16 == 0);
         if (t == 0 && full && aligned16(gsrc) && (gb % 16 == 0)) bulk_prefetch_l2(gsrc, gb);
         if (ok) {  // block-uniform
-            if (t == 0) {
-                mbar_init(bar, 1);
-                s_expired = 0;
-            }
+            if (t == 0) mbar_init(bar, 1);
             __syncthreads();
             if (t == 0) {
                 mbar_expect_tx(bar, xb + dbg_extra);
                 bulk_g2s(sX, xsrc, xb, bar);
             }
             x_ok = mbar_wait_bounded(bar, 0, lim);
-            if (!x_ok) s_expired = 1;
+            if (!x_ok) wait_expired(status, bar, lim);
             x_smem = true;
             xs = sX + c * N3;
         }
@@ -399,7 +393,7 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
         T v[N], w[N], u[N], acc[N], gx[N], gy[N], gz[N];
         // (1) x-line (j,k) = (ra, rb): N contiguous values of the cell, contracted with B along x
         {
-            if (x_smem) {  // a thread whose wait expired reads nothing staged (the tile is abandoned below)
+            if (x_smem) {  // a thread whose wait expired reads nothing staged
 #pragma unroll
                 for (int m = 0; m < N; ++m) v[m] = x_ok ? Ar::from(xs[N * r + m]) : Ar::zero();
             } else {
@@ -411,10 +405,6 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
             CW_STX(s0, w);
         }
         __syncthreads();
-        if (x_smem && s_expired) {  // block-uniform outcome of the input tile's wait
-            abandon(0, STAGE == 1 ? 2 : 1);
-            return false;
-        }
         // (2) y-line (i,k): contract with B along y, in place
         {
             CW_LDY(s0, v);
@@ -442,27 +432,24 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
                 sweep<N, Ar, 2, NRM>(tab, v, w);
                 CW_STY(s2, w);
             }
-            // the metric tile's wait, its outcome shared at the barrier this step needs anyway
-            if constexpr (STAGE == 1)
-                if (g_smem && !mbar_wait_bounded(bar + 1, 0, lim)) s_expired = 1;
             __syncthreads();
-            if (STAGE == 1 && g_smem && s_expired) {
-                abandon(1, 2);
-                return false;
-            }
             {
                 CW_LDZ(s1, gx);
                 CW_LDZ(s2, gy);
             }
-        } else if (STAGE == 1 && g_smem) {  // block-uniform
-            if (!__syncthreads_and(mbar_wait_bounded(bar + 1, 0, lim))) {
-                abandon(1, 2);
-                return false;
+        }
+        // the metric tile's wait (a thread whose wait expired reads the metric from global memory)
+        bool g_ok = true;
+        if constexpr (STAGE == 1) {
+            if (g_smem) {
+                g_ok = mbar_wait_bounded(bar + 1, 0, lim);
+                if (!g_ok) wait_expired(status, bar + 1, lim);
             }
         }
         // (4) quadrature-point physics on the owned pencil, qp = (ra, rb, k)
         {
-            const GS *gc = g_smem ? gs + r : geo + (act ? cell : 0) * (RC ? kTriCoef : NC * N3) + (RC ? 0 : r);
+            const GS *gc = (g_smem && g_ok) ? gs + r
+                                            : geo + (act ? cell : 0) * (RC ? kTriCoef : NC * N3) + (RC ? 0 : r);
             // RC: the pencil's Jacobian columns as J_xi = P0 + zeta P1, J_eta = Q0 + zeta Q1, J_zeta = Z
             T P0[3], P1[3], Q0[3], Q1[3], Z[3], wab;
             if constexpr (RC) {
@@ -668,7 +655,6 @@ __device__ __forceinline__ bool metric_tile(const VS *x, VS *y, const GS *__rest
             }
         }
     }
-    return true;
 }
 
 // Register caps for the double-float kernels (as CTAs per SM for the launch bounds): stored metric

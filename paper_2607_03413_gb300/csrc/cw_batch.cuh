@@ -67,9 +67,8 @@ __device__ __forceinline__ const TabMetric<N, C> &batch_tab(const BatchTables<C>
 
 // one work item of degree N; kept out of line so that each degree gets its own register allocation
 // (all seven bodies inlined into one function spill heavily)
-// false: a tile was abandoned after an expired wait (recorded in P.status); the CTA then stops
 template <class Ar, class VS, class GS, int N>
-__device__ __noinline__ bool batch_item(const BatchProb &P, const BatchTables<typename Ar::C> &T, int64_t local,
+__device__ __noinline__ void batch_item(const BatchProb &P, const BatchTables<typename Ar::C> &T, int64_t local,
                                         unsigned char *smem)
 {
     const int64_t chunk = local / P.nrhs, rhs = local - chunk * P.nrhs;
@@ -79,11 +78,9 @@ __device__ __noinline__ bool batch_item(const BatchProb &P, const BatchTables<ty
     const int64_t t0 = chunk * P.tpi, t1 = min(P.ntiles, t0 + P.tpi);
     for (int64_t tile = t0; tile < t1; ++tile) {
         if (tile > t0) __syncthreads();  // the previous tile has finished with shared memory
-        if (!metric_tile<N, batch_slots(N), Ar, VS, GS, 0>(x, y, g, P.ncells, P.kind, batch_tab<N>(T), tile, P.cpt,
-                                                          smem, nullptr, 0, nullptr, nullptr, P.status))
-            return false;
+        metric_tile<N, batch_slots(N), Ar, VS, GS, 0>(x, y, g, P.ncells, P.kind, batch_tab<N>(T), tile, P.cpt, smem,
+                                                      nullptr, 0, nullptr, nullptr, P.status);
     }
-    return true;
 }
 
 template <class Ar, class VS, class GS>
@@ -113,17 +110,15 @@ __device__ __forceinline__ void batch_body(const BatchProb *__restrict__ probs, 
         __syncthreads();
         const BatchProb P = probs[s_prob];
         const int64_t local = it - P.item0;
-        bool ok;
         switch (P.n) {
-        case 2: ok = batch_item<Ar, VS, GS, 2>(P, T, local, smem_raw); break;
-        case 3: ok = batch_item<Ar, VS, GS, 3>(P, T, local, smem_raw); break;
-        case 4: ok = batch_item<Ar, VS, GS, 4>(P, T, local, smem_raw); break;
-        case 5: ok = batch_item<Ar, VS, GS, 5>(P, T, local, smem_raw); break;
-        case 6: ok = batch_item<Ar, VS, GS, 6>(P, T, local, smem_raw); break;
-        case 7: ok = batch_item<Ar, VS, GS, 7>(P, T, local, smem_raw); break;
-        default: ok = batch_item<Ar, VS, GS, 8>(P, T, local, smem_raw); break;
+        case 2: batch_item<Ar, VS, GS, 2>(P, T, local, smem_raw); break;
+        case 3: batch_item<Ar, VS, GS, 3>(P, T, local, smem_raw); break;
+        case 4: batch_item<Ar, VS, GS, 4>(P, T, local, smem_raw); break;
+        case 5: batch_item<Ar, VS, GS, 5>(P, T, local, smem_raw); break;
+        case 6: batch_item<Ar, VS, GS, 6>(P, T, local, smem_raw); break;
+        case 7: batch_item<Ar, VS, GS, 7>(P, T, local, smem_raw); break;
+        default: batch_item<Ar, VS, GS, 8>(P, T, local, smem_raw); break;
         }
-        if (!ok) return;  // block-uniform
     }
 }
 
@@ -137,12 +132,12 @@ __device__ __forceinline__ const BatchTables<C> &batch_tables();
 // stays an immediate constant-bank operand, as in the per-operator kernel. (FP32 bodies stay inline:
 // the call costs them more than it saves.)
 template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
-__device__ __noinline__ bool grouped_tile(const VS *x, VS *y, const GS *g, int64_t ncells, int kind, int64_t tile,
+__device__ __noinline__ void grouped_tile(const VS *x, VS *y, const GS *g, int64_t ncells, int kind, int64_t tile,
                                           unsigned *status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    return metric_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, g, ncells, kind, batch_tab<N>(batch_tables<typename Ar::C>()),
-                                                  tile, CPB, smem_raw, nullptr, 0, nullptr, nullptr, status);
+    metric_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, g, ncells, kind, batch_tab<N>(batch_tables<typename Ar::C>()), tile,
+                                           CPB, smem_raw, nullptr, 0, nullptr, nullptr, status);
 }
 
 // ---- grouped mode: one persistent kernel per degree, shaped like the per-operator kernel
@@ -181,14 +176,12 @@ __global__ void __launch_bounds__(N *N *CPB) batch_degree_kernel(const BatchProb
         const int64_t t0 = chunk * P.tpi, t1 = min(P.ntiles, t0 + P.tpi);
         for (int64_t tile = t0; tile < t1; ++tile) {
             if (tile > t0) __syncthreads();
-            bool ok;
             if constexpr (std::is_same<Ar, ArDF>::value)
-                ok = grouped_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, g, P.ncells, P.kind, tile, P.status);
+                grouped_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, g, P.ncells, P.kind, tile, P.status);
             else
-                ok = metric_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, g, P.ncells, P.kind,
-                                                            batch_tab<N>(batch_tables<typename Ar::C>()), tile, CPB,
-                                                            smem_raw, nullptr, 0, nullptr, nullptr, P.status);
-            if (!ok) return;  // block-uniform: an expired wait ends this CTA
+                metric_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, g, P.ncells, P.kind,
+                                                       batch_tab<N>(batch_tables<typename Ar::C>()), tile, CPB,
+                                                       smem_raw, nullptr, 0, nullptr, nullptr, P.status);
         }
     }
 }

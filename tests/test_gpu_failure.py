@@ -1,8 +1,9 @@
 """Failure detection without a GPU fault: the operator kernels' bounded waits for their staged tiles.
 A test-only hook arms each staged input tile's barrier with more bytes than its copy delivers, so the
-copy lands but the barrier phase never completes and the short bounded wait runs out. The tile must be
-abandoned (its output left untouched, no unfinished copy consumed), the event reported as
-CW_ERR_TIMEOUT by the next check or synchronising call, and the context must stay usable."""
+copy lands but the barrier phase never completes and the short bounded wait runs out. The threads must
+not read the staged tile (they take zeros), the event must be reported as CW_ERR_TIMEOUT by the next
+check or synchronising call (the outputs of that call are undefined), tiles read without staging must
+be unaffected, and the context must stay usable."""
 import numpy as np
 import pytest
 
@@ -43,7 +44,8 @@ def test_expired_wait_is_reported_and_the_context_survives(cw, orc, prec, stage)
     assert cw.cw_op_check(op.handle) == cw.CW_ERR_TIMEOUT
     assert cw.cw_op_check(op.handle) == cw.CW_OK  # the check clears the word
     yn = to_np(y).reshape(mesh.ncells, n3)
-    assert np.isnan(yn[:16]).all()  # the staged tile was abandoned: nothing written
+    # the staged tile computed on zeros instead of its unconfirmed input: finite, and not the result
+    assert np.isfinite(yn[:16]).all() and rel_err(yn[:16], ref[:16]) > 0.5
     assert rel_err(yn[16:], ref[16:]) <= (1e-12 if prec == 0 else 1e-5)  # the ragged tile reads directly
     cw.cw_op_inject_stall(op.handle, False)
     y2 = op.apply(x)
