@@ -669,17 +669,49 @@ def mg_bench(cw, args, stream):
         for o in ops:
             if o is not fine:
                 o.close()
-    fine.cg_solve(b, u, rtol=1e-3, maxit=200, mode=cw.CW_CG_IR_F32, check=False)
-    torch.cuda.synchronize()
-    _, st, rc = fine.cg_solve(b, u, rtol=1e-10, maxit=20000, mode=cw.CW_CG_IR_F32, check=False)
-    res["jacobi_ir_f32"] = {"seconds": st.seconds, "iterations": st.iterations, "outer": st.outer_iterations,
-                            "rel_residual": st.rel_residual, "status": int(rc)}
-    best = min(res["mg_f64_cycle"]["seconds"], res["mg_f32_cycle"]["seconds"])
-    res["speedup_mg_vs_jacobi_ir_f32"] = res["jacobi_ir_f32"]["seconds"] / best
+    if args.mg_jacobi:
+        fine.cg_solve(b, u, rtol=1e-3, maxit=200, mode=cw.CW_CG_IR_F32, check=False)
+        torch.cuda.synchronize()
+        _, st, rc = fine.cg_solve(b, u, rtol=1e-10, maxit=20000, mode=cw.CW_CG_IR_F32, check=False)
+        res["jacobi_ir_f32"] = {"seconds": st.seconds, "iterations": st.iterations, "outer": st.outer_iterations,
+                                "rel_residual": st.rel_residual, "status": int(rc)}
+        best = min(res["mg_f64_cycle"]["seconds"], res["mg_f32_cycle"]["seconds"])
+        res["speedup_mg_vs_jacobi_ir_f32"] = res["jacobi_ir_f32"]["seconds"] / best
     fine.close()
     for M in Ms:
         M.close()
     return res
+
+
+def mg_cycle_profile(cw, n, prec, cycles=3):
+    """Profiling case: V-cycles alone (zero initial guess) on a Q3 hierarchy whose finest mesh has n^3
+    cells (5 levels, refined from a curved (n/16)^3 mesh), in one precision; no solver. Returns the mean
+    cycle time in ms."""
+    import torch
+    p, nl = 3, 5
+    ms = [synth.box_mesh(n // 16, perturb=0.1)]
+    for _ in range(nl - 1):
+        ms.append(synth.refine(ms[-1]))
+    Ms = [cw.Mesh.from_synth(m) for m in ms]
+    ops = [cw.Operator(M, p, cw.CW_LAPLACE, cw.CW_GEOM_METRIC, prec, cw.CW_BC_DIRICHLET0) for M in Ms]
+    mg = cw.Multigrid(ops)
+    b = ops[-1].empty()
+    b.copy_(torch.from_numpy(synth.cellwise_random(ms[-1], p, seed=0)).to(b.dtype))
+    z = ops[-1].empty()
+    for _ in range(2):
+        mg.vcycle(b, z)
+    torch.cuda.synchronize()
+    a, e = event_pair()
+    a.record()
+    for _ in range(cycles):
+        mg.vcycle(b, z)
+    e.record()
+    torch.cuda.synchronize()
+    ms_cycle = a.elapsed_time(e) / cycles
+    mg.close()
+    for o in ops:
+        o.close()
+    return ms_cycle
 
 
 # ------------------------------------------------------------------------- CPU oracle ----
@@ -765,6 +797,10 @@ def main():
     ap.add_argument("--no-cg", dest="cg", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-mg", dest="mg", action="store_false")
+    ap.add_argument("--no-mg-jacobi", dest="mg_jacobi", action="store_false",
+                    help="multigrid leg without the Jacobi comparison solve")
+    ap.add_argument("--profile-mg", type=int, default=0,
+                    help="profiling case: only V-cycles on an N^3 Q3 hierarchy (FP32), then exit")
     ap.add_argument("--no-mixed", dest="mixed", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
@@ -782,6 +818,14 @@ def main():
         out = reference_arm(args, rank, world)
         if out is not None:
             print(json.dumps(out))
+        return
+    if args.profile_mg:
+        import torch
+        import paper_2607_03413_gb300 as cw
+        torch.cuda.set_device(0)
+        cw.load()
+        print(json.dumps({"profile": "mg_cycle", "cells": args.profile_mg ** 3,
+                          "f32_cycle_ms": mg_cycle_profile(cw, args.profile_mg, cw.CW_PREC_F32)}))
         return
     rank, local, world = dist_init(args)
     args.book = SampleBook() if (rank == 0 and world == 1 and args.cpu) else None
