@@ -685,11 +685,11 @@ def mg_bench(cw, args, stream):
 
 def mg_cycle_profile(cw, n, prec, cycles=3):
     """Profiling case: V-cycles alone (zero initial guess) on a Q3 hierarchy whose finest mesh has n^3
-    cells (5 levels, refined from a curved (n/16)^3 mesh), in one precision; no solver. Returns the mean
+    cells (6 levels, refined from a curved (n/32)^3 mesh), in one precision; no solver. Returns the mean
     cycle time in ms."""
     import torch
-    p, nl = 3, 5
-    ms = [synth.box_mesh(n // 16, perturb=0.1)]
+    p, nl = 3, 6
+    ms = [synth.box_mesh(n // 32, perturb=0.1)]
     for _ in range(nl - 1):
         ms.append(synth.refine(ms[-1]))
     Ms = [cw.Mesh.from_synth(m) for m in ms]
