@@ -118,17 +118,24 @@ __global__ void __launch_bounds__(4 * N * N * CP) restrict_kernel(const VS *__re
     T *S2 = S1 + 4 * CP * N3;                 // [CP][2][N3] after y (bx)
     const int t = threadIdx.x;
     const int64_t e0 = static_cast<int64_t>(blockIdx.x) * CP;
-    // load: for each parent and child pair (bx = 0, 1) one contiguous span of 2 N3 fine values
+    // first fine value of each child pair (bx = 0, 1: two adjacent cells) of each parent, -1 past the
+    // end; computed once per CTA so that the load loop does no 64-bit index division
+    __shared__ int64_t s_base[CP * 4];
+    if (t < CP * 4) {
+        const int64_t e = e0 + t / 4;
+        s_base[t] = e < ncoarse ? child_cell(e, nx, ny, 2 * (t % 4)) * N3 : -1;
+    }
+    __syncthreads();
+    // load: for each parent and child pair one contiguous span of 2 N3 fine values
     for (int k = t; k < CP * 8 * N3; k += blockDim.x) {
-        const int c = k / (8 * N3), r = k - c * 8 * N3, pr = r / (2 * N3), w = r - pr * 2 * N3;
-        const int64_t e = e0 + c;
+        const int q = k / (2 * N3), w = k - q * (2 * N3);  // q = 4 c + pr
+        const int64_t base = s_base[q];
         T v = Ar::zero();
-        if (e < ncoarse) {
-            const int64_t g = child_cell(e, nx, ny, 2 * pr) * N3 + w;  // children 2pr and 2pr+1 adjacent
-            v = Ar::from(ldg_nc(bf + g));
-            if constexpr (SUB) v = Ar::sub(v, Ar::from(ldg_nc(vf + g)));
+        if (base >= 0) {
+            v = Ar::from(ldg_nc(bf + base + w));
+            if constexpr (SUB) v = Ar::sub(v, Ar::from(ldg_nc(vf + base + w)));
         }
-        S0[c * 8 * N3 + r] = v;  // r = (2 pr + bx) N3 + local
+        S0[k] = v;  // k = c 8 N3 + (2 pr + bx) N3 + local
     }
     __syncthreads();
     T in[N], out[N], acc[N];
