@@ -14,7 +14,9 @@ Pieces:
     transfers, the cell-wise damped Jacobi smoother in its literal and fused forms, the V-cycle and
     the V-cycle-preconditioned CG, beside the classical assembled V-cycle they are equivalent to;
   * ``oracle.dist``: the DSS and the Jacobi-PCG of a mesh split into z-slabs over torch.distributed
-    ranks (face-layer exchange per slab interface, sums over ranks for the inner products).
+    ranks (face-layer exchange per slab interface, sums over ranks for the inner products);
+  * ``oracle.mblock``: multi-block meshes (structured blocks glued face to face in any orientation):
+    the global numbering by node position, G, G^T, S and the assembled A_CG across block interfaces.
 """
 import ctypes
 import os

@@ -9,14 +9,18 @@ Inputs (the paper's cube / ball sweeps are not available, so these stand in for 
     ``(ix/nx, iy/ny, iz/nz)`` optionally moved by a smooth sinusoidal displacement of amplitude
     ``0.1*h`` that vanishes on the boundary of the cube (so the domain stays the unit cube);
   * global vectors of length ``(nx*p+1)*(ny*p+1)*(nz*p+1)`` drawn uniform in [-1, 1];
-  * raw cell-wise arrays of length ``E*(p+1)^3`` drawn uniform in [-1, 1] (unassembled duals).
+  * raw cell-wise arrays of length ``E*(p+1)^3`` drawn uniform in [-1, 1] (unassembled duals);
+  * multi-block meshes (several structured blocks glued face to face with seeded relative
+    orientations): the unit cube cut into nb^3 blocks, and the 7-block "cube in cube" (an inner cube
+    and six frustum-shaped shell blocks, edges shared by three blocks, vertices by four), the stand-in
+    for the paper's curved multi-block ball.
 """
 from dataclasses import dataclass
 import math
 import numpy as np
 
 __all__ = ["Mesh", "box_mesh", "refine", "global_vector", "cellwise_random", "batched_problem_list",
-           "global_len", "cellwise_len"]
+           "global_len", "cellwise_len", "MultiBlock", "cube_blocks", "cube_in_cube", "rotate_block"]
 
 
 @dataclass
@@ -120,3 +124,88 @@ def batched_problem_list(count: int = 48, seed: int = 0, lo: int = 8, hi: int = 
         out.append(dict(n=n, p=degrees[i % len(degrees)], freq=freq, direction=d / np.linalg.norm(d),
                         seed=i))
     return out
+
+
+# ----------------------------------------------------------------------------- multi-block
+@dataclass
+class MultiBlock:
+    blocks: list       # list of Mesh, each a structured block with its own local axes
+    lo: float          # the domain is the cube [lo, hi]^3 (its boundary carries the Dirichlet nodes)
+    hi: float
+
+
+def _proper_rotations():
+    """The 24 orientation-preserving symmetries of the index cube as (axis permutation, flips): a
+    permutation of odd parity needs an odd number of flips (so the trilinear maps keep det J > 0)."""
+    import itertools
+    out = []
+    for perm in itertools.permutations(range(3)):
+        inv = sum(1 for i in range(3) for j in range(i + 1, 3) if perm[i] > perm[j]) % 2
+        for flips in itertools.product((0, 1), repeat=3):
+            if (inv + sum(flips)) % 2 == 0:
+                out.append((perm, flips))
+    return out
+
+
+def rotate_block(mesh: Mesh, rot) -> Mesh:
+    """The same cells with the block's local index axes permuted and reversed by a proper rotation
+    ``rot = (perm, flips)``: local axis a of the result runs along old axis perm[a], reversed when
+    flips[a] (the physical cells are unchanged, only their local numbering)."""
+    perm, flips = rot
+    v = mesh.verts  # array axes (z, y, x, 3)
+    n_old = (mesh.nx, mesh.ny, mesh.nz)
+    # new local axis a (0 = x) comes from old local axis perm[a]; array axis of local axis a is 2 - a
+    w = np.transpose(v, (2 - perm[2], 2 - perm[1], 2 - perm[0], 3))
+    for a in range(3):
+        if flips[a]:
+            w = np.flip(w, axis=2 - a)
+    n = tuple(n_old[perm[a]] for a in range(3))
+    return Mesh(n[0], n[1], n[2], np.ascontiguousarray(w), affine=mesh.affine)
+
+
+def cube_blocks(nb=2, ncell=2, perturb=0.0, seed=0, rotate=True) -> MultiBlock:
+    """The unit cube cut into nb^3 cubic blocks of ncell^3 cells: the cells of box_mesh(nb*ncell,
+    perturb) exactly, each block with a seeded proper rotation of its local axes (so neighbouring
+    blocks meet in every relative orientation)."""
+    g = box_mesh(nb * ncell, perturb=perturb)
+    rots = _proper_rotations()
+    rng = np.random.default_rng(seed)
+    blocks = []
+    for bz in range(nb):
+        for by in range(nb):
+            for bx in range(nb):
+                sub = g.verts[bz * ncell:(bz + 1) * ncell + 1, by * ncell:(by + 1) * ncell + 1,
+                              bx * ncell:(bx + 1) * ncell + 1]
+                m = Mesh(ncell, ncell, ncell, np.ascontiguousarray(sub), affine=g.affine)
+                blocks.append(rotate_block(m, rots[int(rng.integers(len(rots)))]) if rotate else m)
+    return MultiBlock(blocks, 0.0, 1.0)
+
+
+def cube_in_cube(ncell=2, a=0.5, b=1.0, seed=0, rotate=True) -> MultiBlock:
+    """Seven blocks of ncell^3 cells filling [-b, b]^3: the inner cube [-a, a]^3 and, on each of its
+    faces, a shell block whose cells run from the inner face out to the outer face along the rays
+    from the origin (point r(t) F(u, v) with F on the unit cube's face, r from a to b). The shell
+    cells are trilinear but not affine. Edges of the inner cube are shared by three blocks, its
+    corners by four. With ``rotate`` every block gets a seeded proper rotation of its local axes."""
+    s = np.linspace(-1.0, 1.0, ncell + 1)
+    t = np.linspace(0.0, 1.0, ncell + 1)
+    K, J, I = np.meshgrid(s, s, s, indexing="ij")
+    blocks = [Mesh(ncell, ncell, ncell, np.ascontiguousarray(a * np.stack([I, J, K], axis=-1)), affine=True)]
+    for axis in range(3):
+        beta, gamma = (axis + 1) % 3, (axis + 2) % 3
+        for sign in (1.0, -1.0):
+            # local axes (i, j, k) = (u, v, radial); for the negative face u and v swap to keep det J > 0
+            Kt, Jv, Iu = np.meshgrid(t, s, s, indexing="ij")
+            if sign < 0:
+                Iu, Jv = Jv, Iu
+            F = np.zeros(Kt.shape + (3,))
+            F[..., axis] = sign
+            F[..., beta] = Iu
+            F[..., gamma] = Jv
+            r = (1.0 - Kt) * a + Kt * b
+            blocks.append(Mesh(ncell, ncell, ncell, np.ascontiguousarray(r[..., None] * F), affine=False))
+    if rotate:
+        rots = _proper_rotations()
+        rng = np.random.default_rng(seed)
+        blocks = [rotate_block(m, rots[int(rng.integers(len(rots)))]) for m in blocks]
+    return MultiBlock(blocks, -b, b)
