@@ -400,6 +400,51 @@ cw_status cw_mg_pcg_solve(cw_mg mg, cw_op op, const double *b, double *u, double
                           void *stream);
 
 /*
+ * Multi-block meshes (Sec. 4.3, unstructured inter-block interfaces; Algorithm unstruct_dss): nblocks
+ * operators, one per structured block, of one degree, kind and precision. The blocks are glued where
+ * their boundaries meet: face to face and conforming (a shared block face has the same cells on both
+ * sides), in any relative orientation, with the shared block-boundary vertices bit-identical in the
+ * meshes' vertex arrays (they are matched by exact coordinates). The multi-block cell-wise vector is
+ * the concatenation of the blocks' cell-wise vectors (block 0 first, each in its own [cell][k][j][i]
+ * layout; cw_mblock_cellwise_len entries). Set-up (host, synchronous) identifies every node on a block
+ * boundary by the global ids of its cell's vertices and its position in a canonical frame of the edge
+ * or face it lies on (orientation reconciled by integer arithmetic) and builds index tables of the DoFs
+ * shared by several blocks, split by the codimension of the block entity they lie on (set 0 macro-face
+ * interiors, 1 macro-line interiors, 2 macro-vertices), the number of copies of every entry, and the
+ * Dirichlet flags of the domain boundary (the block faces no other block shares). The operators must
+ * outlive the multi-block handle.
+ */
+typedef struct cw_mblock_s *cw_mblock;
+cw_status cw_mblock_create(const cw_op *ops, int nblocks, cw_mblock *out);
+cw_status cw_mblock_destroy(cw_mblock mb); /* waits for the device first */
+int64_t cw_mblock_cellwise_len(cw_mblock mb);
+int64_t cw_mblock_global_len(cw_mblock mb); /* distinct DoFs of the whole mesh */
+/* number of DoFs shared by several blocks in codimension set 0, 1 or 2 (-1 for a bad argument) */
+int64_t cw_mblock_shared_dofs(cw_mblock mb, int set);
+/* the library's global DoF of every cell-wise entry (host array of cw_mblock_cellwise_len int64) */
+cw_status cw_mblock_global_index(cw_mblock mb, int64_t *out);
+/*
+ * v <- S v (CW_DSS_SUM) or S_bar v (CW_DSS_AVERAGE) on the multi-block cell-wise device vector of the
+ * blocks' vector type: Algorithm struct_dss inside every block, then Algorithm unstruct_dss across
+ * the blocks (three launches: faces, lines, vertices; each shared DoF gets the sum of one copy per
+ * sharing block), then, for AVERAGE, division by the number of copies.
+ */
+cw_status cw_mblock_dss(cw_mblock mb, void *v, int flags, void *stream);
+/* y = A x (CW_APPLY_LOCAL: every block's operator on its part) or S A x (CW_APPLY_ASSEMBLE) */
+cw_status cw_mblock_apply(cw_mblock mb, const void *x, void *y, int flags, void *stream);
+/* d = G diag(A_CG) of the whole multi-block mesh (FP64 cell-wise device vector) */
+cw_status cw_mblock_diagonal(cw_mblock mb, double *d, void *stream);
+/*
+ * Solve A_CG u = G^T b on the multi-block mesh with homogeneous Dirichlet conditions on the domain
+ * boundary by Jacobi-preconditioned CG in primal-dual form (Sec. 4.4), FP64 (blocks of CW_PREC_F64),
+ * from u = 0, until ||m G^T r|| <= rtol ||m G^T b|| (recursive residual) or maxit (CW_ERR_NOT_CONVERGED).
+ * b: FP64 cell-wise dual, u: FP64 cell-wise primal output. The first call allocates five vectors.
+ * Synchronises `stream` (the host reads the residual every iteration). stats may be NULL.
+ */
+cw_status cw_mblock_cg_solve(cw_mblock mb, const double *b, double *u, double rtol, int maxit, cw_cg_stats *stats,
+                             void *stream);
+
+/*
  * Allocation-free variant of cw_cg_solve. The paper has no counterpart; this entry point exists
  * for callers that must not allocate device memory while solving -- e.g. code that runs inside a
  * caller-managed memory pool or an allocator callback, a real-time loop whose memory is fixed at

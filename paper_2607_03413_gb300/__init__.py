@@ -37,7 +37,9 @@ EXPORTED = [
     "cw_batch_get_variant", "cw_batch_autotune", "cw_batch_set_mode", "cw_apply_batched", "cw_apply_host",
     "cw_mesh_refine_vertices", "cw_rules_1d", "cw_basis_1d", "cw_cg_residual", "cw_mg_create", "cw_mg_destroy",
     "cw_mg_device_bytes", "cw_mg_vcycle", "cw_mg_prolong", "cw_mg_restrict", "cw_mg_smooth", "cw_mg_coarse_solve",
-    "cw_mg_pcg_solve", "cw_op_check", "cw_op_inject_stall",
+    "cw_mg_pcg_solve", "cw_op_check", "cw_op_inject_stall", "cw_mblock_create", "cw_mblock_destroy",
+    "cw_mblock_cellwise_len", "cw_mblock_global_len", "cw_mblock_shared_dofs", "cw_mblock_global_index",
+    "cw_mblock_dss", "cw_mblock_apply", "cw_mblock_diagonal", "cw_mblock_cg_solve",
 ]
 
 
@@ -106,6 +108,16 @@ def load(path: str = LIB_PATH):
         "cw_basis_1d": ([i32, vp, vp, vp, vp, vp], i32),
         "cw_cg_residual": ([vp, vp, vp, i32, ctypes.POINTER(dbl), vp], i32),
         "cw_op_check": ([vp, vp], i32),
+        "cw_mblock_create": ([ctypes.POINTER(vp), i32, ctypes.POINTER(vp)], i32),
+        "cw_mblock_destroy": ([vp], i32),
+        "cw_mblock_cellwise_len": ([vp], i64),
+        "cw_mblock_global_len": ([vp], i64),
+        "cw_mblock_shared_dofs": ([vp, i32], i64),
+        "cw_mblock_global_index": ([vp, vp], i32),
+        "cw_mblock_dss": ([vp, vp, i32, vp], i32),
+        "cw_mblock_apply": ([vp, vp, vp, i32, vp], i32),
+        "cw_mblock_diagonal": ([vp, vp, vp], i32),
+        "cw_mblock_cg_solve": ([vp, vp, vp, dbl, i32, ctypes.POINTER(cw_cg_stats), vp], i32),
         "cw_op_inject_stall": ([vp, i32], i32),
         "cw_mg_create": ([ctypes.POINTER(vp), i32, i32, i32, dbl, ctypes.POINTER(vp)], i32),
         "cw_mg_destroy": ([vp], i32),
@@ -689,6 +701,75 @@ class Multigrid:
     def close(self):
         if self.handle:
             cw_mg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MultiBlock:
+    """Owns a cw_mblock handle over per-block Operators (kept referenced); cell-wise vectors are the
+    concatenation of the blocks' vectors."""
+
+    def __init__(self, ops):
+        self.ops = list(ops)
+        n = len(self.ops)
+        h = ctypes.c_void_p()
+        _check(load().cw_mblock_create((ctypes.c_void_p * n)(*[o.handle.value for o in self.ops]), n, ctypes.byref(h)),
+               "cw_mblock_create")
+        self.handle = h
+        self.L = load().cw_mblock_cellwise_len(h)
+        self.NG = load().cw_mblock_global_len(h)
+        self.vec_dtype = self.ops[0].vec_dtype
+
+    def shared_dofs(self):
+        return tuple(load().cw_mblock_shared_dofs(self.handle, s) for s in range(3))
+
+    def global_index(self):
+        import numpy as np
+        out = np.empty(self.L, dtype=np.int64)
+        _check(load().cw_mblock_global_index(self.handle, out.ctypes.data_as(ctypes.c_void_p)), "cw_mblock_global_index")
+        return out
+
+    def empty(self):
+        import torch
+        return torch.empty(self.L, dtype=self.vec_dtype, device="cuda")
+
+    def dss(self, v, average=False):
+        _vec(v, self.L, self.vec_dtype, "mblock dss: v")
+        _check(load().cw_mblock_dss(self.handle, _ptr(v), CW_DSS_AVERAGE if average else CW_DSS_SUM, _stream(None)),
+               "cw_mblock_dss")
+        return v
+
+    def apply(self, x, y=None, assemble=False):
+        _vec(x, self.L, self.vec_dtype, "mblock apply: x")
+        y = self.empty() if y is None else _vec(y, self.L, self.vec_dtype, "mblock apply: y")
+        _check(load().cw_mblock_apply(self.handle, _ptr(x), _ptr(y), CW_APPLY_ASSEMBLE if assemble else CW_APPLY_LOCAL,
+                                      _stream(None)), "cw_mblock_apply")
+        return y
+
+    def diagonal(self):
+        import torch
+        d = torch.empty(self.L, dtype=torch.float64, device="cuda")
+        _check(load().cw_mblock_diagonal(self.handle, _ptr(d), _stream(None)), "cw_mblock_diagonal")
+        return d
+
+    def cg_solve(self, b, u=None, rtol=1e-10, maxit=10000, check=True):
+        import torch
+        _vec(b, self.L, torch.float64, "mblock cg_solve: b")
+        u = torch.empty(self.L, dtype=torch.float64, device="cuda") if u is None else _vec(u, self.L, torch.float64, "u")
+        st = cw_cg_stats()
+        rc = load().cw_mblock_cg_solve(self.handle, _ptr(b), _ptr(u), rtol, maxit, ctypes.byref(st), _stream(None))
+        if check and rc != CW_OK:
+            raise CwError(rc, "cw_mblock_cg_solve")
+        return u, st, rc
+
+    def close(self):
+        if self.handle:
+            _check(load().cw_mblock_destroy(self.handle), "cw_mblock_destroy")
             self.handle = None
 
     def __del__(self):
