@@ -9,11 +9,12 @@ flush is needed between steps.
 Extra measurements in the same JSON line: the same workload in FP32 / BF16-metric / BF16, a
 degree sweep p=1..7 at ~2^27 cell-wise values (FP64, FP32 and BF16 Laplace), the Poisson CG
 time-to-1e-10 (plain FP64 Jacobi-PCG vs FP64 iterative refinement around an FP32 inner CG), the
-same Poisson problem solved with the V-cycle-preconditioned CG (FP64 and FP32 cycles), and
+same Poisson problem solved with the V-cycle-preconditioned CG (FP64 and FP32 cycles), the
+multi-block cube in cube (assembled apply with the inter-block DSS, and its Jacobi-PCG solve), and
 the batched apply (16 RHS on Q5 64^3 + 48 uneven problems in one persistent launch).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-sweep] [--no-cg]
-                  [--no-batched] [--no-mg] [--no-mixed] [--no-e2e] [--no-cpu] [--no-tune] [--variant C,S] [--cg-mode M]
+                  [--no-batched] [--no-mg] [--no-mblock] [--no-mixed] [--no-e2e] [--no-cpu] [--no-tune] [--variant C,S] [--cg-mode M]
                   [--cells N] [--prec P]
 
 --impl reference times the FP64 CPU oracle (explicit element matrices) on a bounded cell sample of
@@ -474,6 +475,8 @@ def gpu_arm(args, rank, local, world):
         out["cg"] = cg_bench(cw, args)
     if args.mg:
         out["mg"] = mg_bench(cw, args, stream)
+    if args.mblock:
+        out["multiblock"] = mblock_bench(cw, args, stream)
     if args.batched:
         out["batched"] = batched_bench(cw, args, stream)
     return out
@@ -683,6 +686,53 @@ def mg_bench(cw, args, stream):
     return res
 
 
+def mblock_bench(cw, args, stream):
+    """The 7-block cube in cube (inner cube [-0.5, 0.5]^3 and six frustum shells out to [-1, 1]^3, the
+    stand-in for the paper's curved multi-block ball), 48^3 cells per block, Q3 Laplace, FP64 double-float
+    (49.5 M cell-wise values): assembled apply (every block's operator, then the structured DSS inside the
+    blocks and the unstructured inter-block DSS), the inter-block DSS alone, and the Jacobi-PCG solve of
+    the sine problem to 1e-10."""
+    import torch
+    p, n = 3, 48
+    mbm = synth.cube_in_cube(n, seed=0)
+    Ms = [cw.Mesh.from_synth(m) for m in mbm.blocks]
+    ops = [cw.Operator(M, p, cw.CW_LAPLACE, cw.CW_GEOM_METRIC, cw.CW_PREC_F64, cw.CW_BC_DIRICHLET0) for M in Ms]
+    for o in ops:
+        xo = o.empty()
+        o.autotune(o.gather(torch.zeros(o.NG, dtype=torch.float64, device="cuda")), xo, reps=2)
+    mb = cw.MultiBlock(ops)
+    x = torch.empty(mb.L, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+    mb.dss(x, average=True)  # a continuous input
+    y = mb.empty()
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = event_pair()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    apply_ms = timed(lambda: mb.apply(x, y, assemble=True), args.steps)
+    local_ms = timed(lambda: mb.apply(x, y, assemble=False), args.steps)
+    dss_ms = timed(lambda: mb.dss(y), args.steps)
+    b = torch.cat([o.load_vector(0) for o in ops])
+    u, st, rc = mb.cg_solve(b, rtol=1e-10, maxit=20000, check=False)
+    out = {"workload": f"7-block cube in cube, {n}^3 cells per block, Q{p} Laplace, {mb.L} cell-wise values, FP64",
+           "assembled_apply_ms": apply_ms, "dofs_per_s": mb.L / (apply_ms * 1e-3),
+           "local_apply_ms": local_ms, "dss_ms": dss_ms, "shared_dofs_face_line_vertex": mb.shared_dofs(),
+           "cg": {"seconds": st.seconds, "iterations": st.iterations, "rel_residual": st.rel_residual,
+                  "status": int(rc)}}
+    mb.close()
+    for o in ops:
+        o.close()
+    return out
+
+
 def mg_cycle_profile(cw, n, prec, cycles=3):
     """Profiling case: V-cycles alone (zero initial guess) on a Q3 hierarchy whose finest mesh has n^3
     cells (6 levels, refined from a curved (n/32)^3 mesh), in one precision; no solver. Returns the mean
@@ -797,6 +847,7 @@ def main():
     ap.add_argument("--no-cg", dest="cg", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-mg", dest="mg", action="store_false")
+    ap.add_argument("--no-mblock", dest="mblock", action="store_false")
     ap.add_argument("--no-mg-jacobi", dest="mg_jacobi", action="store_false",
                     help="multigrid leg without the Jacobi comparison solve")
     ap.add_argument("--profile-mg", type=int, default=0,
