@@ -8,8 +8,8 @@
 //
 // Transfers (Algorithms prolongation and restriction): per parent the 3D child operator is the
 // Kronecker product P_bz x P_by x P_bx of the 1D matrices P_b[i][a] = l_a((g_i + b)/2), applied
-// axis by axis (sum factorisation): prolongation x, then y, then z, fanning 1 -> 2 -> 4 -> 8 blocks;
-// restriction the transposes in the reverse order, summing the children 8 -> 4 -> 2 -> 1.
+// axis by axis (sum factorisation): prolongation z, then y, then x, fanning 1 -> 2 -> 4 -> 8 blocks;
+// restriction the transposes z, y, x, summing the children 8 -> 4 -> 2 -> 1.
 // Intermediate blocks live in shared memory.
 #pragma once
 #include "cw_apply.cuh"
@@ -43,7 +43,9 @@ __device__ __forceinline__ int64_t child_cell(int64_t e, int nx, int ny, int ch)
 
 // uf|K_c (+)= (P_bz x P_by x P_bx) uc|K for every child c of the coarse cells of this CTA.
 // ADD: add into uf (the V-cycle's u += P e), else overwrite (Algorithm prolongation into a zeroed
-// vector). nx, ny: coarse cells per direction.
+// vector). nx, ny: coarse cells per direction. The axes are contracted z, y, x, so that the last phase
+// owns whole x-lines of a child: each thread writes N contiguous values, consecutive threads the
+// consecutive lines of one child (the Kronecker factors commute).
 template <int N, int CP, class Ar, class VS, bool ADD>
 __global__ void __launch_bounds__(8 * N * N * CP) prolong_kernel(const VS *__restrict__ uc, VS *__restrict__ uf,
                                                                   int nx, int ny, int64_t ncoarse,
@@ -53,8 +55,8 @@ __global__ void __launch_bounds__(8 * N * N * CP) prolong_kernel(const VS *__res
     constexpr int N2 = N * N, N3 = N2 * N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *S0 = reinterpret_cast<T *>(smem_raw);  // [CP][N3] coarse values
-    T *S1 = S0 + CP * N3;                     // [CP][2][N3] after x (bx)
-    T *S2 = S1 + 2 * CP * N3;                 // [CP][4][N3] after y (bx + 2 by)
+    T *S1 = S0 + CP * N3;                     // [CP][2][N3] after z (bz)
+    T *S2 = S1 + 2 * CP * N3;                 // [CP][4][N3] after y (by + 2 bz)
     const int t = threadIdx.x;
     const int64_t e0 = static_cast<int64_t>(blockIdx.x) * CP;
     const int64_t nval = ncoarse * N3;
@@ -64,39 +66,39 @@ __global__ void __launch_bounds__(8 * N * N * CP) prolong_kernel(const VS *__res
     }
     __syncthreads();
     T in[N], out[N];
-    if (t < CP * 2 * N2) {  // x: line (j, k) of parent c, child half bx
-        const int c = t / (2 * N2), r = t - c * 2 * N2, bx = r / N2, jk = r - bx * N2;
+    if (t < CP * 2 * N2) {  // z: pencil (i, j) of parent c, child half bz
+        const int c = t / (2 * N2), r = t - c * 2 * N2, bz = r / N2, ij = r - bz * N2;
 #pragma unroll
-        for (int m = 0; m < N; ++m) in[m] = S0[c * N3 + jk * N + m];
-        contract<N, false, Ar>(tab.P[bx], in, out);
+        for (int m = 0; m < N; ++m) in[m] = S0[c * N3 + ij + N2 * m];
+        contract<N, false, Ar>(tab.P[bz], in, out);
 #pragma unroll
-        for (int i = 0; i < N; ++i) S1[(c * 2 + bx) * N3 + jk * N + i] = out[i];
+        for (int k = 0; k < N; ++k) S1[(c * 2 + bz) * N3 + ij + N2 * k] = out[k];
     }
     __syncthreads();
-    if (t < CP * 4 * N2) {  // y: line (i, k), quarter bx + 2 by
+    if (t < CP * 4 * N2) {  // y: line (i, k) of the quarter q = by + 2 bz
         const int c = t / (4 * N2), r = t - c * 4 * N2, q = r / N2, ik = r - q * N2;
-        const int i = ik % N, k = ik / N, bx = q & 1, by = q >> 1;
+        const int i = ik % N, k = ik / N, by = q & 1, bz = q >> 1;
 #pragma unroll
-        for (int m = 0; m < N; ++m) in[m] = S1[(c * 2 + bx) * N3 + i + N * m + N2 * k];
+        for (int m = 0; m < N; ++m) in[m] = S1[(c * 2 + bz) * N3 + i + N * m + N2 * k];
         contract<N, false, Ar>(tab.P[by], in, out);
 #pragma unroll
         for (int j = 0; j < N; ++j) S2[(c * 4 + q) * N3 + i + N * j + N2 * k] = out[j];
     }
     __syncthreads();
-    {  // z: pencil (i, j) of child ch = bx + 2 by + 4 bz
-        const int c = t / (8 * N2), r = t - c * 8 * N2, ch = r / N2, ij = r - ch * N2;
+    {  // x: line (j, k) of child ch = bx + 2 by + 4 bz
+        const int c = t / (8 * N2), r = t - c * 8 * N2, ch = r / N2, jk = r - ch * N2;
         const int64_t e = e0 + c;
 #pragma unroll
-        for (int m = 0; m < N; ++m) in[m] = S2[(c * 4 + (ch & 3)) * N3 + ij + N2 * m];
-        contract<N, false, Ar>(tab.P[ch >> 2], in, out);
+        for (int m = 0; m < N; ++m) in[m] = S2[(c * 4 + (ch >> 1)) * N3 + jk * N + m];
+        contract<N, false, Ar>(tab.P[ch & 1], in, out);
         if (e < ncoarse) {
-            VS *dst = uf + child_cell(e, nx, ny, ch) * N3 + ij;
+            VS *dst = uf + child_cell(e, nx, ny, ch) * N3 + jk * N;
 #pragma unroll
-            for (int k = 0; k < N; ++k) {
+            for (int i = 0; i < N; ++i) {
                 VS o;
-                Ar::to(o, out[k]);
-                if constexpr (ADD) dst[N2 * k] = dst[N2 * k] + o;
-                else dst[N2 * k] = o;
+                Ar::to(o, out[i]);
+                if constexpr (ADD) dst[i] = dst[i] + o;
+                else dst[i] = o;
             }
         }
     }
