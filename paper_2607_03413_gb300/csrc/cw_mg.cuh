@@ -60,6 +60,16 @@ __global__ void __launch_bounds__(8 * N * N * CP) prolong_kernel(const VS *__res
     const int t = threadIdx.x;
     const int64_t e0 = static_cast<int64_t>(blockIdx.x) * CP;
     const int64_t nval = ncoarse * N3;
+    // this thread's fine x-line (last phase): with ADD its old values are loaded first, so that the
+    // read overlaps the three contraction phases instead of stalling the store
+    const int xc = t / (8 * N2), xr = t - xc * 8 * N2, xch = xr / N2, xjk = xr - xch * N2;
+    const int64_t xe = e0 + xc;
+    VS *dst = xe < ncoarse ? uf + child_cell(xe, nx, ny, xch) * N3 + xjk * N : nullptr;
+    VS old[N];
+    if constexpr (ADD) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) old[i] = dst ? dst[i] : VS(0);
+    }
     for (int k = t; k < CP * N3; k += blockDim.x) {
         const int64_t g = e0 * N3 + k;
         S0[k] = g < nval ? Ar::from(ldg_nc(uc + g)) : Ar::zero();
@@ -86,18 +96,15 @@ __global__ void __launch_bounds__(8 * N * N * CP) prolong_kernel(const VS *__res
     }
     __syncthreads();
     {  // x: line (j, k) of child ch = bx + 2 by + 4 bz
-        const int c = t / (8 * N2), r = t - c * 8 * N2, ch = r / N2, jk = r - ch * N2;
-        const int64_t e = e0 + c;
 #pragma unroll
-        for (int m = 0; m < N; ++m) in[m] = S2[(c * 4 + (ch >> 1)) * N3 + jk * N + m];
-        contract<N, false, Ar>(tab.P[ch & 1], in, out);
-        if (e < ncoarse) {
-            VS *dst = uf + child_cell(e, nx, ny, ch) * N3 + jk * N;
+        for (int m = 0; m < N; ++m) in[m] = S2[(xc * 4 + (xch >> 1)) * N3 + xjk * N + m];
+        contract<N, false, Ar>(tab.P[xch & 1], in, out);
+        if (dst) {
 #pragma unroll
             for (int i = 0; i < N; ++i) {
                 VS o;
                 Ar::to(o, out[i]);
-                if constexpr (ADD) dst[i] = dst[i] + o;
+                if constexpr (ADD) dst[i] = old[i] + o;
                 else dst[i] = o;
             }
         }
