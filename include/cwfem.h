@@ -301,13 +301,17 @@ cw_status cw_cg_residual(cw_op op, const double *b, const double *u, int prec, d
  * vectors of ops[i] (stride cw_op_cellwise_len(ops[i]); x[i] and y[i] must not overlap); they are
  * bound at create and used by every launch. All operators must be CW_GEOM_METRIC and share one
  * precision, CW_PREC_F64 (double-float arithmetic) or CW_PREC_F32; they must outlive the batch.
- * Work items are (problem, chunk of tiles, right-hand side), right-hand side fastest, taken from a
- * device counter by persistent CTAs (no waiting: an item number past the end ends a CTA).
- * Mode CW_BATCH_GROUPED (default): one persistent kernel per degree present, shaped like the
- * per-operator kernel (variant = cells-per-CTA choice + 2 * staging mode of cw_op_set_variant, 0..5). Mode
+ * Work items are taken from a device counter by persistent CTAs (no waiting: an item number past the
+ * end ends a CTA). Mode CW_BATCH_GROUPED (default): one persistent kernel per degree present, shaped
+ * like the per-operator kernel (variant = cells-per-CTA choice + 2 * staging mode, 0..5); an item is a
+ * (problem, chunk of tiles) pair and runs every right-hand side of the problem through each tile. With
+ * staging mode 1 a tile's metric is moved into shared memory once and serves all right-hand sides (a
+ * problem with R right-hand sides reads its metric from HBM once, not R times); modes 0 and 2 are the
+ * per-operator kernel's, per right-hand side. Mode
  * CW_BATCH_SINGLE: all degrees in ONE persistent kernel of 128-thread CTAs (variant = 0 full tile,
- * 1 half tile); its 1D tables live in the library's constant memory, uploaded at create, so only
- * one single-mode batch per precision may be launched at a time.
+ * 1 half tile; items are (problem, chunk of tiles, right-hand side), right-hand side fastest); its 1D
+ * tables live in the library's constant memory, uploaded at create, so only one single-mode batch per
+ * precision may be launched at a time.
  */
 #define CW_BATCH_GROUPED 0
 #define CW_BATCH_SINGLE 1

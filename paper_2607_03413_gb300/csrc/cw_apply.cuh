@@ -251,7 +251,8 @@ __host__ __device__ constexpr int metric_ncomp(int kind) { return kind == 1 ? 6 
 // global loads instead.
 // STAGE 0: direct loads; 1: x and metric tiles staged in shared memory by TMA; 2: x tile staged by
 // TMA, metric tile prefetched into L2 by a bulk prefetch (a third of the shared memory of mode 1,
-// so more CTAs per SM), then read with direct loads.
+// so more CTAs per SM), then read with direct loads; 3: the metric tile already in shared memory
+// (staged by the caller for several right-hand sides, gsm), x read directly.
 template <int N, int CPB, class T, class GS>
 __host__ __device__ constexpr size_t metric_smem_bytes(int nc, int stage)
 {
@@ -304,7 +305,8 @@ __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__rest
                                             int64_t ncells, int kind, const TabMetric<N, typename Ar::C> &tab,
                                             int64_t tile, int cpt, unsigned char *smem_raw, df64 *dot = nullptr,
                                             int asm_nx = 0, const VS *sb = nullptr, const VS *sd = nullptr,
-                                            unsigned *status = nullptr, uint32_t dbg_extra = 0)
+                                            unsigned *status = nullptr, uint32_t dbg_extra = 0,
+                                            const GS *gsm = nullptr)
 {
     static_assert(!(RC && STAGE == 1), "recomputed geometry has no metric tile to stage");
     // Double-float renormalisation of the intermediate values: kept where the operator serves the
@@ -362,6 +364,12 @@ __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__rest
             gs = sG + c * NC * N3;
             g_smem = true;  // its wait comes before the physics step
         }
+    } else if constexpr (STAGE == 3) {
+        // the caller passes this tile's metric (gsm): staged in shared memory, where one copy serves
+        // several right-hand sides, or in global memory when it could not be staged (cell slots past
+        // a ragged tile's end read slot 0's, in bounds, and store nothing)
+        gs = gsm + (act ? c : 0) * NC * N3;
+        g_smem = true;
     } else if constexpr (STAGE == 2) {
         bar = reinterpret_cast<uint64_t *>(smem_raw + (3 * CPB * CS * sizeof(T) + 15) / 16 * 16);
         VS *sX = reinterpret_cast<VS *>(S0 + CPB * CS);

@@ -1,9 +1,10 @@
 // cw_batch.cuh -- one persistent launch that applies many operators (uneven meshes, mixed degrees,
 // several right-hand sides each) to their vectors.
 //
-// Work items are (problem, chunk of tiles, right-hand side) with the right-hand side fastest, so the
-// R items of one chunk run at nearly the same time and its metric comes from HBM once and from L2
-// for the other R-1. A chunk holds about kItemValues cell-wise values, enough work to hide the
+// Single mode: work items are (problem, chunk of tiles, right-hand side) with the right-hand side
+// fastest, so the R items of one chunk run at nearly the same time and its metric comes from HBM once
+// and from L2 for the other R-1. Grouped mode: items are (problem, chunk of tiles), and an item runs all
+// R right-hand sides through every tile with the tile's metric staged in shared memory once. A chunk holds about kItemValues cell-wise values, enough work to hide the
 // per-item cost (an atomicAdd on the global counter, a search of the problem table). Each CTA
 // (128 threads) fetches the number of its next item while it works on the current one; an item
 // number past the end ends the CTA (no spinning). The tile size is chosen per degree: the largest
@@ -130,26 +131,47 @@ __device__ __forceinline__ const BatchTables<C> &batch_tables();
 // persistent item loop, its 1D tables (loop-invariant, two floats per entry) were hoisted into
 // registers, which took the kernel from ~80 to 128-166 registers; out of line every table entry
 // stays an immediate constant-bank operand, as in the per-operator kernel. (FP32 bodies stay inline:
-// the call costs them more than it saves.)
+// the call costs them more than it saves.) gsm: the tile's metric in shared memory (STAGE 3).
 template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
 __device__ __noinline__ void grouped_tile(const VS *x, VS *y, const GS *g, int64_t ncells, int kind, int64_t tile,
-                                          unsigned *status)
+                                          unsigned *status, const GS *gsm)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     metric_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, g, ncells, kind, batch_tab<N>(batch_tables<typename Ar::C>()), tile,
-                                           CPB, smem_raw, nullptr, 0, nullptr, nullptr, status);
+                                           CPB, smem_raw, nullptr, 0, nullptr, nullptr, status, 0, gsm);
+}
+
+template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
+__device__ __forceinline__ void grouped_one(const VS *x, VS *y, const GS *g, int64_t ncells, int kind, int64_t tile,
+                                            unsigned *status, const GS *gsm, unsigned char *smem_raw)
+{
+    if constexpr (std::is_same<Ar, ArDF>::value)
+        grouped_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, g, ncells, kind, tile, status, gsm);
+    else
+        metric_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, g, ncells, kind, batch_tab<N>(batch_tables<typename Ar::C>()),
+                                               tile, CPB, smem_raw, nullptr, 0, nullptr, nullptr, status, 0, gsm);
 }
 
 // ---- grouped mode: one persistent kernel per degree, shaped like the per-operator kernel
-// (N*N*CPB threads, optional TMA staging). Work items are (problem, chunk of tiles, right-hand
-// side) over the problems of that degree only.
+// (N*N*CPB threads). Work items are (problem, chunk of tiles) over the problems of that degree; an
+// item runs every right-hand side of its problem through each of its tiles before the next tile.
+// STAGE 1: the tile's metric is moved into shared memory once (a bulk copy on an mbarrier, bounded
+// wait) and serves all the right-hand sides, so a problem with R right-hand sides reads its metric
+// from HBM once instead of R times; the right-hand sides' input is read directly. STAGE 0 and 2: the
+// per-operator kernel's modes, per right-hand side (the metric read again from L2 for each).
 template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
 __global__ void __launch_bounds__(N *N *CPB) batch_degree_kernel(const BatchProb *__restrict__ probs, int nprob,
                                                                   int64_t nitems, unsigned long long *__restrict__ counter)
 {
+    using T = typename Ar::T;
+    constexpr int N3 = N * N * N, CS = Lines<N>::CS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ long long s_next;
     __shared__ int s_prob;
+    // STAGE 1 layout: [line buffers][mbarrier, 16 B][metric tile]
+    const size_t offb = (3 * CPB * CS * sizeof(T) + 15) / 16 * 16;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + offb);
+    GS *sG = reinterpret_cast<GS *>(smem_raw + offb + 16);
     if (threadIdx.x == 0) s_next = static_cast<long long>(atomicAdd(counter, 1ull));
     for (;;) {
         __syncthreads();
@@ -168,20 +190,44 @@ __global__ void __launch_bounds__(N *N *CPB) batch_degree_kernel(const BatchProb
         }
         __syncthreads();
         const BatchProb P = probs[s_prob];
-        const int64_t local = it - P.item0;
-        const int64_t chunk = local / P.nrhs, rhs = local - chunk * P.nrhs;
-        const VS *x = static_cast<const VS *>(P.x) + rhs * P.stride;
-        VS *y = static_cast<VS *>(P.y) + rhs * P.stride;
+        const int64_t chunk = it - P.item0;
         const GS *g = static_cast<const GS *>(P.geo);
         const int64_t t0 = chunk * P.tpi, t1 = min(P.ntiles, t0 + P.tpi);
+        const int NC = metric_ncomp(P.kind);
         for (int64_t tile = t0; tile < t1; ++tile) {
-            if (tile > t0) __syncthreads();
-            if constexpr (std::is_same<Ar, ArDF>::value)
-                grouped_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, g, P.ncells, P.kind, tile, P.status);
-            else
-                metric_tile<N, CPB, Ar, VS, GS, STAGE>(x, y, g, P.ncells, P.kind,
-                                                       batch_tab<N>(batch_tables<typename Ar::C>()), tile, CPB,
-                                                       smem_raw, nullptr, 0, nullptr, nullptr, P.status);
+            if (tile > t0) __syncthreads();  // the previous tile has finished with shared memory
+            bool staged = false;
+            if constexpr (STAGE == 1) {
+                const int64_t cell0 = tile * CPB;
+                const GS *gsrc = g + cell0 * NC * N3;
+                const uint32_t gb = CPB * NC * N3 * sizeof(GS);
+                staged = cell0 + CPB <= P.ncells && aligned16(gsrc) && gb % 16 == 0;  // block-uniform
+                if (staged) {
+                    if (threadIdx.x == 0) mbar_init(bar, 1);
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        mbar_expect_tx(bar, gb);
+                        bulk_g2s(sG, gsrc, gb, bar);
+                    }
+                    const bool ok = mbar_wait_bounded(bar, 0, kWaitLimit);
+                    if (!ok) {  // reported; the copy is waited for once more, the tile reads from global memory
+                        if (P.status) atomicOr(P.status, kDevStatusTimeout);
+                        mbar_wait_bounded(bar, 0, kWaitLimit);
+                    }
+                    staged = !__syncthreads_or(!ok);
+                }
+            }
+            for (int r = 0; r < P.nrhs; ++r) {
+                if (r > 0) __syncthreads();  // the previous right-hand side has finished with the line buffers
+                const VS *x = static_cast<const VS *>(P.x) + r * P.stride;
+                VS *y = static_cast<VS *>(P.y) + r * P.stride;
+                if constexpr (STAGE == 1) {  // one code path: the metric from shared or from global memory
+                    const GS *gm = staged ? sG : g + tile * CPB * NC * N3;
+                    grouped_one<N, CPB, Ar, VS, GS, 3>(x, y, g, P.ncells, P.kind, tile, P.status, gm, smem_raw);
+                } else {
+                    grouped_one<N, CPB, Ar, VS, GS, STAGE>(x, y, g, P.ncells, P.kind, tile, P.status, nullptr, smem_raw);
+                }
+            }
         }
     }
 }
