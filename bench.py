@@ -733,6 +733,32 @@ def mblock_bench(cw, args, stream):
     return out
 
 
+def batch_profile(cw, n, variant, launches=3):
+    """Profiling case: one grouped batch of 16 right-hand sides on a Q5 n^3 curved mesh (FP32 Laplace)
+    with the given variant of degree 5 (cells-per-CTA choice + 2 * staging mode), launched a few times;
+    returns the mean launch time in ms."""
+    import torch
+    mesh = synth.box_mesh(n, perturb=0.1)
+    M = cw.Mesh.from_synth(mesh)
+    op = cw.Operator(M, 5, cw.CW_LAPLACE, cw.CW_GEOM_METRIC, cw.CW_PREC_F32)
+    x = torch.empty((16, op.L), dtype=torch.float32, device="cuda").uniform_(-1, 1)
+    y = torch.empty_like(x)
+    B = cw.Batch([op], [16], [x], [y])
+    B.set_variant(5, variant)
+    B.launch()
+    torch.cuda.synchronize()
+    a, e = event_pair()
+    a.record()
+    for _ in range(launches):
+        B.launch()
+    e.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(e) / launches
+    B.close()
+    op.close()
+    return ms
+
+
 def mg_cycle_profile(cw, n, prec, cycles=3):
     """Profiling case: V-cycles alone (zero initial guess) on a Q3 hierarchy whose finest mesh has n^3
     cells (6 levels, refined from a curved (n/32)^3 mesh), in one precision; no solver. Returns the mean
@@ -852,6 +878,9 @@ def main():
                     help="multigrid leg without the Jacobi comparison solve")
     ap.add_argument("--profile-mg", type=int, default=0,
                     help="profiling case: only V-cycles on an N^3 Q3 hierarchy (FP32), then exit")
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="profiling case: only a 16-RHS grouped batch on a Q5 N^3 mesh (FP32), then exit")
+    ap.add_argument("--batch-variant", type=int, default=2, help="degree-5 variant of --profile-batch")
     ap.add_argument("--no-mixed", dest="mixed", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
@@ -869,6 +898,14 @@ def main():
         out = reference_arm(args, rank, world)
         if out is not None:
             print(json.dumps(out))
+        return
+    if args.profile_batch:
+        import torch
+        import paper_2607_03413_gb300 as cw
+        torch.cuda.set_device(0)
+        cw.load()
+        print(json.dumps({"profile": "batch_16rhs_q5", "cells": args.profile_batch ** 3, "variant": args.batch_variant,
+                          "ms_per_launch": batch_profile(cw, args.profile_batch, args.batch_variant)}))
         return
     if args.profile_mg:
         import torch

@@ -80,15 +80,17 @@ static cw_status batch_rebuild(Batch &b)
         P.nrhs = b.nrhs[i];
         P.cpt = b.mode == CW_BATCH_SINGLE ? batch_cpt(o.n, b.half[o.n]) : degree_cpb(o.n, b.variant[o.n] & 1);
         P.ntiles = (o.E + P.cpt - 1) / P.cpt;
-        // grouped items carry every right-hand side of their tiles: fewer tiles per item
-        const int rh = b.mode == CW_BATCH_SINGLE ? 1 : P.nrhs;
+        // grouped items with the metric staged once (staging mode 1) carry every right-hand side of
+        // their tiles: fewer tiles per item
+        const bool all_rhs = b.mode == CW_BATCH_GROUPED && (b.variant[o.n] >> 1) == 1;
+        const int rh = all_rhs ? P.nrhs : 1;
         P.tpi = std::max(1, kItemValues / (P.cpt * o.n * o.n * o.n * rh));
         if (b.mode == CW_BATCH_GROUPED && b.g_count[o.n] == 0) {  // items restart per degree group
             b.g_first[o.n] = (int64_t)i;
             item = 0;
         }
         P.item0 = item;
-        item += (P.ntiles + P.tpi - 1) / P.tpi * (b.mode == CW_BATCH_SINGLE ? P.nrhs : 1);
+        item += (P.ntiles + P.tpi - 1) / P.tpi * (all_rhs ? 1 : P.nrhs);
         b.values += o.L * b.nrhs[i];
         b.g_count[o.n] += 1;
         b.g_items[o.n] = item;

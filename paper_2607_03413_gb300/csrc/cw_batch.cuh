@@ -153,12 +153,12 @@ __device__ __forceinline__ void grouped_one(const VS *x, VS *y, const GS *g, int
 }
 
 // ---- grouped mode: one persistent kernel per degree, shaped like the per-operator kernel
-// (N*N*CPB threads). Work items are (problem, chunk of tiles) over the problems of that degree; an
-// item runs every right-hand side of its problem through each of its tiles before the next tile.
-// STAGE 1: the tile's metric is moved into shared memory once (a bulk copy on an mbarrier, bounded
-// wait) and serves all the right-hand sides, so a problem with R right-hand sides reads its metric
-// from HBM once instead of R times; the right-hand sides' input is read directly. STAGE 0 and 2: the
-// per-operator kernel's modes, per right-hand side (the metric read again from L2 for each).
+// (N*N*CPB threads) over the problems of that degree. STAGE 1: work items are (problem, chunk of
+// tiles), and an item runs every right-hand side of its problem through each tile with the tile's
+// metric moved into shared memory once (a bulk copy on an mbarrier, bounded wait), so a problem with
+// R right-hand sides reads its metric from HBM once instead of R times; the right-hand sides' input is
+// read directly. STAGE 0 and 2: the per-operator kernel's modes, items (problem, chunk, right-hand
+// side) with the right-hand side fastest (the metric of a chunk read again from L2 for each).
 template <int N, int CPB, class Ar, class VS, class GS, int STAGE>
 __global__ void __launch_bounds__(N *N *CPB) batch_degree_kernel(const BatchProb *__restrict__ probs, int nprob,
                                                                   int64_t nitems, unsigned long long *__restrict__ counter)
@@ -190,7 +190,12 @@ __global__ void __launch_bounds__(N *N *CPB) batch_degree_kernel(const BatchProb
         }
         __syncthreads();
         const BatchProb P = probs[s_prob];
-        const int64_t chunk = it - P.item0;
+        const int64_t local = it - P.item0;
+        // STAGE 1: item = chunk, every right-hand side inside; else item = (chunk, right-hand side),
+        // right-hand side fastest, so that one item streams consecutive tiles of one vector
+        const int64_t chunk = STAGE == 1 ? local : local / P.nrhs;
+        const int r0 = STAGE == 1 ? 0 : static_cast<int>(local - chunk * P.nrhs);
+        const int r1 = STAGE == 1 ? P.nrhs : r0 + 1;
         const GS *g = static_cast<const GS *>(P.geo);
         const int64_t t0 = chunk * P.tpi, t1 = min(P.ntiles, t0 + P.tpi);
         const int NC = metric_ncomp(P.kind);
@@ -217,8 +222,8 @@ __global__ void __launch_bounds__(N *N *CPB) batch_degree_kernel(const BatchProb
                     staged = !__syncthreads_or(!ok);
                 }
             }
-            for (int r = 0; r < P.nrhs; ++r) {
-                if (r > 0) __syncthreads();  // the previous right-hand side has finished with the line buffers
+            for (int r = r0; r < r1; ++r) {
+                if (r > r0) __syncthreads();  // the previous right-hand side has finished with the line buffers
                 const VS *x = static_cast<const VS *>(P.x) + r * P.stride;
                 VS *y = static_cast<VS *>(P.y) + r * P.stride;
                 if constexpr (STAGE == 1) {  // one code path: the metric from shared or from global memory
