@@ -28,4 +28,8 @@ def test_readme_quick_start_runs(tmp_path, monkeypatch):
     for o, x, y in zip(ns["ops"], ns["xs"], ns["ys"]):
         for r in range(x.shape[0]):
             assert torch.equal(y[r], o.apply(x[r]))
+    # the multigrid solve converges in a handful of V-cycles; the two-block solve converges
+    assert ns["mg_rc"] == cw.CW_OK and ns["mg_stats"].rel_residual <= 1e-10 and ns["mg_stats"].iterations <= 20
+    assert ns["mb_rc"] == cw.CW_OK and ns["mb_stats"].rel_residual <= 1e-10
+    assert ns["mb"].shared_dofs()[0] > 0  # the glued face's interior DoFs
     assert (tmp_path / "tune.json").exists()
