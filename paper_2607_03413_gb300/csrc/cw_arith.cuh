@@ -25,9 +25,9 @@ struct __align__(8) df64s {
 
 // ---------------------------------------------------------------- conversions ----
 
-// Split a double into hi + lo floats using integer operations only. |x| < 2^-126 maps to 0 and
-// the low part is dropped when it would be subnormal (|x| < 2^-80); both are far below the
-// precision the operator needs relative to the vector norm. Infinities, NaNs and finite values
+// Split a double into hi + lo floats using integer operations only. |x| < 2^-126 maps to 0; the
+// low part is exact while it is a normal float (|x| above about 2^-102) and rounded to the float
+// subnormal grid below that. Infinities, NaNs and finite values
 // beyond the float range map to +-inf / NaN in hi (lo = 0), so non-finite data stays non-finite.
 __device__ __forceinline__ df64 split_f64(double x)
 {
@@ -53,10 +53,15 @@ __device__ __forceinline__ df64 split_f64(double x)
     // remainder: the low 29 mantissa bits, worth rem * 2^(e-1075); keep its top 23 bits
     const unsigned r23 = (l32 & 0x1FFFFFFFu) >> 6;
     const float f = __fsub_rn(__uint_as_float(0x4B000000u | r23), 8388608.0f);  // exact
-    const int se = e - 942;  // biased exponent of 2^(e-1069), in [1, 254] when fe in [1, 254] and se >= 1
-    const float scale = __uint_as_float(static_cast<unsigned>(max(se, 1)) << 23);
-    const float lo = __fmul_rn(f, scale);
-    r.lo = (se >= 1) ? __uint_as_float(__float_as_uint(lo) | sign) : 0.0f;
+    // scale by 2^(e-1069): one power-of-two factor (biased exponent se = e - 942) while that is a
+    // normal float, else 2^(e-1069+64) and then 2^-64 (f * 2^(e-1005) is exact and normal for every
+    // e >= 897; the second product is exact while the low part is normal)
+    const int se = e - 942;
+    const bool tiny = se < 1;
+    const float scale = __uint_as_float(static_cast<unsigned>(tiny ? se + 64 : se) << 23);
+    float lo = __fmul_rn(f, scale);
+    if (tiny) lo = __fmul_rn(lo, 5.42101086242752217e-20f);  // 2^-64
+    r.lo = __uint_as_float(__float_as_uint(lo) | sign);
     return r;
 }
 
