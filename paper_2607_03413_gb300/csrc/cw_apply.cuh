@@ -230,6 +230,106 @@ struct Lines {
     static __device__ __forceinline__ int z(int ra, int rb, int m) { return ra + PI * (rb + N * m); }
 };
 
+// ---- line buffers of the curved kernels (metric_tile)
+// Element (i, j, k) of cell slot c sits at c*CS + i + PI*j + PP*k in each of the three buffers, and
+// buffer R starts at element R*RS (RS: CPB*CS rounded up to 16 bytes, so that a bulk copy can land in
+// buffer 1). A thread keeps the z-pencil (i, j) = (ra, rb) of its own cell in registers from one step
+// to the next, and serves x-line (j, k) = (ra, rb) of its own cell where a step reads the input from
+// memory or writes the output (coalesced global accesses). The other x-line steps and the y-line
+// steps only load a line from shared memory, contract it and store it back, so any thread may serve
+// any cell's line there: with `deal_x` / `deal_y` those lines are dealt to threads in the order of the
+// shared-memory bank of their first element, round-robin over the warps, so that a warp touches
+// distinct banks wherever the bank counts allow. The pitches come from an exhaustive search over
+// (PI, PP, CS <= 1.6 n^3) that minimised the wavefronts of all line accesses of one apply (per
+// element: 2 x-line accesses in thread order, 4 dealt, 8 y-line, 9 z-pencil) for 4-byte elements:
+// at n = 5 and 8 cells per CTA 1105 instead of 1315 per tile (805 without any conflict). Dealing the
+// global x-line steps as well cut more wavefronts but scattered the output stores over the tile's
+// cells (2.4x the L2 store sectors) and was slower. Double-float and FP64 tiles (8-byte elements)
+// keep odd row pitches with lines in thread order: their kernel is bound by the FP32 pipes, and 22 %
+// fewer wavefronts changed nothing in its time.
+struct TileGeom {
+    int pi, pp, cs;  // row pitch, plane pitch, cell stride (elements)
+    bool deal_x, deal_y;
+};
+__host__ __device__ constexpr TileGeom tile_geom(int N, int CPB, int ESZ, bool allow_remap)
+{
+    if (allow_remap && ESZ == 4) {
+        switch (N * 100 + CPB) {
+        case 216: case 232: return {2, 6, 12, false, true};
+        case 308: case 316: return {3, 10, 41, true, true};
+        case 404: case 408: return {4, 19, 80, true, true};
+        case 504: case 508: return {5, 33, 185, true, true};
+        case 602: case 604: return {6, 37, 228, true, true};
+        case 704: return {7, 73, 529, true, true};
+        case 802: return {8, 66, 528, true, true};
+        default: break;
+        }
+    }
+    return {N | 1, N * (N | 1), N * N * (N | 1), false, false};
+}
+
+template <int N, int CPB, int ESZ, bool REMAP>
+struct TileLines {
+    static constexpr TileGeom G = tile_geom(N, CPB, ESZ, REMAP);
+    static constexpr int PI = G.pi, PP = G.pp, CS = G.cs;
+    static constexpr int RS = (CPB * CS * ESZ + 15) / 16 * 16 / ESZ;  // buffer stride (elements)
+    static_assert(PI >= N && PP >= N * PI && CS >= N * PP, "tile buffers overlap");
+};
+
+// in the shared-memory-only steps thread t serves x-line m[t] >> 16 and y-line m[t] & 0xffff; a line
+// l = c N^2 + a + N b is cell slot c's x-line (j, k) = (a, b) or y-line (i, k) = (a, b)
+template <int N, int CPB, int ESZ>
+struct LineMap {
+    uint32_t m[N * N * CPB];
+};
+template <int N, int CPB, int ESZ, bool REMAP>
+constexpr LineMap<N, CPB, ESZ> make_line_map()
+{
+    constexpr TileGeom G = tile_geom(N, CPB, ESZ, REMAP);
+    constexpr int T = N * N * CPB, N2 = N * N;
+    constexpr int GRP = ESZ == 4 ? 32 : 16;  // lanes served by one wavefront = banks, in elements
+    constexpr int NG = (T + GRP - 1) / GRP;
+    LineMap<N, CPB, ESZ> r{};
+    for (int dir = 0; dir < 2; ++dir) {
+        int order[T] = {};
+        int n = 0;
+        for (int b = 0; b < GRP; ++b)
+            for (int l = 0; l < T; ++l) {
+                const int c = l / N2, a = l % N, bb = (l / N) % N;
+                const int base = c * G.cs + (dir == 0 ? G.pi * a : a) + G.pp * bb;
+                if (base % GRP == b) order[n++] = l;
+            }
+        n = 0;
+        for (int lane = 0; lane < GRP; ++lane)
+            for (int g = 0; g < NG; ++g) {
+                const int t = g * GRP + lane;
+                if (t >= T) continue;
+                const uint32_t l = static_cast<uint32_t>((dir == 0 ? G.deal_x : G.deal_y) ? order[n++] : t);
+                r.m[t] |= dir == 0 ? (l << 16) : l;
+            }
+    }
+    return r;
+}
+template <int N, int CPB, int ESZ, bool REMAP>
+constexpr bool line_map_is_bijection()
+{
+    constexpr LineMap<N, CPB, ESZ> M = make_line_map<N, CPB, ESZ, REMAP>();
+    constexpr int T = N * N * CPB;
+    bool seen_x[T] = {}, seen_y[T] = {};
+    for (int t = 0; t < T; ++t) {
+        const uint32_t lx = M.m[t] >> 16, ly = M.m[t] & 0xffffu;
+        if (lx >= static_cast<uint32_t>(T) || ly >= static_cast<uint32_t>(T) || seen_x[lx] || seen_y[ly]) return false;
+        seen_x[lx] = seen_y[ly] = true;
+    }
+    return true;
+}
+template <int N, int CPB, int ESZ, bool REMAP>
+__device__ constexpr LineMap<N, CPB, ESZ> kLineMap = make_line_map<N, CPB, ESZ, REMAP>();
+
+// element m of a line in buffer R: x-line at offset o (stride 1), y-line (stride PI), z-pencil (PP)
+#define CW_TLD(R, o, st, v) _Pragma("unroll") for (int m_ = 0; m_ < N; ++m_) v[m_] = S0[(R) * TL::RS + (o) + (st) * m_]
+#define CW_TST(R, o, st, v) _Pragma("unroll") for (int m_ = 0; m_ < N; ++m_) S0[(R) * TL::RS + (o) + (st) * m_] = v[m_]
+
 #define CW_LDX(s, v) _Pragma("unroll") for (int m_ = 0; m_ < N; ++m_) v[m_] = (s)[L::x(ra, rb, m_)]
 #define CW_LDY(s, v) _Pragma("unroll") for (int m_ = 0; m_ < N; ++m_) v[m_] = (s)[L::y(ra, rb, m_)]
 #define CW_LDZ(s, v) _Pragma("unroll") for (int m_ = 0; m_ < N; ++m_) v[m_] = (s)[L::z(ra, rb, m_)]
@@ -253,13 +353,11 @@ __host__ __device__ constexpr int metric_ncomp(int kind) { return kind == 1 ? 6 
 // TMA, metric tile prefetched into L2 by a bulk prefetch (a third of the shared memory of mode 1,
 // so more CTAs per SM), then read with direct loads; 3: the metric tile already in shared memory
 // (staged by the caller for several right-hand sides, gsm), x read directly.
-template <int N, int CPB, class T, class GS>
+template <int N, int CPB, class T, class GS, bool REMAP = true>
 __host__ __device__ constexpr size_t metric_smem_bytes(int nc, int stage)
 {
-    return stage == 1 ? ((3 * CPB * Lines<N>::CS * sizeof(T) + 15) / 16 * 16 +
-                         (CPB * nc * N * N * N * sizeof(GS) + 15) / 16 * 16 + 16)
-           : stage == 2 ? (3 * CPB * Lines<N>::CS * sizeof(T) + 15) / 16 * 16 + 16
-                        : 3 * CPB * Lines<N>::CS * sizeof(T);
+    constexpr size_t lb = 3 * TileLines<N, CPB, sizeof(T), REMAP>::RS * sizeof(T);  // a multiple of 16
+    return stage == 1 ? lb + (CPB * nc * N * N * N * sizeof(GS) + 15) / 16 * 16 + 16 : stage == 2 ? lb + 16 : lb;
 }
 
 // One tile of `cpt` consecutive cells starting at cell tile*cpt, worked by CPB cell slots of N*N
@@ -300,7 +398,7 @@ static __device__ __noinline__ void wait_expired(unsigned *status, uint64_t *bar
 // arms the input tile's barrier with dbg_extra bytes more than the copy delivers, so that its phase
 // can never complete and the (then short) bounded wait runs out.
 template <int N, int CPB, class Ar, class VS, class GS, int STAGE, bool DOT = false, bool RC = false,
-          bool SMOOTH = false>
+          bool SMOOTH = false, bool REMAP = true>
 __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__restrict__ geo,
                                             int64_t ncells, int kind, const TabMetric<N, typename Ar::C> &tab,
                                             int64_t tile, int cpt, unsigned char *smem_raw, df64 *dot = nullptr,
@@ -315,8 +413,9 @@ __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__rest
     // errors against the oracle <= 1.0e-13 instead of <= 3e-14).
     constexpr bool NRM = DOT;
     using T = typename Ar::T;
-    using L = Lines<N>;
-    constexpr int N2 = N * N, N3 = N2 * N, CS = L::CS;
+    using TL = TileLines<N, CPB, sizeof(T), REMAP>;
+    static_assert(line_map_is_bijection<N, CPB, sizeof(T), REMAP>(), "every line has one thread");
+    constexpr int N2 = N * N, N3 = N2 * N, PI = TL::PI, PP = TL::PP, CS = TL::CS, RS = TL::RS;
     const bool HAS_K = (kind & 1) != 0, HAS_M = (kind & 2) != 0;
     const int NC = metric_ncomp(kind);
     T *S0 = reinterpret_cast<T *>(smem_raw);
@@ -325,9 +424,19 @@ __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__rest
     const int64_t cell0 = tile * cpt;
     const int64_t cell = cell0 + c;
     const bool act = c < cpt && cell < ncells;
-    T *s0 = S0 + c * CS;
-    T *s1 = S0 + (CPB + c) * CS;
-    T *s2 = S0 + (2 * CPB + c) * CS;
+    // offsets of the first elements of this thread's lines in a buffer: its own cell's x-line
+    // (j, k) = (ra, rb) (xi, the steps that read or write memory) and z-pencil (i, j) = (ra, rb) (zo);
+    // the dealt x-line (xo) and y-line (yo) of the shared-memory-only steps
+    const int xi = c * CS + PI * ra + PP * rb;
+    const int zo = c * CS + ra + PI * rb;
+    int xo = xi, yo = c * CS + ra + PP * rb;
+    if constexpr (TL::G.deal_x || TL::G.deal_y) {
+        const uint32_t lm = kLineMap<N, CPB, sizeof(T), REMAP>.m[t];
+        const int lx = static_cast<int>(lm >> 16), ly = static_cast<int>(lm & 0xffffu);
+        const int xc = lx / N2, xr = lx - xc * N2, yc = ly / N2, yr = ly - yc * N2;
+        xo = xc * CS + PI * (xr % N) + PP * (xr / N);
+        yo = yc * CS + (yr % N) + PP * (yr / N);
+    }
 
     // ---- tile staging (single right-hand side)
     bool x_smem = false, g_smem = false, x_ok = true;
@@ -336,10 +445,10 @@ __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__rest
     uint64_t *bar = nullptr;
     const uint32_t lim = dbg_extra ? kWaitLimitInjected : kWaitLimit;
     if constexpr (STAGE == 1) {
-        const size_t offg = (3 * CPB * CS * sizeof(T) + 15) / 16 * 16;
+        const size_t offg = 3 * RS * sizeof(T);
         GS *sG = reinterpret_cast<GS *>(smem_raw + offg);
         bar = reinterpret_cast<uint64_t *>(smem_raw + offg + (CPB * NC * N3 * sizeof(GS) + 15) / 16 * 16);
-        VS *sX = reinterpret_cast<VS *>(S0 + CPB * CS);  // the S1 region is free until the gradients
+        VS *sX = reinterpret_cast<VS *>(S0 + RS);  // buffer 1 is free until the gradients
         const VS *xsrc = x + cell0 * N3;
         const GS *gsrc = geo + cell0 * NC * N3;
         const uint32_t xb = CPB * N3 * sizeof(VS), gb = CPB * NC * N3 * sizeof(GS);
@@ -371,8 +480,8 @@ __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__rest
         gs = gsm + (act ? c : 0) * NC * N3;
         g_smem = true;
     } else if constexpr (STAGE == 2) {
-        bar = reinterpret_cast<uint64_t *>(smem_raw + (3 * CPB * CS * sizeof(T) + 15) / 16 * 16);
-        VS *sX = reinterpret_cast<VS *>(S0 + CPB * CS);
+        bar = reinterpret_cast<uint64_t *>(smem_raw + 3 * RS * sizeof(T));
+        VS *sX = reinterpret_cast<VS *>(S0 + RS);
         const VS *xsrc = x + cell0 * N3;
         constexpr int GV = RC ? kTriCoef : 0;  // geometry values per cell (RC), else NC * N3
         const int gpc = RC ? GV : NC * N3;
@@ -396,8 +505,6 @@ __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__rest
     }
 
     {
-        const VS *xr = x;
-        VS *yr = y;
         T v[N], w[N], u[N], acc[N], gx[N], gy[N], gz[N];
         // (1) x-line (j,k) = (ra, rb): N contiguous values of the cell, contracted with B along x
         {
@@ -405,45 +512,45 @@ __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__rest
 #pragma unroll
                 for (int m = 0; m < N; ++m) v[m] = x_ok ? Ar::from(xs[N * r + m]) : Ar::zero();
             } else {
-                const VS *xc = xr + (act ? cell : 0) * N3 + N * r;
+                const VS *xg = x + (act ? cell : 0) * N3 + N * r;
 #pragma unroll
-                for (int m = 0; m < N; ++m) v[m] = act ? Ar::from(ldg_nc(xc + m)) : Ar::zero();
+                for (int m = 0; m < N; ++m) v[m] = act ? Ar::from(ldg_nc(xg + m)) : Ar::zero();
             }
             sweep<N, Ar, 0, NRM>(tab, v, w);
-            CW_STX(s0, w);
+            CW_TST(0, xi, 1, w);
         }
         __syncthreads();
         // (2) y-line (i,k): contract with B along y, in place
         {
-            CW_LDY(s0, v);
+            CW_TLD(0, yo, PI, v);
             sweep<N, Ar, 0, NRM>(tab, v, w);
-            CW_STY(s0, w);
+            CW_TST(0, yo, PI, w);
         }
         __syncthreads();
         // (3) z-pencil (i,j): contract with B along z -> u at the Gauss points (registers)
         {
-            CW_LDZ(s0, v);
+            CW_TLD(0, zo, PP, v);
             sweep<N, Ar, 0, NRM>(tab, v, u);
         }
         if (HAS_K) {
             {
                 sweep<N, Ar, 2, NRM>(tab, u, gz);
-                CW_STZ(s0, u);
+                CW_TST(0, zo, PP, u);
             }
             __syncthreads();
             // x- and y-derivatives by collocation, as line owners
             {
-                CW_LDX(s0, v);
+                CW_TLD(0, xo, 1, v);
                 sweep<N, Ar, 2, NRM>(tab, v, w);
-                CW_STX(s1, w);
-                CW_LDY(s0, v);
+                CW_TST(1, xo, 1, w);
+                CW_TLD(0, yo, PI, v);
                 sweep<N, Ar, 2, NRM>(tab, v, w);
-                CW_STY(s2, w);
+                CW_TST(2, yo, PI, w);
             }
             __syncthreads();
             {
-                CW_LDZ(s1, gx);
-                CW_LDZ(s2, gy);
+                CW_TLD(1, zo, PP, gx);
+                CW_TLD(2, zo, PP, gy);
             }
         }
         // the metric tile's wait (a thread whose wait expired reads the metric from global memory)
@@ -577,22 +684,22 @@ __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__rest
                 sweep<N, Ar, 3, NRM>(tab, gz, v);
 #pragma unroll
                 for (int k = 0; k < N; ++k) acc[k] = HAS_M ? Ar::add(acc[k], v[k]) : v[k];
-                CW_STZ(s1, gx);  // own pencil only: no other thread reads s1/s2 pencils now
-                CW_STZ(s2, gy);
+                CW_TST(1, zo, PP, gx);  // own pencil only: no other thread reads s1/s2 pencils now
+                CW_TST(2, zo, PP, gy);
             }
             __syncthreads();
             {
-                CW_LDX(s1, v);
+                CW_TLD(1, xo, 1, v);
                 sweep<N, Ar, 3, NRM>(tab, v, w);
-                CW_STX(s1, w);
-                CW_LDY(s2, v);
+                CW_TST(1, xo, 1, w);
+                CW_TLD(2, yo, PI, v);
                 sweep<N, Ar, 3, NRM>(tab, v, w);
-                CW_STY(s2, w);
+                CW_TST(2, yo, PI, w);
             }
             __syncthreads();
             {
-                CW_LDZ(s1, v);
-                CW_LDZ(s2, w);
+                CW_TLD(1, zo, PP, v);
+                CW_TLD(2, zo, PP, w);
 #pragma unroll
                 for (int k = 0; k < N; ++k) {
                     const T t = Ar::add(acc[k], Ar::add(v[k], w[k]));
@@ -603,17 +710,17 @@ __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__rest
         // (5) integrate back: B^T along z (registers), y and x as line owners
         {
             sweep<N, Ar, 1, NRM>(tab, acc, w);
-            CW_STZ(s0, w);
+            CW_TST(0, zo, PP, w);
         }
         __syncthreads();
         {
-            CW_LDY(s0, v);
+            CW_TLD(0, yo, PI, v);
             sweep<N, Ar, 1, NRM>(tab, v, w);
-            CW_STY(s0, w);
+            CW_TST(0, yo, PI, w);
         }
         __syncthreads();
         {
-            CW_LDX(s0, v);
+            CW_TLD(0, xi, 1, v);
             sweep<N, Ar, 1, NRM>(tab, v, w);
             if constexpr (SMOOTH) {
                 VS nv[N];
@@ -624,15 +731,15 @@ __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__rest
                     Ar::to(av, w[m]);
                     nv[m] = act ? y[o + m] + sd[o + m] * (sb[o + m] - av) : VS(0);
                 }
-                VS *exl = reinterpret_cast<VS *>(S0 + CPB * CS), *exr = exl + CPB * N2;  // S1 is free
+                VS *exl = reinterpret_cast<VS *>(S0 + RS), *exr = exl + CPB * N2;  // buffer 1 is free
                 exl[c * N2 + r] = nv[0];
                 exr[c * N2 + r] = nv[N - 1];
                 __syncthreads();
                 if (act) {
-                    const int64_t cx = cell % asm_nx;
-                    if (c + 1 < cpt && cell + 1 < ncells && cx + 1 < asm_nx)
+                    const int64_t ix = cell % asm_nx;
+                    if (c + 1 < cpt && cell + 1 < ncells && ix + 1 < asm_nx)
                         nv[N - 1] = AddOp<VS>::add(nv[N - 1], exl[(c + 1) * N2 + r]) * VS(0.5);
-                    if (c > 0 && cx > 0) nv[0] = AddOp<VS>::add(exr[(c - 1) * N2 + r], nv[0]) * VS(0.5);
+                    if (c > 0 && ix > 0) nv[0] = AddOp<VS>::add(exr[(c - 1) * N2 + r], nv[0]) * VS(0.5);
 #pragma unroll
                     for (int m = 0; m < N; ++m) y[o + m] = nv[m];
                 }
@@ -641,23 +748,23 @@ __device__ __forceinline__ void metric_tile(const VS *x, VS *y, const GS *__rest
                 Ar::to(o0, w[0]);
                 Ar::to(o1, w[N - 1]);
                 // the S1 buffer is free: its last reads precede the first barrier of step (5)
-                VS *exl = reinterpret_cast<VS *>(S0 + CPB * CS), *exr = exl + CPB * N2;
+                VS *exl = reinterpret_cast<VS *>(S0 + RS), *exr = exl + CPB * N2;
                 exl[c * N2 + r] = o0;
                 exr[c * N2 + r] = o1;
                 __syncthreads();
                 if (act) {
-                    const int64_t cx = cell % asm_nx;
-                    if (c + 1 < cpt && cell + 1 < ncells && cx + 1 < asm_nx)
+                    const int64_t ix = cell % asm_nx;
+                    if (c + 1 < cpt && cell + 1 < ncells && ix + 1 < asm_nx)
                         o1 = AddOp<VS>::add(o1, exl[(c + 1) * N2 + r]);
-                    if (c > 0 && cx > 0) o0 = AddOp<VS>::add(exr[(c - 1) * N2 + r], o0);
-                    VS *yc = yr + cell * N3 + N * r;
+                    if (c > 0 && ix > 0) o0 = AddOp<VS>::add(exr[(c - 1) * N2 + r], o0);
+                    VS *yc = y + cell * N3 + N * r;
                     yc[0] = o0;
 #pragma unroll
                     for (int m = 1; m < N - 1; ++m) Ar::to(yc[m], w[m]);
                     yc[N - 1] = o1;
                 }
             } else if (act) {
-                VS *yc = yr + cell * N3 + N * r;
+                VS *yc = y + cell * N3 + N * r;
 #pragma unroll
                 for (int m = 0; m < N; ++m) Ar::to(yc[m], w[m]);
             }

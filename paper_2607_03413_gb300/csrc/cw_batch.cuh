@@ -79,8 +79,9 @@ __device__ __noinline__ void batch_item(const BatchProb &P, const BatchTables<ty
     const int64_t t0 = chunk * P.tpi, t1 = min(P.ntiles, t0 + P.tpi);
     for (int64_t tile = t0; tile < t1; ++tile) {
         if (tile > t0) __syncthreads();  // the previous tile has finished with shared memory
-        metric_tile<N, batch_slots(N), Ar, VS, GS, 0>(x, y, g, P.ncells, P.kind, batch_tab<N>(T), tile, P.cpt, smem,
-                                                      nullptr, 0, nullptr, nullptr, P.status);
+        // kBatchThreads threads, not N*N*slots: lines stay in thread order (slots past cpt are idle)
+        metric_tile<N, batch_slots(N), Ar, VS, GS, 0, false, false, false, false>(
+            x, y, g, P.ncells, P.kind, batch_tab<N>(T), tile, P.cpt, smem, nullptr, 0, nullptr, nullptr, P.status);
     }
 }
 
@@ -164,12 +165,12 @@ __global__ void __launch_bounds__(N *N *CPB) batch_degree_kernel(const BatchProb
                                                                   int64_t nitems, unsigned long long *__restrict__ counter)
 {
     using T = typename Ar::T;
-    constexpr int N3 = N * N * N, CS = Lines<N>::CS;
+    constexpr int N3 = N * N * N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ long long s_next;
     __shared__ int s_prob;
     // STAGE 1 layout: [line buffers][mbarrier, 16 B][metric tile]
-    const size_t offb = (3 * CPB * CS * sizeof(T) + 15) / 16 * 16;
+    const size_t offb = 3 * TileLines<N, CPB, sizeof(T), true>::RS * sizeof(T);  // a multiple of 16
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + offb);
     GS *sG = reinterpret_cast<GS *>(smem_raw + offb + 16);
     if (threadIdx.x == 0) s_next = static_cast<long long>(atomicAdd(counter, 1ull));
@@ -255,7 +256,15 @@ inline int degree_cpb(int n, int alt)
 template <class T>
 inline size_t batch_smem_bytes(int n)
 {
-    return 3 * (size_t)batch_slots(n) * ((n | 1) * n * n) * sizeof(T);
+    switch (n) {  // the three line buffers of metric_tile in this mode (lines in thread order)
+    case 2: return metric_smem_bytes<2, batch_slots(2), T, float, false>(0, 0);
+    case 3: return metric_smem_bytes<3, batch_slots(3), T, float, false>(0, 0);
+    case 4: return metric_smem_bytes<4, batch_slots(4), T, float, false>(0, 0);
+    case 5: return metric_smem_bytes<5, batch_slots(5), T, float, false>(0, 0);
+    case 6: return metric_smem_bytes<6, batch_slots(6), T, float, false>(0, 0);
+    case 7: return metric_smem_bytes<7, batch_slots(7), T, float, false>(0, 0);
+    default: return metric_smem_bytes<8, batch_slots(8), T, float, false>(0, 0);
+    }
 }
 
 // per-unit entry points (cw_batch_df.cu: double-float on FP64 data; cw_batch_f32.cu: FP32)
