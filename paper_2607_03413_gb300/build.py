@@ -56,7 +56,7 @@ def build(force=False, verbose=False, jobs=None):
     with cf.ThreadPoolExecutor(jobs) as ex:
         objs = [o for o, log in ex.map(compile_one, srcs)]
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")

@@ -22,6 +22,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "cw_internal.h"
@@ -263,43 +264,88 @@ static void free_hier(MgHier *h)
     delete h;
 }
 
+// f(i) for i in [0, n) on up to 16 host threads (contiguous chunks)
+template <class F>
+static void host_parallel_for(int n, F f)
+{
+    const int nt = std::max(1, std::min<int>({16, (int)std::thread::hardware_concurrency(), n / 8}));
+    if (nt == 1) {
+        for (int i = 0; i < n; ++i) f(i);
+        return;
+    }
+    std::atomic<int> next{0};
+    auto work = [&]() {
+        for (int i; (i = next.fetch_add(1)) < n;) f(i);
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(work);
+    work();
+    for (auto &t : th) t.join();
+}
+
 // In-place inverse of a symmetric positive definite row-major n x n matrix through its Cholesky
-// factor A = L L^T: L^-1 by forward substitution, then A^-1 = L^-T L^-1. Returns false if a pivot is
+// factor A = L L^T (blocked by columns: each panel of kNb columns is factored, then the trailing
+// lower triangle is updated row by row on the host threads), then W^T = L^-T by forward substitution
+// of the columns of L^-1 (independent, on the threads; stored as rows, so every inner loop reads
+// memory contiguously) and A^-1 = W^T W as dot products of rows of W^T. Returns false if a pivot is
 // not positive.
 static bool spd_inverse(std::vector<double> &A, int n)
 {
-    std::vector<double> Lm(A);  // lower triangle holds L
-    for (int j = 0; j < n; ++j) {
-        double d = Lm[(size_t)j * n + j];
-        for (int k = 0; k < j; ++k) d -= Lm[(size_t)j * n + k] * Lm[(size_t)j * n + k];
-        if (!(d > 0.0)) return false;
-        d = std::sqrt(d);
-        Lm[(size_t)j * n + j] = d;
-        for (int i = j + 1; i < n; ++i) {
-            double s = Lm[(size_t)i * n + j];
-            const double *li = &Lm[(size_t)i * n], *lj = &Lm[(size_t)j * n];
-            for (int k = 0; k < j; ++k) s -= li[k] * lj[k];
-            Lm[(size_t)i * n + j] = s / d;
+    constexpr int kNb = 48;
+    std::vector<double> Lm(A);  // lower triangle: A, then L
+    auto row = [&](int i) { return &Lm[(size_t)i * n]; };
+    for (int kb = 0; kb < n; kb += kNb) {
+        const int ke = std::min(n, kb + kNb);
+        // panel: columns kb..ke-1 (earlier panels are already subtracted from them)
+        for (int j = kb; j < ke; ++j) {
+            double *lj = row(j);
+            double d = lj[j];
+            for (int k = kb; k < j; ++k) d -= lj[k] * lj[k];
+            if (!(d > 0.0)) return false;
+            d = std::sqrt(d);
+            lj[j] = d;
+            for (int i = j + 1; i < n; ++i) {
+                double *li = row(i);
+                double s = li[j];
+                for (int k = kb; k < j; ++k) s -= li[k] * lj[k];
+                li[j] = s / d;
+            }
         }
+        // trailing update: A[i][j] -= sum_{k in panel} L[i][k] L[j][k] for ke <= j <= i
+        host_parallel_for(n - ke, [&](int r) {
+            const int i = ke + r;
+            double *li = row(i);
+            for (int j = ke; j <= i; ++j) {
+                const double *lj = row(j);
+                double s = 0.0;
+                for (int k = kb; k < ke; ++k) s += li[k] * lj[k];
+                li[j] -= s;
+            }
+        });
     }
-    // W = L^-1 (lower triangular), row by row
-    std::vector<double> W((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i) {
-        W[(size_t)i * n + i] = 1.0 / Lm[(size_t)i * n + i];
-        for (int j = 0; j < i; ++j) {
-            double s = 0.0;
-            for (int k = j; k < i; ++k) s += Lm[(size_t)i * n + k] * W[(size_t)k * n + j];
-            W[(size_t)i * n + j] = -s / Lm[(size_t)i * n + i];
+    // Wt row j = column j of L^-1: solve L x = e_j (x_i = 0 for i < j)
+    std::vector<double> Wt((size_t)n * n, 0.0);
+    host_parallel_for(n, [&](int j) {
+        double *x = &Wt[(size_t)j * n];
+        for (int i = j; i < n; ++i) {
+            const double *li = row(i);
+            double s = (i == j) ? 1.0 : 0.0;
+            for (int k = j; k < i; ++k) s -= li[k] * x[k];
+            x[i] = s / li[i];
         }
-    }
-    // A^-1 = W^T W: (A^-1)_ij = sum_{k >= max(i,j)} W_ki W_kj
-    for (int i = 0; i < n; ++i)
+    });
+    // (A^-1)_ij = sum_{k >= max(i, j)} W_ki W_kj = <Wt row i, Wt row j> over k >= i (j <= i)
+    host_parallel_for(n, [&](int i) {
+        const double *wi = &Wt[(size_t)i * n];
         for (int j = 0; j <= i; ++j) {
+            const double *wj = &Wt[(size_t)j * n];
             double s = 0.0;
-            for (int k = i; k < n; ++k) s += W[(size_t)k * n + i] * W[(size_t)k * n + j];
+            for (int k = i; k < n; ++k) s += wi[k] * wj[k];
             A[(size_t)i * n + j] = s;
-            A[(size_t)j * n + i] = s;
         }
+    });
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < i; ++j) A[(size_t)j * n + i] = A[(size_t)i * n + j];
     return true;
 }
 
