@@ -67,10 +67,9 @@ def peaks():
 # dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture per variant of a 40^3-cell case
 # (64,000 cells), to be scaled by the cell count of a launch. Variants not listed report null.
 DF64_KM_P4_TRAFFIC_PER_CELL = {
-    (8, 0): (512.132864e6 + 55.399936e6) / 64000,
-    (8, 1): (512.126464e6 + 55.275008e6) / 64000,
-    (8, 2): (512.075008e6 + 55.760128e6) / 64000,
-    (4, 2): (512.066560e6 + 55.559424e6) / 64000,
+    (8, 0): (512.066560e6 + 55.982592e6) / 64000,
+    (8, 2): (512.073984e6 + 55.491072e6) / 64000,
+    (4, 2): (512.065792e6 + 55.499776e6) / 64000,
 }
 
 # FP32 issue-rate roofline for double-float arithmetic: 152 SMs x 128 FP32 lanes x 2.07 GHz,
