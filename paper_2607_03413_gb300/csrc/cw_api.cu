@@ -1300,7 +1300,10 @@ cw_status cw_op_autotune(cw_op oh, const void *x, void *y, int reps, void *strea
 extern "C" {
 
 // Apply with host input and output. The cells are split into slabs of whole z-layers: the
-// host-to-device copy of slab k overlaps the work of slab k-1. For CW_APPLY_LOCAL slab k is copied
+// host-to-device copy of slab k overlaps the work of slab k-1. The nominal slab has P = nz / 16
+// layers (rounded up); the first and the last slabs ramp through 1, 2, 4, ... < P layers, so that the
+// pipeline starts on a small copy and ends on a small apply and copy (with equal slabs the link ran
+// one direction only for about one slab time at each end). For CW_APPLY_LOCAL slab k is copied
 // back as soon as its apply is done. For CW_APPLY_ASSEMBLE each slab runs its apply, its x and y DSS
 // passes and the z pass of its interior interfaces, then the z pass of the interface with slab k-1;
 // the DSS cascade couples slabs only through that interface, so slab k-1 is then final and its
@@ -1329,8 +1332,27 @@ cw_status cw_apply_host(cw_op oh, const void *x_host, void *y_host, int flags, v
     for (int i = 0; i < 3; ++i) CW_CUDA_TRY(cudaStreamWaitEvent(op->h_st[i], op->h_done, 0));
     const Mesh &m = *op->mesh;
     const int64_t plane = (int64_t)m.nx * m.ny;  // cells per z-layer
-    const int planes = std::max(1, (m.nz + Op::kMaxSlabs - 1) / Op::kMaxSlabs);  // at most kMaxSlabs slabs
-    const int nslab = (m.nz + planes - 1) / planes;
+    // slab plan: first z-layer of every slab, and an end marker
+    std::vector<int> zs;
+    {
+        const int P = std::max(1, (m.nz + Op::kNominalSlabs - 1) / Op::kNominalSlabs);
+        std::vector<int> ramp;
+        int rs = 0;
+        for (int r = 1; r < P; r *= 2) ramp.push_back(r), rs += r;
+        if (2 * rs + P > m.nz) ramp.clear(), rs = 0;  // too few layers to ramp
+        int z = 0;
+        for (int r : ramp) zs.push_back(z), z += r;
+        const int zend = m.nz - rs;
+        for (; z < zend; z += P) zs.push_back(z);
+        z = zend;
+        for (auto it = ramp.rbegin(); it != ramp.rend(); ++it) zs.push_back(z), z += *it;
+        if ((int)zs.size() > Op::kMaxSlabs) {  // cannot happen for kMaxSlabs >= 16 + 2 log2(P); keep it safe
+            zs.clear();
+            for (z = 0; z < m.nz; z += P) zs.push_back(z);
+        }
+        zs.push_back(m.nz);
+    }
+    const int nslab = (int)zs.size() - 1;
     const size_t gbytes_per_cell = op->geo_bytes / op->E;
     unsigned char *dx = static_cast<unsigned char *>(op->h_dx), *dy = static_cast<unsigned char *>(op->h_dy);
     const unsigned char *hx = static_cast<const unsigned char *>(x_host);
@@ -1357,7 +1379,7 @@ cw_status cw_apply_host(cw_op oh, const void *x_host, void *y_host, int flags, v
         o.d_geo = static_cast<unsigned char *>(op->d_geo) + z0 * plane * gbytes_per_cell;
     };
     auto slab_bytes = [&](int k, size_t &off, size_t &bytes) {
-        const int64_t z0 = (int64_t)k * planes, nz = std::min<int64_t>(planes, m.nz - z0);
+        const int64_t z0 = zs[k], nz = zs[k + 1] - zs[k];
         off = (size_t)(z0 * plane * n3) * es;
         bytes = (size_t)(nz * plane * n3) * es;
     };
@@ -1365,7 +1387,7 @@ cw_status cw_apply_host(cw_op oh, const void *x_host, void *y_host, int flags, v
     for (int k = 0; k < nslab; ++k) {
         size_t off, bytes;
         slab_bytes(k, off, bytes);
-        const int z0 = k * planes, nzk = std::min(planes, m.nz - z0);
+        const int z0 = zs[k], nzk = zs[k + 1] - zs[k];
         CW_CUDA_TRY(cudaMemcpyAsync(dx + off, hx + off, bytes, cudaMemcpyHostToDevice, sin));
         CW_CUDA_TRY(cudaEventRecord(op->h_ev[0][k], sin));
         CW_CUDA_TRY(cudaStreamWaitEvent(scomp, op->h_ev[0][k], 0));

@@ -54,7 +54,8 @@ struct Op {
     // host-buffer apply (cw_apply_host): device staging vectors, streams and events, lazily
     void *h_dx = nullptr, *h_dy = nullptr;
     cudaStream_t h_st[3] = {nullptr, nullptr, nullptr};
-    static constexpr int kMaxSlabs = 16;  // 32 measured slower (more, smaller copies)
+    static constexpr int kNominalSlabs = 16;  // equal slabs: 32 measured slower than 16
+    static constexpr int kMaxSlabs = 32;      // with the ramped first and last slabs
     cudaEvent_t h_ev[2][kMaxSlabs] = {};
     cudaEvent_t h_done = nullptr;
     unsigned *d_status = nullptr;  // device status word: kDevStatusTimeout when a bounded wait expired
