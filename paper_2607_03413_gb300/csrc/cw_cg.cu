@@ -23,6 +23,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 #include <string>
 #include <type_traits>
 
@@ -544,7 +546,8 @@ static cudaError_t launch_precond_yz(const Op &op, const V *w, V *r, V *zo, cons
     const uint32_t nl = static_cast<uint32_t>(op.L / op.n);
     const FastDiv fx = FastDiv::make(m.nx), fy = FastDiv::make(m.ny);
 #define CW_PYZ(NN)                                                                                     \
-    k_precond_yz_fin<NN, V><<<kRedBlocks, kRedThreads, 0, s>>>(w, r, zo, dinv, nl, m.nx, m.ny, m.nz, fx, fy, \
+    k_precond_yz_fin<NN, V><<<res_grid(k_precond_yz_fin<NN, V>, kRedThreads), kRedThreads, 0, s>>>( \
+        w, r, zo, dinv, nl, m.nx, m.ny, m.nz, fx, fy, \
                                                               part, scal, flags, stage)
     switch (op.n) {
     case 2: CW_PYZ(2); break;
@@ -562,6 +565,33 @@ static cudaError_t launch_precond_yz(const Op &op, const V *w, V *r, V *zo, cons
 
 // --------------------------------------------------------------------------- host side ----
 static unsigned vec_grid() { return kRedBlocks; }
+
+// Grid of a grid-stride kernel whose reduction (if any) takes its partial count from gridDim.x: whole
+// waves of the blocks that are resident at once on this device, at most kRedBlocks. A fixed grid that
+// is not a multiple of that runs its last blocks as a partial wave at a fraction of the occupancy (40
+// registers leave 6 of 8 blocks of 256 threads per SM resident: 912 of 1216 blocks, then 304).
+template <class K>
+static unsigned res_grid(K kernel, int threads)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, unsigned> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return kRedBlocks;
+    const std::pair<const void *, int> key(reinterpret_cast<const void *>(kernel), dev);
+    std::lock_guard<std::mutex> g(mu);
+    const auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return kRedBlocks;
+    }
+    const int wave = per_sm * sms;
+    const unsigned grid = (unsigned)(wave >= kRedBlocks ? kRedBlocks : wave * (kRedBlocks / wave));
+    cache[key] = grid;
+    return grid;
+}
 
 // CWFEM_DEBUG=1 in the environment prints the outer refinement loop of cw_cg_solve to stderr
 static bool debug_trace()
@@ -665,7 +695,7 @@ static cudaError_t apply_pq(const Op &aop, int ak, const V *p, V *q, CgScratch &
         k_sum_fin<<<g, kRedThreads, 0, s>>>(c.dotpart, nb, c.partials, c.scal, c.flags, STAGE_PQ);
     } else {
         if ((e = apply_by_kind(aop, ak, p, q, s)) != cudaSuccess) return e;
-        k_dot_fin<V><<<vec_grid(), kRedThreads, 0, s>>>(p, q, aop.L, c.partials, c.scal, c.flags, STAGE_PQ);
+        k_dot_fin<V><<<res_grid(k_dot_fin<V>, kRedThreads), kRedThreads, 0, s>>>(p, q, aop.L, c.partials, c.scal, c.flags, STAGE_PQ);
     }
     return cudaGetLastError();
 }
@@ -688,15 +718,15 @@ static cudaError_t cg_iteration(const Op &aop, int ak, CgLevel &lv, U *u, CgScra
             if (e != cudaSuccess) return e;
             e = launch_precond_yz<V>(aop, z, r, q, dinv, c.partials, c.scal, c.flags, STAGE_RHO, s);
             if (e != cudaSuccess) return e;
-            k_pupdate_u<V, U><<<vec_grid(), 256, 0, s>>>(u, p, q, L, c.scal, c.flags);
+            k_pupdate_u<V, U><<<res_grid(k_pupdate_u<V, U>, 256), 256, 0, s>>>(u, p, q, L, c.scal, c.flags);
             return cudaGetLastError();
         }
     }
     // z = S (r - alpha q): the residual update rides on the DSS's first pass
     if ((e = dss_from_axpy(aop, r, q, c.scal + S_ALPHA, c.flags + F_ACTIVE, z, s)) != cudaSuccess) return e;
-    k_precond_fin<V><<<vec_grid(), kRedThreads, 0, s>>>(r, z, dinv, L, c.kappa, c.partials, c.scal, c.flags,
+    k_precond_fin<V><<<res_grid(k_precond_fin<V>, kRedThreads), kRedThreads, 0, s>>>(r, z, dinv, L, c.kappa, c.partials, c.scal, c.flags,
                                                         STAGE_RHO);
-    k_pupdate_u<V, U><<<vec_grid(), 256, 0, s>>>(u, p, z, L, c.scal, c.flags);
+    k_pupdate_u<V, U><<<res_grid(k_pupdate_u<V, U>, 256), 256, 0, s>>>(u, p, z, L, c.scal, c.flags);
     return cudaGetLastError();
 }
 
@@ -721,7 +751,7 @@ static cw_status cg_run(const Op &aop, int ak, CgLevel &lv, U *u, CgScratch &c, 
     CW_CUDA_TRY(cudaMemcpyAsync(c.flags + F_MAXIT, &c.h_flags[1], sizeof(int), cudaMemcpyHostToDevice, s));
     // z = D^-1 S r, r <- S_bar r, rho = <r, z>, res0 = <m S r, r>, p = z
     CW_CUDA_TRY(dss_from(aop, r, z, CW_DSS_SUM, s));
-    k_precond_fin<V><<<vec_grid(), kRedThreads, 0, s>>>(r, z, dinv, L, c.kappa, c.partials, c.scal, c.flags,
+    k_precond_fin<V><<<res_grid(k_precond_fin<V>, kRedThreads), kRedThreads, 0, s>>>(r, z, dinv, L, c.kappa, c.partials, c.scal, c.flags,
                                                         STAGE_INIT);
     if (!keep_p) CW_CUDA_TRY(cudaMemcpyAsync(p, z, L * sizeof(V), cudaMemcpyDeviceToDevice, s));
     CW_CUDA_TRY(cudaGetLastError());
@@ -827,18 +857,18 @@ static cudaError_t mgcg_iteration(const Op &aop, MgHier &h, CgLevel &lv, double 
     cudaError_t e;
     if ((e = apply_pq<double>(aop, AK_DF, p, q, c, s)) != cudaSuccess) return e;
     if ((e = dss_from_axpy(aop, r, q, c.scal + S_ALPHA, c.flags + F_ACTIVE, w, s)) != cudaSuccess) return e;
-    if (f32) k_mg_average<true><<<vec_grid(), 256, 0, s>>>(r, w, c.kappa, c.r32, L, c.flags);
-    else k_mg_average<false><<<vec_grid(), 256, 0, s>>>(r, w, c.kappa, nullptr, L, c.flags);
+    if (f32) k_mg_average<true><<<res_grid(k_mg_average<true>, 256), 256, 0, s>>>(r, w, c.kappa, c.r32, L, c.flags);
+    else k_mg_average<false><<<res_grid(k_mg_average<false>, 256), 256, 0, s>>>(r, w, c.kappa, nullptr, L, c.flags);
     if ((e = mg_vcycle_zero(h, f32 ? static_cast<void *>(c.r32) : r, f32 ? static_cast<void *>(c.z32) : z, s)) !=
         cudaSuccess)
         return e;
     if (f32)
-        k_mg_dots_fin<true><<<vec_grid(), kRedThreads, 0, s>>>(r, z, c.z32, w, dinv, L, c.partials, c.scal, c.flags,
+        k_mg_dots_fin<true><<<res_grid(k_mg_dots_fin<true>, kRedThreads), kRedThreads, 0, s>>>(r, z, c.z32, w, dinv, L, c.partials, c.scal, c.flags,
                                                                STAGE_RHO);
     else
-        k_mg_dots_fin<false><<<vec_grid(), kRedThreads, 0, s>>>(r, z, nullptr, w, dinv, L, c.partials, c.scal,
+        k_mg_dots_fin<false><<<res_grid(k_mg_dots_fin<false>, kRedThreads), kRedThreads, 0, s>>>(r, z, nullptr, w, dinv, L, c.partials, c.scal,
                                                                 c.flags, STAGE_RHO);
-    k_pupdate_u<double, double><<<vec_grid(), 256, 0, s>>>(d, p, z, L, c.scal, c.flags);
+    k_pupdate_u<double, double><<<res_grid(k_pupdate_u<double, double>, 256), 256, 0, s>>>(d, p, z, L, c.scal, c.flags);
     return cudaGetLastError();
 }
 
@@ -862,14 +892,14 @@ static cw_status mgcg_run(const Op &aop, MgHier &h, CgLevel &lv, double *d, CgSc
     CW_CUDA_TRY(cudaMemcpyAsync(c.flags + F_MAXIT, &c.h_flags[1], sizeof(int), cudaMemcpyHostToDevice, s));
     // w = S r; r <- S_bar r; z = MG(r); rho = <r, z>, res0 = <m S r, r>; p = z
     CW_CUDA_TRY(dss_from(aop, r, w, CW_DSS_SUM, s));
-    if (f32) k_mg_average<true><<<vec_grid(), 256, 0, s>>>(r, w, c.kappa, c.r32, L, c.flags);
-    else k_mg_average<false><<<vec_grid(), 256, 0, s>>>(r, w, c.kappa, nullptr, L, c.flags);
+    if (f32) k_mg_average<true><<<res_grid(k_mg_average<true>, 256), 256, 0, s>>>(r, w, c.kappa, c.r32, L, c.flags);
+    else k_mg_average<false><<<res_grid(k_mg_average<false>, 256), 256, 0, s>>>(r, w, c.kappa, nullptr, L, c.flags);
     CW_CUDA_TRY(mg_vcycle_zero(h, f32 ? static_cast<void *>(c.r32) : r, f32 ? static_cast<void *>(c.z32) : z, s));
     if (f32)
-        k_mg_dots_fin<true><<<vec_grid(), kRedThreads, 0, s>>>(r, z, c.z32, w, dinv, L, c.partials, c.scal, c.flags,
+        k_mg_dots_fin<true><<<res_grid(k_mg_dots_fin<true>, kRedThreads), kRedThreads, 0, s>>>(r, z, c.z32, w, dinv, L, c.partials, c.scal, c.flags,
                                                                STAGE_INIT);
     else
-        k_mg_dots_fin<false><<<vec_grid(), kRedThreads, 0, s>>>(r, z, nullptr, w, dinv, L, c.partials, c.scal,
+        k_mg_dots_fin<false><<<res_grid(k_mg_dots_fin<false>, kRedThreads), kRedThreads, 0, s>>>(r, z, nullptr, w, dinv, L, c.partials, c.scal,
                                                                 c.flags, STAGE_INIT);
     CW_CUDA_TRY(cudaMemcpyAsync(p, z, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CW_CUDA_TRY(cudaGetLastError());
