@@ -228,14 +228,17 @@ def test_autotune_keeps_a_valid_variant(cw, orc):
     assert rel_err(to_np(y2), ref) <= TOL64
 
 
+@pytest.mark.parametrize("nz", [1, 19, 40])
 @pytest.mark.parametrize("geom", [1, 2], ids=["stored", "recompute"])
 @pytest.mark.parametrize("assemble", [False, True])
 @pytest.mark.parametrize("prec", [0, 2], ids=["df64", "f32"])
-def test_apply_host_buffers(cw, orc, prec, assemble, geom):
-    """cw_apply_host (host input and output, chunked and pipelined) equals cw_apply on device data."""
+def test_apply_host_buffers(cw, orc, prec, assemble, geom, nz):
+    """cw_apply_host (host input and output, chunked and pipelined) equals cw_apply on device data.
+    z-slabs by layer count: 1 -> one slab; 19 -> 1, 2 x 8, 1, 1 (nominal 2 layers, ramp 1); 40 -> 1, 2,
+    3 x 11, 1, 2, 1 (nominal 3, ramp 1, 2; a ragged middle slab)."""
     import torch
     p = 3
-    mesh = synth.box_mesh(5, 4, 19, perturb=0.2)  # 19 z-layers: slabs of 2 layers and a ragged last one
+    mesh = synth.box_mesh(5, 4, nz, perturb=0.2)
     M = cw.Mesh.from_synth(mesh)
     op = cw.Operator(M, p, 3, geom, prec)
     x = op.gather(torch.from_numpy(synth.global_vector(mesh, p, seed=3)).cuda())
