@@ -425,8 +425,10 @@ static cudaError_t mb_apply_local(const MBlock &mb, const void *x, void *y, cuda
 
 // ------------------------------------------------------------------ Jacobi-PCG (FP64) ----
 // Primal-dual CG of Sec. 4.4 on the concatenated vector, preconditioner z = D^-1 S r with zeros of the
-// inverse diagonal on the domain boundary; dots with double-float accumulation, one partial per CTA
-// summed in a fixed order.
+// inverse diagonal on the domain boundary; FP64 dots, one partial per CTA, the partials summed in a
+// fixed order by one CTA (so every run gives the same bits). Per iteration: q = A p block by block,
+// <p, q>, one pass for u += alpha p, r -= alpha q and z = r, the DSS of z, one pass for the two dots
+// around z <- D^-1 z, and the direction update.
 constexpr int kMbBlocks = 1216, kMbThreads = 256;
 
 __device__ __forceinline__ double mb_block_sum(double v, double *sh)
@@ -454,21 +456,57 @@ __global__ void __launch_bounds__(kMbThreads) mb_dot_kernel(const double *__rest
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-__global__ void mb_sum_kernel(const double *__restrict__ part, int nb, double *__restrict__ out)
+// out[k] = sum of part[k * nb .. k * nb + nb) for k < nsum (one CTA of kMbThreads: strided sums in a
+// fixed order, then the fixed tree of mb_block_sum)
+__global__ void __launch_bounds__(kMbThreads) mb_sum_kernel(const double *__restrict__ part, int nb, int nsum,
+                                                            double *__restrict__ out)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double s = 0.0;
-    for (int i = 0; i < nb; ++i) s += part[i];
-    *out = s;
+    __shared__ double sh[kMbThreads / 32];
+    for (int k = 0; k < nsum; ++k) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[(int64_t)k * nb + i];
+        s = mb_block_sum(s, sh);
+        if (threadIdx.x == 0) out[k] = s;
+    }
 }
 
-// x += alpha y with alpha = num / den (device scalars), sign +1 or -1
-__global__ void mb_axpy_kernel(double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ num,
-                               const double *__restrict__ den, double sign, int64_t n)
+// alpha = num / den: u += alpha p, r -= alpha q, z = r (the DSS input)
+__global__ void __launch_bounds__(kMbThreads) mb_update_kernel(double *__restrict__ u, double *__restrict__ r,
+                                                               double *__restrict__ z, const double *__restrict__ p,
+                                                               const double *__restrict__ q,
+                                                               const double *__restrict__ num,
+                                                               const double *__restrict__ den, int64_t n)
 {
-    const double a = sign * (*num) / (*den);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = fma(a, y[i], x[i]);
+    const double a = (*num) / (*den);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        u[i] = fma(a, p[i], u[i]);
+        const double ri = fma(-a, q[i], r[i]);
+        r[i] = ri;
+        z[i] = ri;
+    }
+}
+
+// z holds S r: part[block] = <m z, r> (m: entries off the domain boundary, dinv != 0), then
+// z <- D^-1 z and part[nb + block] = <r, z>
+__global__ void __launch_bounds__(kMbThreads) mb_precond_kernel(double *__restrict__ z, const double *__restrict__ r,
+                                                                const double *__restrict__ dinv, int64_t n,
+                                                                double *__restrict__ part)
+{
+    __shared__ double sh[kMbThreads / 32];
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double di = dinv[i], ri = r[i], zi = z[i];
+        if (di != 0.0) s1 = fma(zi, ri, s1);
+        const double zn = di * zi;
+        z[i] = zn;
+        s2 = fma(ri, zn, s2);
+    }
+    s1 = mb_block_sum(s1, sh);
+    s2 = mb_block_sum(s2, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = s1;
+        part[gridDim.x + blockIdx.x] = s2;
+    }
 }
 
 // p = z + (rho_new / rho_old) p
@@ -478,12 +516,6 @@ __global__ void mb_pupdate_kernel(double *__restrict__ p, const double *__restri
     const double beta = (*num) / (*den);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = fma(beta, p[i], z[i]);
-}
-
-__global__ void mb_mul_kernel(double *__restrict__ z, const double *__restrict__ d, int64_t n)
-{
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        z[i] *= d[i];
 }
 
 __global__ void mb_dinv_kernel(const double *__restrict__ d, const uint8_t *__restrict__ dir, double *__restrict__ dinv,
@@ -626,9 +658,9 @@ cw_status cw_mblock_cg_solve(cw_mblock h, const double *b, double *u, double rto
     const int64_t L = mb->L;
     if (!mb->r) {
         for (double **pp : {&mb->r, &mb->pv, &mb->q, &mb->z, &mb->dinv}) CW_CUDA_TRY(cudaMalloc(pp, L * sizeof(double)));
-        CW_CUDA_TRY(cudaMalloc(&mb->part, kMbBlocks * sizeof(double)));
+        CW_CUDA_TRY(cudaMalloc(&mb->part, 2 * kMbBlocks * sizeof(double)));
         CW_CUDA_TRY(cudaMalloc(&mb->scal, 8 * sizeof(double)));
-        mb->bytes += 5 * L * (int64_t)sizeof(double) + (kMbBlocks + 8) * (int64_t)sizeof(double);
+        mb->bytes += 5 * L * (int64_t)sizeof(double) + (2 * kMbBlocks + 8) * (int64_t)sizeof(double);
         cw_status st = cw_mblock_diagonal(h, mb->q, stream);
         if (st != CW_OK) return st;
         mb_dinv_kernel<<<kMbBlocks, kMbThreads, 0, s>>>(mb->q, mb->dirichlet, mb->dinv, L);
@@ -650,10 +682,9 @@ cw_status cw_mblock_cg_solve(cw_mblock h, const double *b, double *u, double rto
     } ev{e0, e1};
     CW_CUDA_TRY(cudaEventRecord(e0, s));
     double *r = mb->r, *p = mb->pv, *q = mb->q, *z = mb->z, *sc = mb->scal;
-    // scalars: 0 rho, 1 <p, q>, 2 rho_new, 3 residual <m S r, r>, 4 res0
-    auto dot = [&](const double *a, const double *bb, const uint8_t *m, double *outp) {
-        mb_dot_kernel<<<kMbBlocks, kMbThreads, 0, s>>>(a, bb, m, L, mb->part);
-        mb_sum_kernel<<<1, 32, 0, s>>>(mb->part, kMbBlocks, outp);
+    auto dot = [&](const double *a, const double *bb, double *outp) {
+        mb_dot_kernel<<<kMbBlocks, kMbThreads, 0, s>>>(a, bb, nullptr, L, mb->part);
+        mb_sum_kernel<<<1, kMbThreads, 0, s>>>(mb->part, kMbBlocks, 1, outp);
     };
     auto host = [&](int i, double *v) -> cw_status {
         CW_CUDA_TRY(cudaMemcpyAsync(v, sc + i, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -662,17 +693,19 @@ cw_status cw_mblock_cg_solve(cw_mblock h, const double *b, double *u, double rto
     };
     CW_CUDA_TRY(cudaMemsetAsync(u, 0, L * sizeof(double), s));
     CW_CUDA_TRY(cudaMemcpyAsync(r, b, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    // z = S r; res = <m z, r> (m: not Dirichlet) = ||m G^T r||^2; z <- D^-1 z; rho = <r, z>
-    auto precond = [&](int res_slot, int rho_slot) -> cudaError_t {
-        cudaError_t e = cudaMemcpyAsync(z, r, L * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    CW_CUDA_TRY(cudaMemcpyAsync(z, b, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    // z (= r) <- S z; res = <m z, r> (m: not Dirichlet) = ||m G^T r||^2; z <- D^-1 z; rho = <r, z>
+    // (res into sc[res_slot], rho into sc[res_slot + 1])
+    auto precond = [&](int res_slot) -> cudaError_t {
+        cudaError_t e = mb_dss(*mb, z, CW_DSS_SUM, s);
         if (e != cudaSuccess) return e;
-        if ((e = mb_dss(*mb, z, CW_DSS_SUM, s)) != cudaSuccess) return e;
-        dot(z, r, mb->dirichlet, sc + res_slot);
-        mb_mul_kernel<<<kMbBlocks, kMbThreads, 0, s>>>(z, mb->dinv, L);
-        dot(r, z, nullptr, sc + rho_slot);
+        mb_precond_kernel<<<kMbBlocks, kMbThreads, 0, s>>>(z, r, mb->dinv, L, mb->part);
+        mb_sum_kernel<<<1, kMbThreads, 0, s>>>(mb->part, kMbBlocks, 2, sc + res_slot);
         return cudaGetLastError();
     };
-    CW_CUDA_TRY(precond(4, 0));
+    // scalars: 0 rho, 1 <p, q>, 2 res and 3 rho_new of an iteration, 4 res0 (5: rho of the start)
+    CW_CUDA_TRY(precond(4));
+    CW_CUDA_TRY(cudaMemcpyAsync(sc + 0, sc + 5, sizeof(double), cudaMemcpyDeviceToDevice, s));
     CW_CUDA_TRY(cudaMemcpyAsync(p, z, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
     double res0 = 0.0, res = 0.0;
     cw_status st;
@@ -686,15 +719,14 @@ cw_status cw_mblock_cg_solve(cw_mblock h, const double *b, double *u, double rto
             break;
         }
         CW_CUDA_TRY(mb_apply_local(*mb, p, q, s));
-        dot(p, q, nullptr, sc + 1);
-        mb_axpy_kernel<<<kMbBlocks, kMbThreads, 0, s>>>(u, p, sc + 0, sc + 1, 1.0, L);
-        mb_axpy_kernel<<<kMbBlocks, kMbThreads, 0, s>>>(r, q, sc + 0, sc + 1, -1.0, L);
-        CW_CUDA_TRY(precond(3, 2));
-        mb_pupdate_kernel<<<kMbBlocks, kMbThreads, 0, s>>>(p, z, sc + 2, sc + 0, L);
-        CW_CUDA_TRY(cudaMemcpyAsync(sc + 0, sc + 2, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        dot(p, q, sc + 1);
+        mb_update_kernel<<<kMbBlocks, kMbThreads, 0, s>>>(u, r, z, p, q, sc + 0, sc + 1, L);
+        CW_CUDA_TRY(precond(2));
+        mb_pupdate_kernel<<<kMbBlocks, kMbThreads, 0, s>>>(p, z, sc + 3, sc + 0, L);
+        CW_CUDA_TRY(cudaMemcpyAsync(sc + 0, sc + 3, sizeof(double), cudaMemcpyDeviceToDevice, s));
         CW_CUDA_TRY(cudaGetLastError());
         ++it;
-        if ((st = host(3, &res)) != CW_OK) return st;
+        if ((st = host(2, &res)) != CW_OK) return st;
         if (!std::isfinite(res)) {
             result = fail(CW_ERR_BREAKDOWN, "cw_mblock_cg_solve: non-finite residual");
             break;
