@@ -193,7 +193,9 @@ int64_t cw_op_device_bytes(cw_op op);
  * tile by TMA there (there is no metric tile).
  */
 cw_status cw_op_set_variant(cw_op op, int cells_per_cta, int stage);
-/* Current variant; choices2 (may be NULL) receives the two cells-per-CTA choices of the degree. */
+/* Current variant; choices2 (may be NULL) receives the two cells-per-CTA choices of the degree and
+ * arithmetic (the default and half of it; the FP32-arithmetic precisions take larger tiles than the
+ * FP64 ones at p = 1, 2, 5, 6). */
 cw_status cw_op_get_variant(cw_op op, int *cells_per_cta, int *stage, int *choices2);
 /*
  * Autotuner: times every variant of the LOCAL apply on the caller's x, y (device, op vector

@@ -1205,7 +1205,7 @@ cw_status cw_op_set_variant(cw_op oh, int cells_per_cta, int stage)
     Op *op = reinterpret_cast<Op *>(oh);
     if (!op) return fail(CW_ERR_ARG, "cw_op_set_variant: NULL handle");
     int ch[2];
-    cpb_choices(op->p, ch);
+    cpb_choices(op->p, op->prec, ch);
     if (cells_per_cta != 0 && cells_per_cta != ch[0] && cells_per_cta != ch[1])
         return fail(CW_ERR_ARG, "cw_op_set_variant: cells_per_cta must be 0 or one of cw_op_get_variant's choices");
     if (stage < 0 || stage > 2) return fail(CW_ERR_ARG, "cw_op_set_variant: stage must be 0, 1 or 2");
@@ -1224,7 +1224,7 @@ cw_status cw_op_get_variant(cw_op oh, int *cells_per_cta, int *stage, int *choic
     Op *op = reinterpret_cast<Op *>(oh);
     if (!op) return fail(CW_ERR_ARG, "cw_op_get_variant: NULL handle");
     int ch[2];
-    cpb_choices(op->p, ch);
+    cpb_choices(op->p, op->prec, ch);
     if (cells_per_cta) *cells_per_cta = op->cpb == 0 ? ch[0] : op->cpb;
     if (stage) *stage = op->stage;
     if (choices2) {
@@ -1247,7 +1247,7 @@ cw_status cw_op_autotune(cw_op oh, const void *x, void *y, int reps, void *strea
         return CW_OK;
     }
     int ch[2];
-    cpb_choices(op->p, ch);
+    cpb_choices(op->p, op->prec, ch);
     cudaEvent_t e0, e1;
     CW_CUDA_TRY(cudaEventCreate(&e0));
     if (const cudaError_t ee = cudaEventCreate(&e1); ee != cudaSuccess) {

@@ -254,14 +254,14 @@ struct TileGeom {
 __host__ __device__ constexpr TileGeom tile_geom(int N, int CPB, int ESZ, bool allow_remap)
 {
     if (allow_remap && ESZ == 4) {
-        switch (N * 100 + CPB) {
-        case 216: case 232: return {2, 6, 12, false, true};
-        case 308: case 316: return {3, 10, 41, true, true};
-        case 404: case 408: return {4, 19, 80, true, true};
-        case 504: case 508: return {5, 33, 185, true, true};
-        case 602: case 604: return {6, 37, 228, true, true};
-        case 704: return {7, 73, 529, true, true};
-        case 802: return {8, 66, 528, true, true};
+        switch (N * 1000 + CPB) {
+        case 2016: case 2032: case 2064: return {2, 6, 12, false, true};
+        case 3008: case 3016: case 3032: return {3, 10, 41, true, true};
+        case 4004: case 4008: return {4, 19, 80, true, true};
+        case 5004: case 5008: return {5, 33, 185, true, true};
+        case 6002: case 6004: case 6008: return {6, 37, 228, true, true};
+        case 7004: case 7008: return {7, 73, 529, true, true};
+        case 8002: return {8, 66, 528, true, true};
         default: break;
         }
     }

@@ -78,7 +78,7 @@ static cw_status batch_rebuild(Batch &b)
         P.n = o.n;
         P.kind = o.kind;
         P.nrhs = b.nrhs[i];
-        P.cpt = b.mode == CW_BATCH_SINGLE ? batch_cpt(o.n, b.half[o.n]) : degree_cpb(o.n, b.variant[o.n] & 1);
+        P.cpt = b.mode == CW_BATCH_SINGLE ? batch_cpt(o.n, b.half[o.n]) : degree_cpb(o.n, b.variant[o.n] & 1, !b.fp64);
         P.ntiles = (o.E + P.cpt - 1) / P.cpt;
         // grouped items with the metric staged once (staging mode 1) carry every right-hand side of
         // their tiles: fewer tiles per item
@@ -118,7 +118,10 @@ static cw_status batch_rebuild(Batch &b)
     return CW_OK;
 }
 
-static cudaError_t batch_enqueue(const Batch &b, cudaStream_t s)
+// only >= 2 (grouped mode): enqueue that degree's kernel alone (the tuner times a degree in isolation:
+// the degrees run concurrently on their own streams, and timing one degree's variants inside the whole
+// batch left its differences below the run-to-run spread of the batch)
+static cudaError_t batch_enqueue(const Batch &b, cudaStream_t s, int only = 0)
 {
     cudaError_t e = cudaMemsetAsync(b.d_counter, 0, 9 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
@@ -127,7 +130,7 @@ static cudaError_t batch_enqueue(const Batch &b, cudaStream_t s)
                       : batch_launch_f32(b.d_probs, (int)b.h_probs.size(), b.nitems, b.d_counter, b.smem, b.grid, s);
     if ((e = cudaEventRecord(b.ev_fork, s)) != cudaSuccess) return e;
     for (int n = 2; n <= 8; ++n) {
-        if (!b.g_count[n]) continue;
+        if (!b.g_count[n] || (only && n != only)) continue;
         const int v = b.variant[n];
         const int kmax = (b.g_kind[n] & 1) ? 3 : 2;  // metric components of the largest kind present
         cudaStream_t gs = b.g_stream[n];
@@ -255,7 +258,7 @@ cw_status cw_batch_get_variant(cw_batch bh, int degree, int *variant, int *cells
     const int n = degree + 1;
     if (variant) *variant = b->mode == CW_BATCH_SINGLE ? b->half[n] : b->variant[n];
     if (cells_per_tile)
-        *cells_per_tile = b->mode == CW_BATCH_SINGLE ? batch_cpt(n, b->half[n]) : degree_cpb(n, b->variant[n] & 1);
+        *cells_per_tile = b->mode == CW_BATCH_SINGLE ? batch_cpt(n, b->half[n]) : degree_cpb(n, b->variant[n] & 1, !b->fp64);
     return CW_OK;
 }
 
@@ -304,7 +307,17 @@ cw_status cw_batch_autotune(cw_batch bh, int reps, void *stream, float *best_ms)
     CW_CUDA_TRY(cudaEventCreate(&ev.e0));
     CW_CUDA_TRY(cudaEventCreate(&ev.e1));
     cudaEvent_t e0 = ev.e0, e1 = ev.e1;
-    float best_all = 0.0f;
+    // time `reps` launches (after one warm-up) of the batch, or of degree `only` alone
+    auto timed = [&](int only, float *ms) -> cudaError_t {
+        cudaError_t e = batch_enqueue(*b, s, only);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = batch_enqueue(*b, s, only);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+        *ms /= reps;
+        return e;
+    };
     for (int n = 2; n <= 8; ++n) {  // coordinate descent over the degrees present
         if (!present[n]) continue;
         float best = 1e30f;
@@ -314,25 +327,20 @@ cw_status cw_batch_autotune(cw_batch bh, int reps, void *stream, float *best_ms)
             *knob = h;
             cw_status st = batch_rebuild(*b);
             if (st != CW_OK) return st;
-            CW_CUDA_TRY(batch_enqueue(*b, s));  // warm-up
-            CW_CUDA_TRY(cudaEventRecord(e0, s));
-            for (int r = 0; r < reps; ++r) CW_CUDA_TRY(batch_enqueue(*b, s));
-            CW_CUDA_TRY(cudaEventRecord(e1, s));
-            CW_CUDA_TRY(cudaEventSynchronize(e1));
             float ms = 0.0f;
-            CW_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            ms /= reps;
+            CW_CUDA_TRY(timed(b->mode == CW_BATCH_GROUPED ? n : 0, &ms));
             if (ms < best) {
                 best = ms;
                 bh_ = h;
             }
         }
         *knob = bh_;
-        best_all = best;
     }
     cw_status st = batch_rebuild(*b);
-    if (best_ms) *best_ms = best_all;
     if (st != CW_OK) return st;
+    float all_ms = 0.0f;
+    CW_CUDA_TRY(timed(0, &all_ms));
+    if (best_ms) *best_ms = all_ms;
     for (Op *o : b->ops)
         if ((st = op_status_take(o, static_cast<cudaStream_t>(stream), "cw_batch_autotune")) != CW_OK) return st;
     return CW_OK;

@@ -246,10 +246,9 @@ cudaError_t batch_degree_launch_f32(int n, int cpb_alt, int stage, const Tables1
                                     int nprob, int64_t nitems, unsigned long long *counter, int kind_max,
                                     cudaStream_t s);
 // cells per CTA of the grouped kernel for degree n (same choices as the per-operator kernel)
-inline int degree_cpb(int n, int alt)
+inline int degree_cpb(int n, int alt, bool f32)
 {
-    static const int d[9] = {0, 0, 32, 16, 8, 8, 4, 4, 2};
-    return alt ? d[n] / 2 : d[n];
+    return alt ? tile_cells(n, f32) / 2 : tile_cells(n, f32);
 }
 
 // shared memory one item of degree n needs (all cell slots of the CTA)

@@ -81,7 +81,7 @@ template <int N>
 static cudaError_t grouped_n(int alt, int stage, const Tables1D &tb, const BatchProb *d_probs, int nprob,
                              int64_t nitems, unsigned long long *counter, int kind_max, cudaStream_t s)
 {
-    constexpr int D = cpb_default<N>(), A = cpb_alt<N>();
+    constexpr int D = cpb_default<N, ArF32>(), A = cpb_alt<N, ArF32>();
     if (alt) return stage == 1 ? grouped<N, A, 1>(tb, d_probs, nprob, nitems, counter, kind_max, s)
                    : stage == 2 ? grouped<N, A, 2>(tb, d_probs, nprob, nitems, counter, kind_max, s)
                                 : grouped<N, A, 0>(tb, d_probs, nprob, nitems, counter, kind_max, s);

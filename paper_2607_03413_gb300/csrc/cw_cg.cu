@@ -619,8 +619,7 @@ static bool apply_dot_ok(const Op &op, int ak)
     if (ak == AK_NATIVE) return false;
     // curved stored metric: the TMA-staged default; recomputed metric: its default (input staged)
     if (op.geom == CW_GEOM_METRIC ? op.stage != 1 : op.geom != CW_GEOM_RECOMPUTE) return false;
-    static const int dflt[9] = {0, 0, 32, 16, 8, 8, 4, 4, 2};  // default cells per CTA by n
-    if (op.cpb != 0 && op.cpb != dflt[op.n]) return false;
+    if (op.cpb != 0 && op.cpb != tile_cells(op.n, prec_f32_arith(op.prec))) return false;  // not the default tile
     return op.prec == CW_PREC_F64 || op.prec == CW_PREC_F32 || op.prec == CW_PREC_F32_BF16G;
 }
 

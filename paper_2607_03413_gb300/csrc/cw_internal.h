@@ -9,6 +9,23 @@
 
 namespace cw {
 
+// Cells per CTA of the curved kernels: the default; the tuner's alternative is half of it. FP32
+// arithmetic (FP32 and BF16 storage; bound by shared-memory traffic) takes more cells at n = 2, 3, 6,
+// 7 (fewer barriers and bulk copies per value: 17-22 % faster at n = 3, 30 % for BF16 at n = 7);
+// double-float and FP64 tiles (bound by registers and the FP32 pipes) keep the smaller ones.
+__host__ __device__ constexpr int tile_cells(int n, bool f32)
+{
+    return n == 2 ? (f32 ? 64 : 32) : n == 3 ? (f32 ? 32 : 16) : n == 4 ? 8 : n == 5 ? 8
+           : n == 6 ? (f32 ? 8 : 4) : n == 7 ? (f32 ? 8 : 4) : 2;
+}
+
+// whether a precision computes in FP32 arithmetic (its kernels use the FP32 tile sizes)
+__host__ __device__ inline bool prec_f32_arith(int prec)
+{
+    return prec == CW_PREC_F32 || prec == CW_PREC_F32_BF16G || prec == CW_PREC_BF16;
+}
+
+
 constexpr int kMaxDegree = 7;
 // cells per mesh direction: the DSS launches put one direction on the grid's y extent (<= 65535)
 constexpr int kMaxCellsPerDir = 65535;

@@ -98,16 +98,17 @@ struct RCStore<ArF32> {
     using type = float;
 };
 
-// cells per CTA: the default (about 128-200 threads) and the alternative the tuner can pick
-template <int N>
+// cells per CTA of an arithmetic's curved kernels (tile_cells): the default and the alternative the
+// tuner can pick
+template <int N, class Ar>
 constexpr int cpb_default()
 {
-    return N == 2 ? 32 : N == 3 ? 16 : N == 4 ? 8 : N == 5 ? 8 : N == 6 ? 4 : N == 7 ? 4 : 2;
+    return tile_cells(N, std::is_same<Ar, ArF32>::value);
 }
-template <int N>
+template <int N, class Ar>
 constexpr int cpb_alt()
 {
-    return cpb_default<N>() / 2;
+    return cpb_default<N, Ar>() / 2;
 }
 
 template <class K>
@@ -197,7 +198,7 @@ cudaError_t launch_metric(const Op &op, const void *x, void *y, cudaStream_t s, 
 template <int N, class Ar, class VS, class GS, bool RC>
 cudaError_t launch_smooth(const Op &op, void *u, const void *b, const void *dhat, cudaStream_t s, int *xfuse)
 {
-    constexpr int CPB = cpb_default<N>();
+    constexpr int CPB = cpb_default<N, Ar>();
     TabMetric<N, typename Ar::C> tab;
     fill_metric_tab<N>(tab, op.tab, [](double v) { return MakeC<Ar>::from(v); });
     const size_t smem = metric_smem_bytes<N, CPB, typename Ar::T, GS>(metric_ncomp(op.kind), 2);
@@ -238,7 +239,7 @@ cudaError_t launch_smooth_degree(const Op &op, void *u, const void *b, const voi
 template <int N, class Ar, class VS, class GS, bool RC = false>
 cudaError_t launch_metric_dot(const Op &op, const void *x, void *y, double *part, int64_t *nblocks, cudaStream_t s)
 {
-    constexpr int CPB = cpb_default<N>(), ST = RC ? 2 : 1;
+    constexpr int CPB = cpb_default<N, Ar>(), ST = RC ? 2 : 1;
     TabMetric<N, typename Ar::C> tab;
     fill_metric_tab<N>(tab, op.tab, [](double v) { return MakeC<Ar>::from(v); });
     const size_t smem = metric_smem_bytes<N, CPB, typename Ar::T, GS>(metric_ncomp(op.kind), ST);
@@ -300,7 +301,7 @@ cudaError_t launch_affine(const Op &op, const void *x, void *y, cudaStream_t s)
 template <int N, class Ar, class VS, class GS, bool ALL_VARIANTS, class GC>
 cudaError_t launch_variant(const Op &op, const void *x, void *y, cudaStream_t s, int *xfuse)
 {
-    constexpr int D = cpb_default<N>(), A = cpb_alt<N>();
+    constexpr int D = cpb_default<N, Ar>(), A = cpb_alt<N, Ar>();
     if (op.geom == CW_GEOM_AFFINE) {  // no fused DSS work: *xfuse stays 0
         if constexpr (ALL_VARIANTS)
             if (op.cpb == A) return launch_affine<N, A, Ar, VS>(op, x, y, s);
@@ -340,11 +341,10 @@ cudaError_t launch_degree(const Op &op, const void *x, void *y, cudaStream_t s, 
 }
 
 // the two cells-per-CTA choices of degree p
-inline void cpb_choices(int p, int out[2])
+inline void cpb_choices(int p, int prec, int out[2])
 {
-    static const int d[8] = {0, 32, 16, 8, 8, 4, 4, 2};
-    out[0] = d[p];
-    out[1] = d[p] / 2;
+    out[0] = tile_cells(p + 1, prec_f32_arith(prec));
+    out[1] = out[0] / 2;
 }
 
 }  // namespace cw

@@ -95,9 +95,6 @@ def test_apply_assemble_f64(cw, orc, p):
     assert rel_err(y, ref) <= TOL64
 
 
-CPB_DEFAULT = {1: 32, 2: 16, 3: 8, 4: 8, 5: 4, 6: 4, 7: 2}
-
-
 @pytest.mark.parametrize("prec", [0, 1, 2, 4], ids=["df64", "f64native", "f32", "bf16"])
 @pytest.mark.parametrize("dims", [(4, 3, 5), (1, 3, 2), (2, 1, 1), (5, 1, 3), (9, 2, 2)])
 @pytest.mark.parametrize("p", [1, 2, 4, 7])
@@ -112,9 +109,10 @@ def test_assemble_fused_x_matches_axis_passes(cw, p, dims, prec, geom):
     M = cw.Mesh.from_synth(mesh)
     op = cw.Operator(M, p, 3, geom, prec)
     x = torch.from_numpy(synth.cellwise_random(mesh, p, seed=40 + p)).cuda().to(op.vec_dtype)
-    variants = [(0, 0)] if prec == 1 else [(c, st) for c in (CPB_DEFAULT[p], CPB_DEFAULT[p] // 2) for st in (0, 1, 2)]
+    _, _, choices = op.variant()  # the default tile and the alternative (half of it)
+    variants = [(0, 0)] if prec == 1 else [(c, st) for c in choices for st in (0, 1, 2)]
     if geom == 2 and prec != 1:  # recomputed geometry: default tile only
-        variants = [(CPB_DEFAULT[p], st) for st in (0, 1, 2)]
+        variants = [(choices[0], st) for st in (0, 1, 2)]
     for cpb, stage in variants:
         if cpb:
             op.set_variant(cpb, stage)

@@ -30,7 +30,10 @@ def cw():
 def test_expired_wait_is_reported_and_the_context_survives(cw, orc, prec, stage):
     import torch
     p, kind = 2, 3
-    mesh = synth.box_mesh(4, 3, 2, perturb=0.1)  # 24 cells, 16 per tile at p = 2: one full tile, one ragged
+    probe = cw.Operator(cw.Mesh.from_synth(synth.box_mesh(2, 2, 2)), p, kind, cw.CW_GEOM_METRIC, prec)
+    T = probe.variant()[2][0]  # cells per tile of the default variant (16 or 32 at p = 2)
+    probe.close()
+    mesh = synth.box_mesh(4, 3, T // 8, perturb=0.1)  # 1.5 T cells: one full (staged) tile, one ragged
     M = cw.Mesh.from_synth(mesh)
     op = cw.Operator(M, p, kind, cw.CW_GEOM_METRIC, prec)
     op.set_variant(0, stage)
@@ -45,8 +48,8 @@ def test_expired_wait_is_reported_and_the_context_survives(cw, orc, prec, stage)
     assert cw.cw_op_check(op.handle) == cw.CW_OK  # the check clears the word
     yn = to_np(y).reshape(mesh.ncells, n3)
     # the staged tile computed on zeros instead of its unconfirmed input: finite, and not the result
-    assert np.isfinite(yn[:16]).all() and rel_err(yn[:16], ref[:16]) > 0.5
-    assert rel_err(yn[16:], ref[16:]) <= (1e-12 if prec == 0 else 1e-5)  # the ragged tile reads directly
+    assert np.isfinite(yn[:T]).all() and rel_err(yn[:T], ref[:T]) > 0.5
+    assert rel_err(yn[T:], ref[T:]) <= (1e-12 if prec == 0 else 1e-5)  # the ragged tile reads directly
     cw.cw_op_inject_stall(op.handle, False)
     y2 = op.apply(x)
     assert cw.cw_op_check(op.handle) == cw.CW_OK
