@@ -758,6 +758,51 @@ def batch_profile(cw, n, variant, launches=3):
     return ms
 
 
+def apply_profile(cw, n, prec, geom, variant, launches=4):
+    """Profiling case: local applies of the bench step's operator (Q4 Laplace+mass) on an n^3 curved
+    mesh in one precision and geometry mode, with a fixed kernel variant ("cells,stage") or the
+    default; returns the mean time per apply in ms."""
+    import torch
+    mesh = synth.box_mesh(n, perturb=0.1)
+    op = cw.Operator(cw.Mesh.from_synth(mesh), P, KIND, geom, prec)
+    x = op.gather(torch.from_numpy(synth.global_vector(mesh, P, seed=0)).cuda())
+    y = op.empty()
+    if variant:
+        op.set_variant(*[int(v) for v in variant.split(",")])
+    op.apply(x, y)
+    torch.cuda.synchronize()
+    a, e = event_pair()
+    a.record()
+    for _ in range(launches):
+        op.apply(x, y)
+    e.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(e) / launches
+
+
+def mblock_profile(cw, n, launches=3):
+    """Profiling case: the 7-block cube in cube with n^3 cells per block, Q3 Laplace, FP64 double-float:
+    assembled multi-block applies (every block's operator, the structured DSS inside the blocks, then the
+    unstructured inter-block DSS), launched a few times; returns the mean time per apply in ms."""
+    import torch
+    mbm = synth.cube_in_cube(n, seed=0)
+    ops = [cw.Operator(cw.Mesh.from_synth(m), 3, cw.CW_LAPLACE, cw.CW_GEOM_METRIC, cw.CW_PREC_F64,
+                       cw.CW_BC_DIRICHLET0) for m in mbm.blocks]
+    mb = cw.MultiBlock(ops)
+    x = torch.empty(mb.L, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+    mb.dss(x, average=True)
+    y = mb.empty()
+    mb.apply(x, y, assemble=True)
+    torch.cuda.synchronize()
+    a, e = event_pair()
+    a.record()
+    for _ in range(launches):
+        mb.apply(x, y, assemble=True)
+    e.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(e) / launches
+
+
 def mg_cycle_profile(cw, n, prec, cycles=3):
     """Profiling case: V-cycles alone (zero initial guess) on a Q3 hierarchy whose finest mesh has n^3
     cells (6 levels, refined from a curved (n/32)^3 mesh), in one precision; no solver. Returns the mean
@@ -877,6 +922,11 @@ def main():
                     help="multigrid leg without the Jacobi comparison solve")
     ap.add_argument("--profile-mg", type=int, default=0,
                     help="profiling case: only V-cycles on an N^3 Q3 hierarchy (FP32), then exit")
+    ap.add_argument("--profile-apply", type=int, default=0,
+                    help="profiling case: local applies of the step's operator on an N^3 mesh (--prec, --geom, --variant)")
+    ap.add_argument("--geom", type=int, default=1, help="CW_GEOM_* of --profile-apply (1 stored metric, 2 recomputed)")
+    ap.add_argument("--profile-mblock", type=int, default=0,
+                    help="profiling case: assembled applies on the 7-block cube in cube, N^3 cells per block")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="profiling case: only a 16-RHS grouped batch on a Q5 N^3 mesh (FP32), then exit")
     ap.add_argument("--batch-variant", type=int, default=2, help="degree-5 variant of --profile-batch")
@@ -905,6 +955,23 @@ def main():
         cw.load()
         print(json.dumps({"profile": "batch_16rhs_q5", "cells": args.profile_batch ** 3, "variant": args.batch_variant,
                           "ms_per_launch": batch_profile(cw, args.profile_batch, args.batch_variant)}))
+        return
+    if args.profile_apply:
+        import torch
+        import paper_2607_03413_gb300 as cw
+        torch.cuda.set_device(0)
+        cw.load()
+        print(json.dumps({"profile": "apply", "cells": args.profile_apply ** 3, "prec": args.prec, "geom": args.geom,
+                          "variant": args.variant,
+                          "ms_per_apply": apply_profile(cw, args.profile_apply, args.prec, args.geom, args.variant)}))
+        return
+    if args.profile_mblock:
+        import torch
+        import paper_2607_03413_gb300 as cw
+        torch.cuda.set_device(0)
+        cw.load()
+        print(json.dumps({"profile": "mblock_apply", "cells_per_block": args.profile_mblock ** 3,
+                          "ms_per_apply": mblock_profile(cw, args.profile_mblock)}))
         return
     if args.profile_mg:
         import torch
