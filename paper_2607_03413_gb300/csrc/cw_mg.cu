@@ -278,7 +278,10 @@ static void host_parallel_for(int n, F f)
         for (int i; (i = next.fetch_add(1)) < n;) f(i);
     };
     std::vector<std::thread> th;
-    for (int t = 1; t < nt; ++t) th.emplace_back(work);
+    try {
+        for (int t = 1; t < nt; ++t) th.emplace_back(work);
+    } catch (...) {  // no more threads: the ones started and this one share the indices
+    }
     work();
     for (auto &t : th) t.join();
 }
