@@ -394,17 +394,23 @@ static cw_status coarse_setup(MgHier &h)
     if (e == cudaSuccess) e = cudaMemcpy(Ae.data(), dA, abytes, cudaMemcpyDeviceToHost);
     cudaFree(dA);
     if (e != cudaSuccess) return cuda_fail(e, "cw_mg_create: coarse element matrices");
-    std::vector<double> A((size_t)ni * ni, 0.0);
-    for (int64_t c = 0; c < op.E; ++c)
-        for (int i = 0; i < n3; ++i) {
-            const int gi_ = gi[c * n3 + i];
-            if (gi_ < 0) continue;
-            for (int j = 0; j < n3; ++j) {
-                const int gj = gi[c * n3 + j];
-                if (gj >= 0) A[(size_t)gi_ * ni + gj] += Ae[((size_t)c * n3 + i) * n3 + j];
+    std::vector<double> A;
+    try {  // the dense interior block and the inverse's work arrays (up to 134 MB each)
+        A.assign((size_t)ni * ni, 0.0);
+        for (int64_t c = 0; c < op.E; ++c)
+            for (int i = 0; i < n3; ++i) {
+                const int gi_ = gi[c * n3 + i];
+                if (gi_ < 0) continue;
+                for (int j = 0; j < n3; ++j) {
+                    const int gj = gi[c * n3 + j];
+                    if (gj >= 0) A[(size_t)gi_ * ni + gj] += Ae[((size_t)c * n3 + i) * n3 + j];
+                }
             }
-        }
-    if (!spd_inverse(A, (int)ni)) return fail(CW_ERR_ARG, "cw_mg_create: the coarse matrix is not positive definite");
+        if (!spd_inverse(A, (int)ni))
+            return fail(CW_ERR_ARG, "cw_mg_create: the coarse matrix is not positive definite");
+    } catch (const std::bad_alloc &) {
+        return fail(CW_ERR_OOM, "cw_mg_create: host allocation failed (coarse matrix)");
+    }
     CW_CUDA_TRY(cudaMalloc(&h.ainv, A.size() * sizeof(double)));
     CW_CUDA_TRY(cudaMalloc(&h.xg, ni * sizeof(double)));
     CW_CUDA_TRY(cudaMalloc(&h.yg, ni * sizeof(double)));
