@@ -166,3 +166,45 @@ def test_config5_batched(cw, orc):
             ref = oracle_local_on_cells(orc, m, p, 1, ugs[i][r], cells)
             assert rel_err(to_np(y[r]).reshape(m.ncells, n3)[cells], ref) <= 1e-12, (i, r)
     B.close()
+
+
+def test_apply_past_2e31_cellwise_values(cw, orc):
+    """162^3 cells at p = 7 hold 2,176,782,336 cell-wise values, more than 2^31: the LOCAL and the
+    assembled apply (FP32, mass) on cells at both ends of the vector and on both sides of value 2^31,
+    each against the oracle on the cell's 3x3x3 neighbourhood cut from the same mesh (the local output
+    of a cell depends on its own vertices and values only; every cell sharing one of its DoFs is in the
+    neighbourhood, so the oracle's DSS there gives its assembled values)."""
+    import torch
+    p, kind, n = 7, 2, 162
+    n3 = (p + 1) ** 3
+    mesh = synth.box_mesh(n, perturb=0.1)
+    op = cw.Operator(cw.Mesh.from_synth(mesh), p, kind, cw.CW_GEOM_METRIC, cw.CW_PREC_F32)
+    assert op.L == n ** 3 * n3 and op.L > 2 ** 31
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(31)
+    x = torch.rand(op.L, dtype=torch.float32, device="cuda", generator=gen).sub_(0.5)
+    y = op.apply(x)
+    ya = op.apply(x, assemble=True)
+    torch.cuda.synchronize()
+    straddle = 2 ** 31 // n3  # the cell whose values reach past 2^31
+    rng = np.random.default_rng(7)
+    cells = sorted({0, n - 1, straddle - 1, straddle, straddle + 1, n ** 3 - n * n + 5 * n + 7, n ** 3 - 1,
+                    *rng.integers(straddle, n ** 3, 4).tolist()})
+    for c in cells:
+        cx, cy, cz = c % n, (c // n) % n, c // (n * n)
+        x0, x1 = max(cx - 1, 0), min(cx + 2, n)
+        y0, y1 = max(cy - 1, 0), min(cy + 2, n)
+        z0, z1 = max(cz - 1, 0), min(cz + 2, n)
+        sub = synth.Mesh(x1 - x0, y1 - y0, z1 - z0,
+                         np.ascontiguousarray(mesh.verts[z0:z1 + 1, y0:y1 + 1, x0:x1 + 1]), False)
+        ids = np.array([(i + x0) + n * ((j + y0) + n * (k + z0))
+                        for k in range(z1 - z0) for j in range(y1 - y0) for i in range(x1 - x0)], dtype=np.int64)
+        idx = torch.from_numpy((ids[:, None] * n3 + np.arange(n3)[None, :]).ravel()).cuda()
+        xs = to_np(x.index_select(0, idx)).astype(np.float64)
+        yl = orc.apply_local(sub, p, kind, xs).reshape(len(ids), n3)
+        ys = orc.dss(sub, p, yl.ravel()).reshape(len(ids), n3)
+        kc = int(np.nonzero(ids == c)[0][0])
+        got = to_np(y[c * n3:(c + 1) * n3]).astype(np.float64)
+        got_a = to_np(ya[c * n3:(c + 1) * n3]).astype(np.float64)
+        assert rel_err(got, yl[kc]) <= 5e-6, c
+        assert rel_err(got_a, ys[kc]) <= 5e-6, c
