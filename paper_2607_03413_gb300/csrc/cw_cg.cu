@@ -26,6 +26,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <type_traits>
 
 #include "cw_arith.cuh"
@@ -574,10 +575,10 @@ template <class K>
 static unsigned res_grid(K kernel, int threads)
 {
     static std::mutex mu;
-    static std::map<std::pair<const void *, int>, unsigned> cache;
+    static std::map<std::tuple<const void *, int, int>, unsigned> cache;  // (kernel, threads, device)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return kRedBlocks;
-    const std::pair<const void *, int> key(reinterpret_cast<const void *>(kernel), dev);
+    const std::tuple<const void *, int, int> key(reinterpret_cast<const void *>(kernel), threads, dev);
     std::lock_guard<std::mutex> g(mu);
     const auto it = cache.find(key);
     if (it != cache.end()) return it->second;
