@@ -149,3 +149,57 @@ def test_failures_are_reported_not_raised_on_device(cw):
     # the context is still usable
     u, st, rc = op.cg_solve(op.load_vector(0), rtol=1e-10, maxit=500)
     assert st.rel_residual <= 1e-10
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3], ids=["f64", "ir_f32", "ir_bf16", "f64_native"])
+def test_zero_right_hand_side(cw, mode):
+    """b = 0: every mode returns u = 0 at once (zero iterations, relative residual 0, CW_OK)."""
+    import torch
+    mesh = synth.box_mesh(3, 2, 4, perturb=0.1)
+    M, op = make(cw, mesh, 2)
+    b = torch.zeros(op.L, dtype=torch.float64, device="cuda")
+    u = torch.full_like(b, float("nan"))
+    u, st, rc = op.cg_solve(b, u, rtol=1e-10, mode=mode)
+    assert rc == cw.CW_OK and st.iterations == 0 and st.rel_residual == 0.0
+    assert torch.count_nonzero(u).item() == 0
+
+
+def test_meshes_with_no_and_one_interior_dof(cw, orc):
+    """One cell with homogeneous Dirichlet conditions: at p = 1 every DoF is on the boundary (the masked
+    right-hand side vanishes; u = 0 with no iteration); at p = 2 the centre node is the only unknown, so
+    one CG iteration reaches the oracle's direct solve."""
+    import torch
+    mesh = synth.box_mesh(1, perturb=0.0)
+    M, op = make(cw, mesh, 1)
+    b = op.load_vector(0)
+    assert torch.count_nonzero(b).item() > 0  # the raw load vector is not zero; its interior part is
+    u, st, rc = op.cg_solve(b, rtol=1e-12)
+    assert rc == cw.CW_OK and st.iterations == 0 and torch.count_nonzero(u).item() == 0
+    mesh2 = synth.box_mesh(1, perturb=0.0)
+    M2, op2 = make(cw, mesh2, 2)
+    b2 = orc.load_vector(mesh2, 2, orc.PROBLEM_SINE)
+    u2, st2, rc2 = op2.cg_solve(torch.from_numpy(b2).cuda(), rtol=1e-12)
+    A = orc.assemble_global(mesh2, 2, 1)
+    ud = orc.gather(mesh2, 2, orc.direct_solve(A, orc.scatter_add(mesh2, 2, b2), orc.boundary_mask_global(mesh2, 2)))
+    assert rc2 == cw.CW_OK and st2.iterations == 1
+    assert rel_err(to_np(u2), ud) <= 1e-12
+
+
+def test_zero_right_hand_side_multigrid_and_multiblock(cw):
+    """b = 0 through the multigrid-preconditioned CG and the multi-block CG: u = 0, CW_OK, no iteration."""
+    import torch
+    ms = [synth.box_mesh(2, perturb=0.1)]
+    ms.append(synth.refine(ms[0]))
+    ops = [cw.Operator(cw.Mesh.from_synth(m), 2, 1, cw.CW_GEOM_METRIC, cw.CW_PREC_F64, cw.CW_BC_DIRICHLET0)
+           for m in ms]
+    mg = cw.Multigrid(ops)
+    b = torch.zeros(ops[-1].L, dtype=torch.float64, device="cuda")
+    u, st, rc = mg.pcg_solve(ops[-1], b)
+    assert rc == cw.CW_OK and st.iterations == 0 and torch.count_nonzero(u).item() == 0
+    mbm = synth.cube_blocks(2, 1, perturb=0.0, seed=1)
+    bops = [cw.Operator(cw.Mesh.from_synth(m), 2, 1, cw.CW_GEOM_METRIC, cw.CW_PREC_F64, cw.CW_BC_DIRICHLET0)
+            for m in mbm.blocks]
+    mb = cw.MultiBlock(bops)
+    bz = torch.zeros(mb.L, dtype=torch.float64, device="cuda")
+    u, st, rc = mb.cg_solve(bz)
+    assert rc == cw.CW_OK and st.iterations == 0 and torch.count_nonzero(u).item() == 0
