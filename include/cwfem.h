@@ -100,6 +100,9 @@ typedef enum {
 #define CW_CG_IR_F32 1     /* inner CG in FP32 (FP32 vectors and metric, FP64-accumulated dots) */
 #define CW_CG_IR_BF16 2    /* inner CG in FP32 with the metric stored in BF16 */
 #define CW_CG_F64_NATIVE 3 /* inner CG in FP64 with the IEEE FP64 operator (plain FP64 CG) */
+/* flag OR-ed into a cw_cg_solve mode: start from the caller's u (resume a solve, or refine a guess)
+   instead of u = 0 */
+#define CW_CG_WARM_START 0x100
 
 typedef struct {
     int iterations;        /* total CG iterations (inner iterations summed for IR modes) */
@@ -273,7 +276,12 @@ cw_status cw_load_vector(cw_op op, int which, double *b, void *stream);
  * Solve A_CG u_g = G^T b for the Poisson / K+M operator with homogeneous Dirichlet conditions
  * (op bc must be CW_BC_DIRICHLET0, precision CW_PREC_F64), by Jacobi-preconditioned CG on
  * cell-wise data from u = 0 (Sec. 4.1 Eq. (jacobi_recap); Sec. 4.4). b: FP64 cell-wise dual;
- * u: FP64 cell-wise primal output. Stops when rel_residual <= rtol or after maxit iterations
+ * u: FP64 cell-wise primal output; with CW_CG_WARM_START in mode, also the input iterate (a continuous
+ * cell-wise vector, e.g. the u of an earlier call: checkpoint = copy u out, resume = call again with
+ * the flag): the first residual b - A u is then evaluated with the IEEE FP64 operator, the stopping
+ * measure stays relative to b, the corrections vanish on boundary DoFs (their values in u are kept:
+ * zero for the homogeneous problem), and a non-finite initial residual returns CW_ERR_BREAKDOWN with
+ * u untouched; with b = 0 the solve returns u = 0. Stops when rel_residual <= rtol or after maxit iterations
  * (CW_ERR_NOT_CONVERGED; u then holds the last iterate). mode selects the inner solver (see the
  * CW_CG_* modes); the relative residual is always measured with the IEEE FP64 operator (a twin of
  * op with precision CW_PREC_F64_NATIVE, its metric stored as doubles). The inner right-hand side

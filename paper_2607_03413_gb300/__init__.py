@@ -25,6 +25,7 @@ CW_BC_NONE, CW_BC_DIRICHLET0 = 0, 1
 CW_APPLY_LOCAL, CW_APPLY_ASSEMBLE = 0, 1
 CW_DSS_SUM, CW_DSS_AVERAGE = 0, 1
 CW_CG_F64, CW_CG_IR_F32, CW_CG_IR_BF16, CW_CG_F64_NATIVE = 0, 1, 2, 3
+CW_CG_WARM_START = 0x100
 CW_BATCH_GROUPED, CW_BATCH_SINGLE = 0, 1
 
 # exported symbols declared in include/cwfem.h (checked by the CPU test suite)
@@ -559,11 +560,15 @@ class Operator:
         cw_load_vector(self.handle, which, b)
         return b
 
-    def cg_solve(self, b, u=None, rtol=1e-10, maxit=10000, mode=CW_CG_F64, check=True):
+    def cg_solve(self, b, u=None, rtol=1e-10, maxit=10000, mode=CW_CG_F64, check=True, warm_start=False):
+        """Jacobi-PCG (cw_cg_solve); warm_start: start from the given u (resume an earlier solve)."""
         import torch
         self._f64(b, "cg_solve: b")
+        if warm_start and u is None:
+            raise ValueError("cg_solve: warm_start needs the initial iterate u")
         u = torch.empty(self.L, dtype=torch.float64, device="cuda") if u is None else self._f64(u, "cg_solve: u")
-        rc, st = cw_cg_solve(self.handle, b, u, rtol, maxit, mode, check=check)
+        rc, st = cw_cg_solve(self.handle, b, u, rtol, maxit, mode | (CW_CG_WARM_START if warm_start else 0),
+                             check=check)
         return u, st, rc
 
     def residual(self, b, u, prec=CW_PREC_F64_NATIVE):

@@ -1076,7 +1076,7 @@ using namespace cw;
 // The outer refinement loop shared by cw_cg_solve (Jacobi-preconditioned inner CG, mg == nullptr)
 // and cw_mg_pcg_solve (V-cycle-preconditioned inner CG in FP64).
 static cw_status solve_impl(Op *op, const double *b, double *u, double rtol, int maxit, int mode, MgHier *mg,
-                            cw_cg_stats *stats, void *stream)
+                            cw_cg_stats *stats, void *stream, bool warm = false)
 {
     cudaStream_t us = static_cast<cudaStream_t>(stream);
     cw_status st = ensure_scratch(op, mode);
@@ -1107,11 +1107,18 @@ static cw_status solve_impl(Op *op, const double *b, double *u, double rtol, int
     double *r = c.rout, *w = c.q64b;
     int iters = 0, outer = 0;
     double res0 = 0.0, res = 0.0;
-    CW_CUDA_TRY(cudaMemsetAsync(u, 0, L * sizeof(double), s));
     k_copy<double, double><<<vec_grid(), 256, 0, s>>>(r, b, L);
     if ((st = residual_norm2(*op, r, w, c, &res0)) != CW_OK) return st;
     if (!std::isfinite(res0)) return fail(CW_ERR_BREAKDOWN, "cw_cg_solve: non-finite right-hand side");
-    res = res0;
+    if (warm && res0 > 0.0) {  // r = b - A u of the caller's iterate, with the IEEE FP64 operator
+        CW_CUDA_TRY(apply_launch_f64n(*op->native, u, w, s));
+        k_sub<<<vec_grid(), 256, 0, s>>>(r, b, w, L);
+        if ((st = residual_norm2(*op, r, w, c, &res)) != CW_OK) return st;
+        if (!std::isfinite(res)) return fail(CW_ERR_BREAKDOWN, "cw_cg_solve: non-finite initial residual (warm start)");
+    } else {
+        CW_CUDA_TRY(cudaMemsetAsync(u, 0, L * sizeof(double), s));
+        res = res0;
+    }
     st = res0 > 0.0 ? CW_ERR_NOT_CONVERGED : CW_OK;
     bool consistent = false;  // the last segment's true reduction followed its recursive one
     while (res0 > 0.0 && iters < maxit && outer < 200) {
@@ -1193,10 +1200,12 @@ extern "C" cw_status cw_cg_solve(cw_op oh, const double *b, double *u, double rt
     if (!op || !b || !u) return fail(CW_ERR_ARG, "cw_cg_solve: NULL argument");
     if (op->prec != CW_PREC_F64) return fail(CW_ERR_ARG, "cw_cg_solve: the operator must be CW_PREC_F64");
     if (op->bc != CW_BC_DIRICHLET0) return fail(CW_ERR_ARG, "cw_cg_solve: the operator must use CW_BC_DIRICHLET0");
+    const bool warm = (mode & CW_CG_WARM_START) != 0;
+    mode &= ~CW_CG_WARM_START;
     if (mode < CW_CG_F64 || mode > CW_CG_F64_NATIVE) return fail(CW_ERR_ARG, "cw_cg_solve: bad mode");
     if (!(rtol > 0.0) || maxit < 1) return fail(CW_ERR_ARG, "cw_cg_solve: rtol must be > 0 and maxit >= 1");
     if (b == u) return fail(CW_ERR_ARG, "cw_cg_solve: b and u must not alias");
-    return solve_impl(op, b, u, rtol, maxit, mode, nullptr, stats, stream);
+    return solve_impl(op, b, u, rtol, maxit, mode, nullptr, stats, stream, warm);
 }
 
 extern "C" cw_status cw_mg_pcg_solve(cw_mg mh, cw_op oh, const double *b, double *u, double rtol, int maxit,

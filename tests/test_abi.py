@@ -23,7 +23,8 @@ def lib():
 
 def declared_constants():
     src = open(os.path.join(ROOT, "include", "cwfem.h")).read()
-    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"^#define (CW_[A-Z0-9_]+) (\d+)", src, re.M)}
+    consts = {m.group(1): int(m.group(2), 0)
+              for m in re.finditer(r"^#define (CW_[A-Z0-9_]+) (0x[0-9a-fA-F]+|\d+)", src, re.M)}
     consts.update({m.group(1): int(m.group(2)) for m in re.finditer(r"^\s+(CW_[A-Z_]+) = (\d+)", src, re.M)})
     return consts
 

@@ -203,3 +203,45 @@ def test_zero_right_hand_side_multigrid_and_multiblock(cw):
     bz = torch.zeros(mb.L, dtype=torch.float64, device="cuda")
     u, st, rc = mb.cg_solve(bz)
     assert rc == cw.CW_OK and st.iterations == 0 and torch.count_nonzero(u).item() == 0
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["f64", "ir_f32"])
+def test_warm_start_resumes_a_solve(cw, orc, mode):
+    """Checkpoint / resume: a solve stopped at rtol 1e-4, copied to the host and back, then continued
+    with CW_CG_WARM_START reaches the oracle's direct solve; the residual stays relative to b, a
+    converged iterate resumes with no iteration and comes back unchanged, a non-finite iterate is
+    reported (CW_ERR_BREAKDOWN) before any write to u, and b = 0 returns u = 0."""
+    import torch
+    p = 3
+    mesh = synth.box_mesh(4, 3, 5, perturb=0.2)
+    M, op = make(cw, mesh, p)
+    bh = orc.load_vector(mesh, p, orc.PROBLEM_SINE)
+    b = torch.from_numpy(bh).cuda()
+    A = orc.assemble_global(mesh, p, 1)
+    ud = orc.gather(mesh, p, orc.direct_solve(A, orc.scatter_add(mesh, p, bh), orc.boundary_mask_global(mesh, p)))
+    u1, s1, rc1 = op.cg_solve(b, rtol=1e-4, maxit=2000, mode=mode)
+    assert rc1 == cw.CW_OK and 1e-9 < s1.rel_residual <= 1e-4
+    ckpt = to_np(u1).copy()  # the checkpoint lives on the host
+    u2 = torch.from_numpy(ckpt).cuda()
+    u2, s2, rc2 = op.cg_solve(b, u2, rtol=1e-11, maxit=2000, mode=mode, warm_start=True)
+    assert rc2 == cw.CW_OK and s2.rel_residual <= 1e-11 and s2.iterations > 0
+    assert rel_err(to_np(u2), ud) <= 1e-9
+    assert abs(op.residual(b, u2) - s2.rel_residual) <= 1e-3 * s2.rel_residual
+    # resuming from the converged iterate: nothing left to do, u untouched
+    keep = u2.clone()
+    u3, s3, rc3 = op.cg_solve(b, u2, rtol=1e-10, maxit=2000, mode=mode, warm_start=True)
+    assert rc3 == cw.CW_OK and s3.iterations == 0 and s3.outer_iterations == 0
+    assert torch.equal(u3, keep)
+    # a non-finite iterate is refused before the solve writes u
+    bad = torch.from_numpy(ckpt).cuda()
+    bad[1 + 4 + 16] = float("nan")  # node (1,1,1) of cell 0: an interior DoF
+    bad_in = bad.clone()
+    _, _, rc4 = op.cg_solve(b, bad, rtol=1e-10, maxit=100, mode=mode, check=False, warm_start=True)
+    assert rc4 == cw.CW_ERR_BREAKDOWN
+    assert torch.equal(torch.isnan(bad), torch.isnan(bad_in)) and torch.equal(bad.nan_to_num(), bad_in.nan_to_num())
+    # b = 0 with a warm start: the solution is 0 whatever the guess
+    u5 = torch.from_numpy(ckpt).cuda()
+    u5, s5, rc5 = op.cg_solve(torch.zeros_like(b), u5, rtol=1e-10, mode=mode, warm_start=True)
+    assert rc5 == cw.CW_OK and s5.iterations == 0 and torch.count_nonzero(u5).item() == 0
+    # an unknown flag bit is an argument error
+    assert cw.load().cw_cg_solve(op.handle, cw._ptr(b), cw._ptr(u5), 1e-8, 10, mode | 0x200, None, None) == cw.CW_ERR_ARG
