@@ -932,6 +932,7 @@ cw_status cw_mesh_destroy(cw_mesh mh)
 
 cw_status cw_op_create(cw_mesh mh, int degree, int kind, int geom, int prec, int bc, cw_op *out)
 {
+    cw::Range nvtx_range("cwfem:cw_op_create");
     if (!out) return fail(CW_ERR_ARG, "cw_op_create: out is NULL");
     *out = nullptr;
     Mesh *m = reinterpret_cast<Mesh *>(mh);
@@ -1111,6 +1112,7 @@ cw_status cw_gather(cw_op oh, const double *ug, void *x, void *stream)
 
 cw_status cw_apply(cw_op oh, const void *x, void *y, int flags, void *stream)
 {
+    cw::Range nvtx_range("cwfem:cw_apply");
     Op *op = reinterpret_cast<Op *>(oh);
     if (!op || !x || !y) return fail(CW_ERR_ARG, "cw_apply: NULL argument");
     if (flags != CW_APPLY_LOCAL && flags != CW_APPLY_ASSEMBLE) return fail(CW_ERR_ARG, "cw_apply: bad flags");
@@ -1139,6 +1141,7 @@ cw_status cw_dss(cw_op oh, void *v, int flags, void *stream)
 
 cw_status cw_diagonal(cw_op oh, double *d, void *stream)
 {
+    cw::Range nvtx_range("cwfem:cw_diagonal");
     Op *op = reinterpret_cast<Op *>(oh);
     if (!op || !d) return fail(CW_ERR_ARG, "cw_diagonal: NULL argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1236,6 +1239,7 @@ cw_status cw_op_get_variant(cw_op oh, int *cells_per_cta, int *stage, int *choic
 
 cw_status cw_op_autotune(cw_op oh, const void *x, void *y, int reps, void *stream, float *best_ms)
 {
+    cw::Range nvtx_range("cwfem:cw_op_autotune");
     Op *op = reinterpret_cast<Op *>(oh);
     if (!op || !x || !y || x == y) return fail(CW_ERR_ARG, "cw_op_autotune: NULL or aliasing argument");
     if (reps < 1) return fail(CW_ERR_ARG, "cw_op_autotune: reps must be >= 1");
@@ -1310,6 +1314,7 @@ extern "C" {
 // copy back overlaps the work on slab k.
 cw_status cw_apply_host(cw_op oh, const void *x_host, void *y_host, int flags, void *stream)
 {
+    cw::Range nvtx_range("cwfem:cw_apply_host");
     Op *op = reinterpret_cast<Op *>(oh);
     if (!op || !x_host || !y_host) return fail(CW_ERR_ARG, "cw_apply_host: NULL argument");
     if (flags != CW_APPLY_LOCAL && flags != CW_APPLY_ASSEMBLE) return fail(CW_ERR_ARG, "cw_apply_host: bad flags");

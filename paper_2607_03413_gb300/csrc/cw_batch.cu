@@ -264,6 +264,7 @@ cw_status cw_batch_get_variant(cw_batch bh, int degree, int *variant, int *cells
 
 cw_status cw_batch_launch(cw_batch bh, void *stream)
 {
+    cw::Range nvtx_range("cwfem:cw_batch_launch");
     Batch *b = reinterpret_cast<Batch *>(bh);
     if (!b) return fail(CW_ERR_ARG, "cw_batch_launch: NULL handle");
     CW_CUDA_TRY(batch_enqueue(*b, static_cast<cudaStream_t>(stream)));
@@ -272,6 +273,7 @@ cw_status cw_batch_launch(cw_batch bh, void *stream)
 
 cw_status cw_batch_graph_launch(cw_batch bh, void *stream)
 {
+    cw::Range nvtx_range("cwfem:cw_batch_graph_launch");
     Batch *b = reinterpret_cast<Batch *>(bh);
     if (!b) return fail(CW_ERR_ARG, "cw_batch_graph_launch: NULL handle");
     if (!b->graph) {
@@ -291,6 +293,7 @@ cw_status cw_batch_graph_launch(cw_batch bh, void *stream)
 
 cw_status cw_batch_autotune(cw_batch bh, int reps, void *stream, float *best_ms)
 {
+    cw::Range nvtx_range("cwfem:cw_batch_autotune");
     Batch *b = reinterpret_cast<Batch *>(bh);
     if (!b || reps < 1) return fail(CW_ERR_ARG, "cw_batch_autotune: NULL handle or reps < 1");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -349,6 +352,7 @@ cw_status cw_batch_autotune(cw_batch bh, int reps, void *stream, float *best_ms)
 cw_status cw_apply_batched(const cw_op *ops, const void *const *x, void *const *y, const int *nrhs, int nprob,
                            int flags, void *stream)
 {
+    cw::Range nvtx_range("cwfem:cw_apply_batched");
     if (flags != CW_APPLY_LOCAL && flags != CW_APPLY_ASSEMBLE)
         return fail(CW_ERR_ARG, "cw_apply_batched: flags must be CW_APPLY_LOCAL or CW_APPLY_ASSEMBLE");
     cw_batch b = nullptr;

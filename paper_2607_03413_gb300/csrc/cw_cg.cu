@@ -1126,6 +1126,7 @@ static cw_status solve_impl(Op *op, const double *b, double *u, double rtol, int
             st = CW_OK;
             break;
         }
+        cw::Range outer_range("cwfem:cg_outer_step");  // inner segment, correction, true residual
         const double need = rtol * std::sqrt(res0 / res);
         const double itol = std::min(0.5, std::max(floor_tol, 0.5 * need));
         int it = 0;
@@ -1196,6 +1197,7 @@ static cw_status solve_impl(Op *op, const double *b, double *u, double rtol, int
 extern "C" cw_status cw_cg_solve(cw_op oh, const double *b, double *u, double rtol, int maxit, int mode,
                                  cw_cg_stats *stats, void *stream)
 {
+    cw::Range nvtx_range("cwfem:cw_cg_solve");
     Op *op = reinterpret_cast<Op *>(oh);
     if (!op || !b || !u) return fail(CW_ERR_ARG, "cw_cg_solve: NULL argument");
     if (op->prec != CW_PREC_F64) return fail(CW_ERR_ARG, "cw_cg_solve: the operator must be CW_PREC_F64");
@@ -1211,6 +1213,7 @@ extern "C" cw_status cw_cg_solve(cw_op oh, const double *b, double *u, double rt
 extern "C" cw_status cw_mg_pcg_solve(cw_mg mh, cw_op oh, const double *b, double *u, double rtol, int maxit,
                                      cw_cg_stats *stats, void *stream)
 {
+    cw::Range nvtx_range("cwfem:cw_mg_pcg_solve");
     Op *op = reinterpret_cast<Op *>(oh);
     MgHier *mg = reinterpret_cast<MgHier *>(mh);
     if (!mg || !op || !b || !u) return fail(CW_ERR_ARG, "cw_mg_pcg_solve: NULL argument");
@@ -1326,6 +1329,7 @@ static cw_status cg_run_eager(const Op &aop, int ak, CgLevel &lv, double *u, CgS
 extern "C" cw_status cw_cg_solve_noalloc(cw_op oh, const double *b, double *u, double rtol, int maxit, int mode,
                                          cw_cg_stats *stats, void *stream)
 {
+    cw::Range nvtx_range("cwfem:cw_cg_solve_noalloc");
     Op *op = reinterpret_cast<Op *>(oh);
     if (!op || !b || !u) return fail(CW_ERR_ARG, "cw_cg_solve_noalloc: NULL argument");
     if (op->prec != CW_PREC_F64) return fail(CW_ERR_ARG, "cw_cg_solve_noalloc: the operator must be CW_PREC_F64");

@@ -1,6 +1,7 @@
 // cw_internal.h -- host-side structures shared by the library's translation units.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -8,6 +9,16 @@
 #include "../../include/cwfem.h"
 
 namespace cw {
+
+// Host-side NVTX range around an entry point or a solver phase: a profiler's timeline (and ncu's
+// --nvtx filters) sees "cwfem:<name>". Header-only NVTX: with no tool attached a push or a pop is a
+// call through a null-checked pointer.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 // Cells per CTA of the curved kernels: the default; the tuner's alternative is half of it. FP32
 // arithmetic (FP32 and BF16 storage; bound by shared-memory traffic) takes more cells at n = 2, 3, 6,

@@ -533,6 +533,7 @@ extern "C" {
 
 cw_status cw_mblock_create(const cw_op *ops, int nblocks, cw_mblock *out)
 {
+    cw::Range nvtx_range("cwfem:cw_mblock_create");
     if (!out) return fail(CW_ERR_ARG, "cw_mblock_create: out is NULL");
     *out = nullptr;
     if (!ops || nblocks < 1) return fail(CW_ERR_ARG, "cw_mblock_create: need at least one block");
@@ -619,6 +620,7 @@ cw_status cw_mblock_dss(cw_mblock h, void *v, int flags, void *stream)
 
 cw_status cw_mblock_apply(cw_mblock h, const void *x, void *y, int flags, void *stream)
 {
+    cw::Range nvtx_range("cwfem:cw_mblock_apply");
     MBlock *mb = reinterpret_cast<MBlock *>(h);
     if (!mb || !x || !y) return fail(CW_ERR_ARG, "cw_mblock_apply: NULL argument");
     if (flags != CW_APPLY_LOCAL && flags != CW_APPLY_ASSEMBLE) return fail(CW_ERR_ARG, "cw_mblock_apply: bad flags");
@@ -649,6 +651,7 @@ cw_status cw_mblock_diagonal(cw_mblock h, double *d, void *stream)
 cw_status cw_mblock_cg_solve(cw_mblock h, const double *b, double *u, double rtol, int maxit, cw_cg_stats *stats,
                              void *stream)
 {
+    cw::Range nvtx_range("cwfem:cw_mblock_cg_solve");
     MBlock *mb = reinterpret_cast<MBlock *>(h);
     if (!mb || !b || !u) return fail(CW_ERR_ARG, "cw_mblock_cg_solve: NULL argument");
     if (mb->prec != CW_PREC_F64) return fail(CW_ERR_ARG, "cw_mblock_cg_solve: the blocks must be CW_PREC_F64");

@@ -434,6 +434,7 @@ extern "C" {
 
 cw_status cw_mg_create(const cw_op *levels, int nlevels, int nu1, int nu2, double omega, cw_mg *out)
 {
+    cw::Range nvtx_range("cwfem:cw_mg_create");
     if (!out) return fail(CW_ERR_ARG, "cw_mg_create: out is NULL");
     *out = nullptr;
     if (!levels || nlevels < 1 || nlevels > 16) return fail(CW_ERR_ARG, "cw_mg_create: need 1..16 levels");
@@ -535,6 +536,7 @@ int64_t cw_mg_device_bytes(cw_mg mh)
 
 cw_status cw_mg_vcycle(cw_mg mh, const void *b, void *u, int zero_guess, void *stream)
 {
+    cw::Range nvtx_range("cwfem:cw_mg_vcycle");
     MgHier *h = reinterpret_cast<MgHier *>(mh);
     if (!h || !b || !u) return fail(CW_ERR_ARG, "cw_mg_vcycle: NULL argument");
     if (b == u) return fail(CW_ERR_ARG, "cw_mg_vcycle: b and u must not alias");

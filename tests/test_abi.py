@@ -236,3 +236,33 @@ def test_library_basis_matrices_match_the_oracle(lib, orc, p):
     assert np.abs(D - LD).max() < 1e-11
     assert np.abs(M1 - LB.T @ np.diag(wq) @ LB).max() < 1e-14
     assert np.abs(K1 - LBd.T @ np.diag(wq) @ LBd).max() < 1e-12 * max(1.0, np.abs(K1).max())
+
+
+def test_entry_points_open_balanced_nvtx_ranges(lib, tmp_path):
+    """Tracing: every entry point pushes an NVTX range "cwfem:<name>" and pops it on every return
+    path (here the argument-error returns, which need no GPU). A small NVTX injection library
+    (tests/nvtx_record.c, loaded by NVTX through NVTX_INJECTION64_PATH) records the ranges."""
+    import shutil
+    import subprocess
+    import sys
+    from paper_2607_03413_gb300 import build
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(build._nvcc())), "include")
+    gcc = shutil.which("gcc") or pytest.skip("no gcc")
+    rec = str(tmp_path / "libnvtx_record.so")
+    subprocess.run([gcc, "-shared", "-fPIC", "-O1", "-I", cuda_inc, os.path.join(ROOT, "tests", "nvtx_record.c"),
+                    "-o", rec], check=True)
+    log = tmp_path / "ranges.txt"
+    script = (
+        "import paper_2607_03413_gb300 as pkg\n"
+        "L = pkg.load()\n"
+        "E = pkg.CW_ERR_ARG\n"
+        "assert L.cw_apply(None, None, None, 0, None) == E\n"
+        "assert L.cw_cg_solve(None, None, None, 1e-8, 10, 0, None, None) == E\n"
+        "assert L.cw_mg_vcycle(None, None, None, 0, None) == E\n"
+        "assert L.cw_mblock_apply(None, None, None, 0, None) == E\n"
+    )
+    env = dict(os.environ, NVTX_INJECTION64_PATH=rec, NVTX_RECORD_FILE=str(log), PYTHONPATH=ROOT)
+    subprocess.run([sys.executable, "-c", script], check=True, env=env, cwd=ROOT, timeout=120)
+    lines = log.read_text().split("\n")[:-1]
+    assert lines == ["push cwfem:cw_apply", "pop", "push cwfem:cw_cg_solve", "pop",
+                     "push cwfem:cw_mg_vcycle", "pop", "push cwfem:cw_mblock_apply", "pop"]
