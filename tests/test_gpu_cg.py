@@ -205,7 +205,7 @@ def test_zero_right_hand_side_multigrid_and_multiblock(cw):
     assert rc == cw.CW_OK and st.iterations == 0 and torch.count_nonzero(u).item() == 0
 
 
-@pytest.mark.parametrize("mode", [0, 1], ids=["f64", "ir_f32"])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3], ids=["f64", "ir_f32", "ir_bf16", "f64_native"])
 def test_warm_start_resumes_a_solve(cw, orc, mode):
     """Checkpoint / resume: a solve stopped at rtol 1e-4, copied to the host and back, then continued
     with CW_CG_WARM_START reaches the oracle's direct solve; the residual stays relative to b, a
