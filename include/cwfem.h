@@ -464,8 +464,8 @@ cw_status cw_mblock_cg_solve(cw_mblock mb, const double *b, double *u, double rt
  * caller-managed memory pool or an allocator callback, a real-time loop whose memory is fixed at
  * start-up, or a host whose policy forbids cudaMalloc/cudaFree after initialisation. It solves the
  * same system with the same operator, preconditioner and stopping measure as cw_cg_solve for mode
- * CW_CG_F64 or CW_CG_F64_NATIVE (arguments, outputs and statuses as there), with three
- * differences: the inner CG restarts at every outer refinement step (no search direction carried
+ * CW_CG_F64 or CW_CG_F64_NATIVE (arguments, outputs and statuses as there; always from u = 0:
+ * CW_CG_WARM_START is rejected with CW_ERR_ARG), with three differences: the inner CG restarts at every outer refinement step (no search direction carried
  * over), the outer loop stops after 50 steps, and both the native-arithmetic inner operator and the
  * outer residual read the op's own float-pair metric (cw_cg_solve builds an IEEE-metric twin for
  * them, which would need an allocation). Iteration counts and round-off may therefore differ

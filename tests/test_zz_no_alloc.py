@@ -74,3 +74,14 @@ def test_noalloc_rejects_operators_beyond_its_limit(cw):
     rc, st = cw.cw_cg_solve_noalloc(op.handle, b, u, 1e-10, 10, 0)
     assert rc == cw.CW_ERR_ARG
     assert b"262144" in cw.load().cw_last_error()
+
+
+def test_noalloc_always_starts_from_zero(cw):
+    """The allocation-free solve has no warm start: CW_CG_WARM_START is an argument error there."""
+    import torch
+    M = cw.Mesh.from_synth(synth.box_mesh(3, perturb=0.1))
+    op = cw.Operator(M, 2, cw.CW_LAPLACE, cw.CW_GEOM_METRIC, cw.CW_PREC_F64, cw.CW_BC_DIRICHLET0)
+    b = op.load_vector(0)
+    u = torch.zeros_like(b)
+    rc, st = cw.cw_cg_solve_noalloc(op.handle, b, u, 1e-10, 10, cw.CW_CG_F64 | cw.CW_CG_WARM_START)
+    assert rc == cw.CW_ERR_ARG
