@@ -131,7 +131,8 @@ inline std::mutex &smem_opt_mutex()
 template <class K>
 static cudaError_t ensure_smem(K kernel, size_t smem, size_t (&opted)[kMaxDevices])
 {
-    if (smem <= 48 * 1024) return smem > 227 * 1024 ? cudaErrorInvalidConfiguration : cudaSuccess;
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;  // past the per-CTA limit
+    if (smem <= 48 * 1024) return cudaSuccess;                     // no opt-in needed
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
